@@ -23,6 +23,8 @@ OK = 0
 UNDER_BUDGET = 1
 SCORE_STRETCH = 0
 SCORE_RESISTANCE = 1
+METHOD_WALK = 0
+METHOD_DISTS = 1
 
 
 def build(force: bool = False) -> str:
@@ -46,7 +48,7 @@ def lib():
             L.orc_exact_sum.restype = f64
             L.orc_exact_sum.argtypes = [P, i64]
             L.orc_offtree_scores.restype = ctypes.c_int
-            L.orc_offtree_scores.argtypes = [i64, P, P, P, P, i32, ctypes.c_int, P, P, P, P, P, P, P, P]
+            L.orc_offtree_scores.argtypes = [i64, P, P, P, P, i32, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P, P]
             L.orc_recover.restype = ctypes.c_int
             L.orc_recover.argtypes = [i64, P, P, P, P, f64, i32, ctypes.c_int, i64, P, P, i64, P, P]
             _lib = L
@@ -67,15 +69,16 @@ def exact_sum(xs) -> float:
     return float(lib().orc_exact_sum(_p(a), a.shape[0]))
 
 
-def offtree_scores(g, c: int = 2, score_mode: int = SCORE_STRETCH) -> dict:
-    """Per off-tree edge (canonical id order): u, v, id, lca, resistance, score, beta."""
+def offtree_scores(g, c: int = 2, score_mode: int = SCORE_STRETCH, method: int = METHOD_WALK) -> dict:
+    """Per off-tree edge (canonical id order): u, v, id, lca, resistance, score, beta.
+    method: METHOD_WALK (path walk, the definition) or METHOD_DISTS (Algorithm 1)."""
     rp, col, w, par = _graph_arrays(g)
     E = max(int(rp[-1]) // 2 - g.n + 1, 1)
     out = {k: np.zeros(E, dtype=np.int32) for k in ("u", "v", "id", "lca", "beta")}
     out["resistance"] = np.zeros(E, dtype=np.float64)
     out["score"] = np.zeros(E, dtype=np.float64)
     n_off = np.zeros(1, dtype=np.int64)
-    st = lib().orc_offtree_scores(g.n, _p(rp), _p(col), _p(w), _p(par), c, score_mode, _p(n_off),
+    st = lib().orc_offtree_scores(g.n, _p(rp), _p(col), _p(w), _p(par), c, score_mode, method, _p(n_off),
                                   _p(out["u"]), _p(out["v"]), _p(out["id"]), _p(out["lca"]),
                                   _p(out["resistance"]), _p(out["score"]), _p(out["beta"]))
     if st != OK:

@@ -11,11 +11,17 @@
  *   1. Split the edges of G into tree and off-tree edges (Sec. 2.2, after
  *      Eq. RT).  Canonical edge id = rank of the CSR entry (u, v), u < v,
  *      among all such entries in row-major order.
- *   2. For every off-tree edge (u, v): l = LCA_T(u, v) by a naive ancestor
- *      walk; the resistance distance of Eq. RT, the sum of 1/w over the tree
- *      path u -> l -> v, summed EXACTLY (wide fixed-point accumulator) and
- *      rounded once to nearest-even FP64; the criticality score; and the
- *      density-aware step beta* = min(hops(u,l), hops(v,l), c) (Eq. beta-new).
+ *   2. For every off-tree edge (u, v): l = LCA_T(u, v); the resistance
+ *      distance of Eq. RT, the sum of 1/w over the tree path u -> l -> v,
+ *      computed EXACTLY and rounded once to nearest-even FP64; the
+ *      criticality score; and the density-aware step
+ *      beta* = min(hops(u,l), hops(v,l), c) (Eq. beta-new).  Two methods
+ *      that must agree bit for bit:
+ *        WALK  -- the definition: naive ancestor walk, path sum in a wide
+ *                 exact accumulator (slow on deep trees);
+ *        DISTS -- Algorithm 1 step 1: exact root distances "dists" (multi-
+ *                 limb integers) and a skip table for the LCA query, then
+ *                 R_T = D(u) + D(v) - 2 D(l) exactly.  Used by orc_recover.
  *   3. Order: score descending, ties by the smaller edge id (a stable sort of
  *      the id-ordered edge list, Algorithm 1 step 2).
  *   4. Subtasks: one index-linked list per LCA, in that order (Algorithm 1
@@ -52,6 +58,9 @@
 
 #define ORC_SCORE_STRETCH 0
 #define ORC_SCORE_RESISTANCE 1
+
+#define ORC_METHOD_WALK 0  /* explicit path walk: the definition of Eq. RT */
+#define ORC_METHOD_DISTS 1 /* Algorithm 1: dists + skip-table LCA, exact */
 
 /* ------------------------------------------------------------------------ */
 /* Exact sum of positive doubles: an integer N in units of 2^-1074 held in   */
@@ -318,6 +327,170 @@ static void score_one(const tree_t* t, int32_t u, int32_t v, double w, int32_t c
 }
 
 /* ------------------------------------------------------------------------ */
+/* Step 2 via Algorithm 1's own data: "dists" (exact root distances) and the */
+/* skip table S (binary lifting).  D(v) is an integer of `limbs` 64-bit words */
+/* in units of 2^(e_min - 52), where e_min is the smallest binary exponent of */
+/* any r(v): every r(v) is then an exact multiple of that unit, so sums are   */
+/* exact and R_T = D(u) + D(v) - 2 D(l) equals the path sum exactly.  The     */
+/* width adapts to the exponent range and the tree depth, so no input that    */
+/* the walk can handle is refused.                                            */
+
+typedef struct {
+  int limbs;
+  int e_min;
+  uint64_t* D;    /* n * limbs */
+  int levels;
+  int32_t* skip;  /* levels * n: skip[j*n + v] = 2^j-th ancestor or -1 */
+} dists_t;
+
+static void dists_free(dists_t* d) {
+  free(d->D);
+  free(d->skip);
+}
+
+static int exp_of(double x) {
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  return (int)((b >> 52) & 0x7ff) - 1023;
+}
+
+static int dists_build(dists_t* d, const tree_t* t) {
+  memset(d, 0, sizeof(*d));
+  int64_t n = t->n, maxdep = 0;
+  int e_min = 1 << 30, e_max = -(1 << 30);
+  for (int64_t v = 0; v < n; v++) {
+    if (t->depth[v] > maxdep) maxdep = t->depth[v];
+    if (t->parent[v] < 0) continue;
+    int e = exp_of(t->r[v]);
+    if (e < e_min) e_min = e;
+    if (e > e_max) e_max = e;
+  }
+  if (e_min > e_max) e_min = e_max = 0; /* single vertex */
+  int dep_bits = 0;
+  while ((1ll << dep_bits) <= maxdep) dep_bits++;
+  int bits = (e_max - e_min + 53) + dep_bits + 2; /* +1 for 2*D(l), +1 spare */
+  d->limbs = (bits + 63) / 64;
+  d->e_min = e_min;
+  d->D = (uint64_t*)calloc((size_t)n * (size_t)d->limbs, sizeof(uint64_t));
+  d->levels = dep_bits > 0 ? dep_bits : 1;
+  d->skip = (int32_t*)malloc(sizeof(int32_t) * (size_t)n * (size_t)d->levels);
+  if (!d->D || !d->skip) return ORC_E_OOM;
+  /* vertices by increasing depth (counting sort) so parents come first */
+  int64_t* cnt = (int64_t*)calloc((size_t)maxdep + 2, sizeof(int64_t));
+  int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!cnt || !ord) {
+    free(cnt);
+    free(ord);
+    return ORC_E_OOM;
+  }
+  for (int64_t v = 0; v < n; v++) cnt[t->depth[v] + 1]++;
+  for (int64_t i = 0; i <= maxdep; i++) cnt[i + 1] += cnt[i];
+  for (int64_t v = 0; v < n; v++) ord[cnt[t->depth[v]]++] = v;
+  int L = d->limbs;
+  for (int64_t i = 0; i < n; i++) {
+    int64_t v = ord[i];
+    int32_t p = t->parent[v];
+    if (p < 0) continue; /* root: D = 0 */
+    uint64_t* dv = d->D + (size_t)v * L;
+    const uint64_t* dp = d->D + (size_t)p * L;
+    for (int k = 0; k < L; k++) dv[k] = dp[k];
+    /* add r(v) = mant * 2^(e - 52) = (mant << (e - e_min)) units */
+    uint64_t b;
+    memcpy(&b, &t->r[v], 8);
+    uint64_t mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    int sh = exp_of(t->r[v]) - e_min;
+    int idx = sh / 64, off = sh % 64;
+    uint64_t lo = mant << off, hi = off ? (mant >> (64 - off)) : 0;
+    uint64_t carry = 0;
+    for (int k = idx; k < L; k++) {
+      uint64_t add = (k == idx) ? lo : (k == idx + 1 ? hi : 0);
+      uint64_t old = dv[k];
+      uint64_t s1 = old + add;
+      uint64_t c1 = s1 < old;
+      uint64_t s2 = s1 + carry;
+      uint64_t c2 = s2 < s1;
+      dv[k] = s2;
+      carry = c1 | c2;
+    }
+  }
+  free(cnt);
+  free(ord);
+  /* skip table: level 0 = parent, level j = level j-1 applied twice */
+  for (int64_t v = 0; v < n; v++) d->skip[v] = t->parent[v];
+  for (int j = 1; j < d->levels; j++)
+    for (int64_t v = 0; v < n; v++) {
+      int32_t a = d->skip[(size_t)(j - 1) * n + v];
+      d->skip[(size_t)j * n + v] = (a < 0) ? -1 : d->skip[(size_t)(j - 1) * n + a];
+    }
+  return ORC_OK;
+}
+
+static int32_t lca_query(const tree_t* t, const dists_t* d, int32_t u, int32_t v) {
+  int64_t n = t->n;
+  if (t->depth[u] < t->depth[v]) {
+    int32_t x = u;
+    u = v;
+    v = x;
+  }
+  int64_t diff = t->depth[u] - t->depth[v];
+  for (int j = 0; diff; j++, diff >>= 1)
+    if (diff & 1) u = d->skip[(size_t)j * n + u];
+  if (u == v) return u;
+  for (int j = d->levels - 1; j >= 0; j--) {
+    int32_t a = d->skip[(size_t)j * n + u], b = d->skip[(size_t)j * n + v];
+    if (a != b) {
+      u = a;
+      v = b;
+    }
+  }
+  return t->parent[u];
+}
+
+static void score_one_dists(const tree_t* t, const dists_t* d, int32_t u, int32_t v, double w, int32_t c,
+                            int score_mode, int32_t* lca_out, double* res_out, double* score_out,
+                            int32_t* beta_out) {
+  int32_t l = lca_query(t, d, u, v);
+  int L = d->limbs;
+  const uint64_t* du = d->D + (size_t)u * L;
+  const uint64_t* dv = d->D + (size_t)v * L;
+  const uint64_t* dl = d->D + (size_t)l * L;
+  /* (D(u) - D(l)) + (D(v) - D(l)), limb by limb */
+  uint64_t r[64];
+  uint64_t borrow1 = 0, borrow2 = 0, carry = 0;
+  for (int k = 0; k < L; k++) {
+    uint64_t a = du[k] - dl[k] - borrow1;
+    borrow1 = (du[k] < dl[k]) || (du[k] - dl[k] < borrow1);
+    uint64_t b = dv[k] - dl[k] - borrow2;
+    borrow2 = (dv[k] < dl[k]) || (dv[k] - dl[k] < borrow2);
+    uint64_t s1 = a + b;
+    uint64_t c1 = s1 < a;
+    uint64_t s2 = s1 + carry;
+    uint64_t c2 = s2 < s1;
+    r[k] = s2;
+    carry = c1 | c2;
+  }
+  /* into units of 2^-1074: shift left by 1074 + (e_min - 52) = 1022 + e_min */
+  exact_acc acc;
+  acc_zero(&acc);
+  int sh = 1022 + d->e_min;
+  for (int k = 0; k < L; k++) {
+    if (!r[k]) continue;
+    int64_t pos = (int64_t)k * 64 + sh;
+    int idx = (int)(pos / 64), off = (int)(pos % 64);
+    acc_add_at(&acc, idx, r[k] << off);
+    if (off) acc_add_at(&acc, idx + 1, r[k] >> (64 - off));
+  }
+  double R = acc_to_double(&acc);
+  *lca_out = l;
+  *res_out = R;
+  *score_out = (score_mode == ORC_SCORE_RESISTANCE) ? R : w * R;
+  int64_t hu = t->depth[u] - t->depth[l], hv = t->depth[v] - t->depth[l];
+  int64_t bs = hu < hv ? hu : hv;
+  if (bs > c) bs = c;
+  *beta_out = (int32_t)bs;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Step 3: order (score descending, id ascending)                             */
 
 typedef struct {
@@ -377,8 +550,8 @@ static int64_t budget_k(int64_t n, double alpha, int64_t k_override) {
 /* Per-off-tree-edge scores, in canonical id order.  All output arrays hold
  * m - n + 1 entries (caller-allocated). */
 int orc_offtree_scores(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
-                       int32_t c, int score_mode, int64_t* n_off, int32_t* off_u, int32_t* off_v, int32_t* off_id,
-                       int32_t* lca, double* resistance, double* score, int32_t* beta) {
+                       int32_t c, int score_mode, int method, int64_t* n_off, int32_t* off_u, int32_t* off_v,
+                       int32_t* off_id, int32_t* lca, double* resistance, double* score, int32_t* beta) {
   if (n <= 0 || !row_ptr || !col || !w || !parent || c < 0 || !n_off) return ORC_E_ARG;
   tree_t t;
   int st = tree_build(&t, n, row_ptr, col, w, parent);
@@ -393,13 +566,25 @@ int orc_offtree_scores(int64_t n, const int64_t* row_ptr, const int32_t* col, co
     tree_free(&t);
     return st;
   }
+  dists_t d;
+  memset(&d, 0, sizeof(d));
+  if (method == ORC_METHOD_DISTS && (st = dists_build(&d, &t)) != ORC_OK) {
+    dists_free(&d);
+    offtree_free(&o);
+    tree_free(&t);
+    return st;
+  }
   for (int64_t i = 0; i < o.count; i++) {
     off_u[i] = o.u[i];
     off_v[i] = o.v[i];
     off_id[i] = o.id[i];
-    score_one(&t, o.u[i], o.v[i], o.w[i], c, score_mode, &lca[i], &resistance[i], &score[i], &beta[i]);
+    if (method == ORC_METHOD_DISTS)
+      score_one_dists(&t, &d, o.u[i], o.v[i], o.w[i], c, score_mode, &lca[i], &resistance[i], &score[i], &beta[i]);
+    else
+      score_one(&t, o.u[i], o.v[i], o.w[i], c, score_mode, &lca[i], &resistance[i], &score[i], &beta[i]);
   }
   *n_off = o.count;
+  dists_free(&d);
   offtree_free(&o);
   tree_free(&t);
   return ORC_OK;
@@ -447,8 +632,18 @@ int orc_recover(int64_t n, const int64_t* row_ptr, const int32_t* col, const dou
     st = ORC_E_OOM;
     goto done;
   }
-  /* step 2: scores */
-  for (int64_t i = 0; i < E; i++) score_one(&t, o.u[i], o.v[i], o.w[i], c, score_mode, &lca[i], &res[i], &sc[i], &beta[i]);
+  /* step 2: scores (dists + skip table, Algorithm 1 step 1) */
+  {
+    dists_t d;
+    st = dists_build(&d, &t);
+    if (st != ORC_OK) {
+      dists_free(&d);
+      goto done;
+    }
+    for (int64_t i = 0; i < E; i++)
+      score_one_dists(&t, &d, o.u[i], o.v[i], o.w[i], c, score_mode, &lca[i], &res[i], &sc[i], &beta[i]);
+    dists_free(&d);
+  }
   /* step 3: global order */
   for (int64_t i = 0; i < E; i++) {
     ord[i].score = sc[i];
@@ -456,9 +651,17 @@ int orc_recover(int64_t n, const int64_t* row_ptr, const int32_t* col, const dou
     ord[i].idx = i;
   }
   qsort(ord, (size_t)E, sizeof(order_item), cmp_order);
+  /* Steps 4-5 run on a prefix [0, P) of the global order: the greedy decides
+   * every edge from earlier edges only, so its decisions inside a prefix do
+   * not depend on what follows.  If the prefix yields fewer than k recovered
+   * edges it is enlarged and the greedy restarts. */
+  int run_full = (out_full_count != NULL);
+  int64_t P = run_full ? E : (2 * k + 1024 < E ? 2 * k + 1024 : E);
+  int64_t taken = 0, full = 0;
+restart:
   /* step 4: subtasks = index-linked lists per LCA, in global order */
   for (int64_t x = 0; x < n; x++) task_tail[x] = -1;
-  for (int64_t pos = E - 1; pos >= 0; pos--) {
+  for (int64_t pos = P - 1; pos >= 0; pos--) {
     int32_t l = lca[ord[pos].idx];
     next_in_task[pos] = task_tail[l]; /* built back to front: head is the earliest */
     task_tail[l] = pos;
@@ -467,10 +670,11 @@ int orc_recover(int64_t n, const int64_t* row_ptr, const int32_t* col, const dou
     stamp_u[x] = -1;
     stamp_v[x] = -1;
   }
+  if (P > 0) memset(marked, 0, (size_t)P);
+  taken = 0;
+  full = 0;
   /* step 5: greedy over the global order */
-  int64_t taken = 0, full = 0;
-  int run_full = (out_full_count != NULL);
-  for (int64_t pos = 0; pos < E; pos++) {
+  for (int64_t pos = 0; pos < P; pos++) {
     if (marked[pos]) continue; /* the "continue" branch */
     int64_t i = ord[pos].idx;
     if (taken < k) {
@@ -493,6 +697,10 @@ int orc_recover(int64_t n, const int64_t* row_ptr, const int32_t* col, const dou
       int sim = (stamp_u[uu] == pos && stamp_v[vv] == pos) || (stamp_v[uu] == pos && stamp_u[vv] == pos);
       if (sim) marked[q] = 1;
     }
+  }
+  if (taken < k && P < E) {
+    P = (4 * P < E) ? 4 * P : E;
+    goto restart;
   }
   *out_count = taken;
   if (out_full_count) *out_full_count = full;

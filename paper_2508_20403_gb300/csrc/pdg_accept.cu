@@ -1,0 +1,479 @@
+// Steps A5 + A6: density-aware scheduling of the subtasks and the
+// strict-similarity greedy inside each of them (Sec. 4.1; Algorithm 1 step 4).
+//
+// Semantics (per subtask, candidates in rank order): a candidate is recovered
+// unless an earlier recovered candidate e = (u, v) of the subtask has it
+// strictly similar, i.e. (u' in S_u and v' in S_v) or (u' in S_v and v' in
+// S_u), with S_x = the beta*_e-hop neighbourhood of x in T (Def. "Similar
+// edge (Strict)", Eq. beta-new).  Tree facts used instead of a BFS:
+//   hops(x, y) <= b  <=>  exists i, j >= 0, i + j <= b, anc_i(x) == anc_j(y)
+// where anc_i is the i-th ancestor.  Every candidate carries its endpoints'
+// ancestors anc_0..c.
+//
+// Tiers (the paper's mixed strategy, re-cut for a GPU):
+//   size 1            recovered outright (no earlier edge can mark it);
+//   2..warp_tier_max  one warp per subtask: lane t holds candidate t, a
+//                     32-bit conflict mask per lane is built from shuffled
+//                     records, then the in-order resolution (an edge survives
+//                     iff no earlier survivor's bit is set in its mask) runs
+//                     as a 32-step shuffle loop -- the sequential semantics
+//                     without any shared-memory round trip;
+//   larger            the cooperative tier: all candidates of all large
+//                     subtasks at once, in rounds over an exact hash index.
+//
+// Cooperative tier.  A candidate e registers keys (anc_j(u), anc_j'(v), j, j')
+// for j, j' <= beta*_e.  A candidate e' = (x, y) (both orientations) probes
+// keys (anc_i(x), anc_i'(y), j, j'): such a key can only come from an edge e
+// of the same subtask (the key determines the LCA) with
+// hops(u, l) = j + hops(x, l) - i and hops(v, l) = j' + hops(y, l) - i', so
+// the prober knows beta*_e exactly and probes only keys for which
+// i + j <= beta*_e and i' + j' <= beta*_e -- every hit is a true marker.
+// Each key slot keeps the smallest rank of an accepted registrant and the
+// smallest rank of a still-undecided registrant (tagged with the round).
+// Per round: undecided e' is REJECTED if a hit has an accepted rank below its
+// own, ACCEPTED if no hit has an undecided rank below its own, else it waits.
+// The earliest undecided candidate of every subtask always decides, so the
+// rounds converge to the sequential result; after max_rounds a serial
+// finisher (one thread per subtask, in rank order) completes the rest.
+#include "pdg_internal.cuh"
+
+namespace pdg {
+
+namespace {
+
+constexpr int kA = PDG_MAX_C + 1;  // ancestors anc_0..anc_c per endpoint
+
+struct Rec {
+  int32_t U[kA], V[kA];
+  int32_t du, dv, b, rank;
+};
+
+__device__ __forceinline__ void load_rec(const Handle* hp, int64_t s, int c, Rec& r, const int32_t* rec_u,
+                                         const int32_t* rec_v, const int32_t* rec_anc, const int32_t* rec_du,
+                                         const int32_t* rec_dv, const uint8_t* rec_b, const int32_t* rec_rank,
+                                         int64_t cap) {
+  r.U[0] = rec_u[s];
+  r.V[0] = rec_v[s];
+#pragma unroll
+  for (int j = 1; j < kA; j++) {
+    r.U[j] = (j <= c) ? rec_anc[(int64_t)(j - 1) * cap + s] : -1;
+    r.V[j] = (j <= c) ? rec_anc[(int64_t)(c + j - 1) * cap + s] : -1;
+  }
+  r.du = rec_du[s];
+  r.dv = rec_dv[s];
+  r.b = rec_b[s];
+  r.rank = rec_rank[s];
+}
+
+// hops(x', x) <= b, given anc_0..b of both (X[j] is valid for j <= b)
+__device__ __forceinline__ bool in_ball(const int32_t (&Xp)[kA], const int32_t (&X)[kA], int b) {
+  bool hit = false;
+#pragma unroll
+  for (int j = 0; j < kA; j++)
+#pragma unroll
+    for (int i = 0; i < kA; i++)
+      if (i + j <= b && Xp[i] == X[j]) hit = true;
+  return hit;
+}
+
+// is e' (Up, Vp) strictly similar to e (U, V, b)?
+__device__ __forceinline__ bool strictly_similar(const int32_t (&Up)[kA], const int32_t (&Vp)[kA],
+                                                 const int32_t (&U)[kA], const int32_t (&V)[kA], int b) {
+  return (in_ball(Up, U, b) && in_ball(Vp, V, b)) || (in_ball(Up, V, b) && in_ball(Vp, U, b));
+}
+
+__device__ __forceinline__ int32_t anc_step(const int32_t* __restrict__ parent, const int32_t* __restrict__ up1,
+                                            int32_t x, int j) {
+  // j-th ancestor for j <= 3 from level 0 (parent) and level 1 (anc_2)
+  if (x < 0 || j == 0) return x;
+  if (j == 1) return parent[x];
+  if (up1 == nullptr) {  // tree of depth <= 1 has no level 1: anc_2 is above the root
+    return -1;
+  }
+  int32_t y = up1[x];
+  if (j == 2) return y;
+  return y < 0 ? -1 : parent[y];
+}
+
+__global__ void __launch_bounds__(kBlock) k_build_records(
+    const int32_t* __restrict__ lsort_rank, const int32_t* __restrict__ rank_cand, const int32_t* __restrict__ cand_idx,
+    const int32_t* __restrict__ ou, const int32_t* __restrict__ ov, const int32_t* __restrict__ lca,
+    const u128* __restrict__ P, const int32_t* __restrict__ parent, const int32_t* __restrict__ up1, int c,
+    const DevScalars* __restrict__ dsc, int64_t cap, int32_t* __restrict__ rec_u, int32_t* __restrict__ rec_v,
+    int32_t* __restrict__ rec_anc, int32_t* __restrict__ rec_du, int32_t* __restrict__ rec_dv,
+    uint8_t* __restrict__ rec_b, int32_t* __restrict__ rec_rank, int32_t* __restrict__ rec_lca) {
+  const int64_t N = dsc->n_cand;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = lsort_rank[s];
+    const int32_t i = cand_idx[rank_cand[r]];
+    const int32_t u = ou[i], v = ov[i], l = lca[i];
+    const int32_t dl = (int32_t)(uint32_t)P[l];
+    const int32_t du = (int32_t)(uint32_t)P[u] - dl, dv = (int32_t)(uint32_t)P[v] - dl;
+    rec_u[s] = u;
+    rec_v[s] = v;
+    for (int j = 1; j <= c; j++) {
+      rec_anc[(int64_t)(j - 1) * cap + s] = anc_step(parent, up1, u, j);
+      rec_anc[(int64_t)(c + j - 1) * cap + s] = anc_step(parent, up1, v, j);
+    }
+    rec_du[s] = du;
+    rec_dv[s] = dv;
+    rec_b[s] = (uint8_t)min(min(du, dv), c);
+    rec_rank[s] = r;
+    rec_lca[s] = l;
+  }
+}
+
+__global__ void k_seg_flags(const int32_t* __restrict__ rec_lca, const DevScalars* __restrict__ dsc,
+                            int32_t* __restrict__ flags) {
+  const int64_t N = dsc->n_cand;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
+    flags[s] = (s == 0 || rec_lca[s] != rec_lca[s - 1]) ? 1 : 0;
+}
+
+// out[scan[i]] = i for flagged i; *count_out = number flagged
+__global__ void k_scatter_idx(const int32_t* __restrict__ flags, const int64_t* __restrict__ scan,
+                              const int64_t* __restrict__ n_dev, int32_t* __restrict__ out,
+                              int64_t* __restrict__ count_out, int64_t tail_value_at_count) {
+  const int64_t N = *n_dev;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    if (flags[i]) out[scan[i]] = (int32_t)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t cnt = scan[N];
+    if (count_out) *count_out = cnt;
+    if (tail_value_at_count >= 0) out[cnt] = (int32_t)N;  // sentinel end of the last segment
+  }
+}
+
+// per segment: tier flags (warp tier / cooperative tier) and statistics
+__global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
+                           int32_t* __restrict__ fw, int32_t* __restrict__ fb) {
+  const int64_t S = dsc->n_seg;
+  int64_t mx = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < S; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sz = seg_begin[q + 1] - seg_begin[q];
+    fw[q] = (sz >= 2 && sz <= warp_max) ? 1 : 0;
+    fb[q] = (sz > warp_max) ? 1 : 0;
+    mx = max(mx, sz);
+  }
+  mx = __reduce_max_sync(0xffffffffu, (unsigned)min(mx, (int64_t)0x7fffffff));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax((unsigned long long*)&dsc->max_seg, (unsigned long long)mx);
+}
+
+// per position: singletons are recovered; cooperative-tier positions flagged
+__global__ void k_pos_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
+                           const int32_t* __restrict__ rec_rank, const uint8_t* __restrict__ rec_b,
+                           uint8_t* __restrict__ acc_flag, int32_t* __restrict__ fbig, uint8_t* __restrict__ state) {
+  const int64_t N = dsc->n_cand;
+  const int32_t S = (int32_t)dsc->n_seg;
+  unsigned long long regs = 0;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = S;  // segment q with seg_begin[q] <= s < seg_begin[q+1]
+    while (hi - lo > 1) {
+      int32_t mid = (lo + hi) >> 1;
+      if (seg_begin[mid] <= s) lo = mid; else hi = mid;
+    }
+    const int64_t sz = seg_begin[lo + 1] - seg_begin[lo];
+    int32_t big = 0;
+    if (sz == 1) acc_flag[rec_rank[s]] = 1;
+    else if (sz > warp_max) {
+      big = 1;
+      state[s] = ST_UNDECIDED;
+      const unsigned b = rec_b[s];
+      regs += (unsigned long long)(b + 1) * (b + 1);
+    }
+    fbig[s] = big;
+  }
+  for (int o = 16; o; o >>= 1) regs += __shfl_down_sync(0xffffffffu, regs, o);
+  if ((threadIdx.x & 31) == 0 && regs) atomicAdd((unsigned long long*)&dsc->big_regs, regs);
+}
+
+// ------------------------------------------------------------------ warp tier
+
+__global__ void __launch_bounds__(kBlock) k_accept_warp(
+    const int32_t* __restrict__ warp_seg, const DevScalars* __restrict__ dsc, const int32_t* __restrict__ seg_begin,
+    int c, int64_t cap, const int32_t* __restrict__ rec_u, const int32_t* __restrict__ rec_v,
+    const int32_t* __restrict__ rec_anc, const int32_t* __restrict__ rec_du, const int32_t* __restrict__ rec_dv,
+    const uint8_t* __restrict__ rec_b, const int32_t* __restrict__ rec_rank, uint8_t* __restrict__ acc_flag) {
+  const int64_t nw = dsc->n_warp_seg;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x = warp; x < nw; x += nwarps) {
+    const int32_t q = warp_seg[x];
+    const int32_t b0 = seg_begin[q];
+    const int sz = seg_begin[q + 1] - b0;
+    Rec me;
+    if (lane < sz) load_rec(nullptr, b0 + lane, c, me, rec_u, rec_v, rec_anc, rec_du, rec_dv, rec_b, rec_rank, cap);
+    else {
+#pragma unroll
+      for (int j = 0; j < kA; j++) me.U[j] = me.V[j] = -1;
+      me.b = 0;
+      me.rank = 0;
+    }
+    unsigned mask = 0;  // bit s: my edge is strictly similar to lane s's edge (s < me)
+    for (int s = 0; s < sz - 1; s++) {
+      int32_t U[kA], V[kA];
+#pragma unroll
+      for (int j = 0; j < kA; j++) {
+        U[j] = __shfl_sync(0xffffffffu, me.U[j], s);
+        V[j] = __shfl_sync(0xffffffffu, me.V[j], s);
+      }
+      const int b = __shfl_sync(0xffffffffu, me.b, s);
+      if (lane > s && lane < sz && strictly_similar(me.U, me.V, U, V, b)) mask |= 1u << s;
+    }
+    unsigned acc = 0;
+    for (int s = 0; s < sz; s++) {
+      const unsigned ms = __shfl_sync(0xffffffffu, mask, s);
+      if ((ms & acc) == 0) acc |= 1u << s;
+    }
+    if (lane < sz) acc_flag[me.rank] = (acc >> lane) & 1u;
+  }
+}
+
+// ------------------------------------------------------------- cooperative tier
+
+__device__ __forceinline__ uint64_t pack_key(int32_t z1, int32_t z2, int j, int jp) {
+  return ((uint64_t)(uint32_t)z1 << 34) | ((uint64_t)(uint32_t)z2 << 4) | ((uint64_t)j << 2) | (uint64_t)jp;
+}
+
+__device__ __forceinline__ int64_t slot_of(uint64_t key, uint64_t cap) {
+  return (int64_t)__umul64hi(mix64(key), cap);
+}
+
+__device__ int64_t table_insert(uint64_t* __restrict__ tkey, uint64_t cap, uint64_t key, DevScalars* dsc) {
+  int64_t s = slot_of(key, cap);
+  for (uint64_t probe = 0; probe < cap; probe++) {
+    uint64_t k = tkey[s];
+    if (k == key) return s;
+    if (k == kEmptyKey) {
+      k = atomicCAS((unsigned long long*)&tkey[s], (unsigned long long)kEmptyKey, (unsigned long long)key);
+      if (k == kEmptyKey || k == key) return s;
+    }
+    if (++s == (int64_t)cap) s = 0;
+  }
+  atomicOr(&dsc->err, ERR_TABLE);
+  return -1;
+}
+
+__device__ __forceinline__ int64_t table_find(const uint64_t* __restrict__ tkey, uint64_t cap, uint64_t key) {
+  int64_t s = slot_of(key, cap);
+  for (uint64_t probe = 0; probe < cap; probe++) {
+    const uint64_t k = tkey[s];
+    if (k == key) return s;
+    if (k == kEmptyKey) return -1;
+    if (++s == (int64_t)cap) s = 0;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
+
+__global__ void k_table_clear(uint64_t* __restrict__ tkey, uint32_t* __restrict__ tacc, uint64_t* __restrict__ tund,
+                              DevScalars* dsc, int64_t table_cap, uint64_t* __restrict__ cap_out) {
+  // effective capacity: twice the registrations (load <= 0.5), at least 1024
+  int64_t want = 2 * dsc->big_regs;
+  if (want < 1024) want = 1024;
+  if (want > table_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&dsc->err, ERR_TABLE);
+    want = table_cap;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *cap_out = (uint64_t)want;
+  if (dsc->n_big == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < want; i += (int64_t)gridDim.x * blockDim.x) {
+    tkey[i] = kEmptyKey;
+    tacc[i] = 0xffffffffu;
+    tund[i] = ~0ull;
+  }
+}
+
+struct BigArgs {
+  const int32_t* big_pos;
+  const int32_t* rec_u;
+  const int32_t* rec_v;
+  const int32_t* rec_anc;
+  const int32_t* rec_du;
+  const int32_t* rec_dv;
+  const uint8_t* rec_b;
+  const int32_t* rec_rank;
+  uint8_t* state;
+  uint64_t* tkey;
+  uint32_t* tacc;
+  uint64_t* tund;
+  const uint64_t* cap;
+  int64_t* und_count;  // per round
+  int64_t rec_cap;
+  int c;
+};
+
+__device__ __forceinline__ void register_keys(const BigArgs& a, const Rec& r, bool accepted, uint64_t und_val,
+                                              uint64_t cap, DevScalars* dsc) {
+  for (int j = 0; j <= r.b; j++)
+    for (int jp = 0; jp <= r.b; jp++) {
+      const int64_t s = table_insert(a.tkey, cap, pack_key(r.U[j], r.V[jp], j, jp), dsc);
+      if (s < 0) return;
+      if (accepted) atomicMin(&a.tacc[s], (uint32_t)r.rank);
+      else atomicMin((unsigned long long*)&a.tund[s], (unsigned long long)und_val);
+    }
+}
+
+// probe outcome: 2 = rejected, 1 = must wait, 0 = free
+template <bool WITH_UND>
+__device__ __forceinline__ int probe_all(const BigArgs& a, const Rec& r, uint64_t tag, uint64_t cap) {
+  int res = 0;
+  const int c = a.c;
+  for (int o = 0; o < 2; o++) {
+    const int32_t* X = o ? r.V : r.U;
+    const int32_t* Y = o ? r.U : r.V;
+    const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
+    for (int i = 0; i <= min(c, dx); i++) {
+      const int h1 = dx - i;
+      for (int ip = 0; ip <= min(c, dy); ip++) {
+        const int h2 = dy - ip;
+        for (int j = 0; j + i <= c; j++)
+          for (int jp = 0; jp + ip <= c; jp++) {
+            const int bb = min(min(j + h1, jp + h2), c);
+            if (i + j > bb || ip + jp > bb) continue;
+            const int64_t s = table_find(a.tkey, cap, pack_key(X[i], Y[ip], j, jp));
+            if (s < 0) continue;
+            if (a.tacc[s] < (uint32_t)r.rank) return 2;
+            if (WITH_UND) {
+              const uint64_t uv = a.tund[s];
+              if ((uv & 0xffffffff00000000ull) == tag && (uint32_t)uv < (uint32_t)r.rank) res = 1;
+            }
+          }
+      }
+    }
+  }
+  return res;
+}
+
+__device__ __forceinline__ void load_big(const BigArgs& a, int64_t s, Rec& r) {
+  load_rec(nullptr, s, a.c, r, a.rec_u, a.rec_v, a.rec_anc, a.rec_du, a.rec_dv, a.rec_b, a.rec_rank, a.rec_cap);
+}
+
+__global__ void __launch_bounds__(kBlock) k_big_register(BigArgs a, DevScalars* dsc, int round) {
+  if (round > 1 && a.und_count[round - 1] == 0) return;
+  const int64_t nb = dsc->n_big;
+  const uint64_t cap = *a.cap;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = a.big_pos[q];
+    const uint8_t st = a.state[s];
+    if (st != ST_UNDECIDED && st != ST_ACCEPTED_NEW) continue;
+    Rec r;
+    load_big(a, s, r);
+    if (st == ST_UNDECIDED) {
+      register_keys(a, r, false, und_tag(round) | (uint64_t)(uint32_t)r.rank, cap, dsc);
+    } else {
+      register_keys(a, r, true, 0, cap, dsc);
+      a.state[s] = ST_ACCEPTED;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_big_probe(BigArgs a, DevScalars* dsc, int round) {
+  if (round > 1 && a.und_count[round - 1] == 0) return;
+  const int64_t nb = dsc->n_big;
+  const uint64_t cap = *a.cap;
+  const uint64_t tag = und_tag(round);
+  int64_t waiting = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = a.big_pos[q];
+    if (a.state[s] != ST_UNDECIDED) continue;
+    Rec r;
+    load_big(a, s, r);
+    const int res = probe_all<true>(a, r, tag, cap);
+    if (res == 2) a.state[s] = ST_REJECTED;
+    else if (res == 0) a.state[s] = ST_ACCEPTED_NEW;
+    else waiting++;
+  }
+  for (int o = 16; o; o >>= 1) waiting += __shfl_down_sync(0xffffffffu, waiting, o);
+  if ((threadIdx.x & 31) == 0 && waiting) atomicAdd((unsigned long long*)&a.und_count[round], (unsigned long long)waiting);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&dsc->rounds_used, round);
+}
+
+// serial completion in rank order, one thread per cooperative subtask
+__global__ void k_big_finish(BigArgs a, DevScalars* dsc, const int32_t* __restrict__ big_seg,
+                             const int32_t* __restrict__ seg_begin, int last_round) {
+  if (a.und_count[last_round] == 0) return;
+  const int64_t ns = dsc->n_big_seg;
+  const uint64_t cap = *a.cap;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ns; x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = big_seg[x];
+    for (int32_t s = seg_begin[q]; s < seg_begin[q + 1]; s++) {
+      const uint8_t st = a.state[s];
+      if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
+      Rec r;
+      load_big(a, s, r);
+      if (st == ST_UNDECIDED && probe_all<false>(a, r, 0, cap) == 2) {
+        a.state[s] = ST_REJECTED;
+        continue;
+      }
+      register_keys(a, r, true, 0, cap, dsc);
+      a.state[s] = ST_ACCEPTED;
+    }
+  }
+}
+
+__global__ void k_big_flags(BigArgs a, DevScalars* dsc, uint8_t* __restrict__ acc_flag) {
+  const int64_t nb = dsc->n_big;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = a.big_pos[q];
+    const uint8_t st = a.state[s];
+    acc_flag[a.rec_rank[s]] = (st == ST_ACCEPTED || st == ST_ACCEPTED_NEW) ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+int step_accept(Handle& h, int c) {
+  const int grid = h.num_sms * 8;
+  const int64_t cap = h.Rcap;
+  const int32_t* up1 = (h.J >= 2) ? h.up : nullptr;
+  int st;
+  k_build_records<<<grid, kBlock, 0, h.stream>>>(h.lsort_rank, h.rank_cand, h.cand_idx, h.off_u, h.off_v, h.lca,
+                                                  h.P[h.p_final], h.parent, up1, c, h.dsc, cap, h.rec_u, h.rec_v,
+                                                  h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.rec_lca);
+  k_seg_flags<<<grid, kBlock, 0, h.stream>>>(h.rec_lca, h.dsc, h.flags);
+  PDG_CUDA(cudaGetLastError());
+  // segment starts -> seg_begin[0..n_seg], seg_begin[n_seg] = N
+  if ((st = scan_excl_i32(h, h.flags, h.scan_tmp, 0, &h.dsc->n_cand, cap))) return st;
+  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(h.flags, h.scan_tmp, &h.dsc->n_cand, h.seg_begin, &h.dsc->n_seg, 1);
+  // tiers per segment
+  int32_t* fw = h.flags;              // reuse: n_seg <= N
+  int32_t* fb = h.flags + cap + 1;    // second half of the flag buffer
+  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, fw, fb);
+  PDG_CUDA(cudaGetLastError());
+  if ((st = scan_excl_i32(h, fw, h.scan_tmp, 0, &h.dsc->n_seg, cap))) return st;
+  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fw, h.scan_tmp, &h.dsc->n_seg, h.warp_seg, &h.dsc->n_warp_seg, -1);
+  if ((st = scan_excl_i32(h, fb, h.scan_tmp, 0, &h.dsc->n_seg, cap))) return st;
+  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fb, h.scan_tmp, &h.dsc->n_seg, h.big_seg, &h.dsc->n_big_seg, -1);
+  // per position: singletons, cooperative-tier membership
+  int32_t* fpos = h.flags;
+  k_pos_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.rec_rank, h.rec_b, h.acc_flag,
+                                            fpos, h.state);
+  PDG_CUDA(cudaGetLastError());
+  if ((st = scan_excl_i32(h, fpos, h.scan_tmp, 0, &h.dsc->n_cand, cap))) return st;
+  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fpos, h.scan_tmp, &h.dsc->n_cand, h.big_pos, &h.dsc->n_big, -1);
+  // warp tier
+  k_accept_warp<<<grid, kBlock, 0, h.stream>>>(h.warp_seg, h.dsc, h.seg_begin, c, cap, h.rec_u, h.rec_v, h.rec_anc,
+                                               h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.acc_flag);
+  PDG_CUDA(cudaGetLastError());
+  // cooperative tier
+  uint64_t* d_cap = reinterpret_cast<uint64_t*>(h.blk_a + 9000);
+  int64_t* und_count = h.blk_a + 9100;  // [0 .. max_rounds]
+  const int R = std::max(1, std::min(h.opt.max_rounds, 64));
+  PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
+  k_table_clear<<<grid, kBlock, 0, h.stream>>>(h.tkey, h.tacc, h.tund, h.dsc, h.table_cap, d_cap);
+  BigArgs a{h.big_pos, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.state,
+            h.tkey, h.tacc, h.tund, d_cap, und_count, cap, c};
+  for (int r = 1; r <= R; r++) {
+    k_big_register<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+    k_big_probe<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+  }
+  k_big_finish<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.big_seg, h.seg_begin, R);
+  k_big_flags<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.acc_flag);
+  PDG_CUDA(cudaGetLastError());
+  return PDG_OK;
+}
+
+}  // namespace pdg

@@ -1,0 +1,637 @@
+// C ABI of the library (include/pdgrass.h): handle life cycle, input upload,
+// the recovery driver (steps A1-A7 on the handle's stream, with the prefix
+// retry of step A7) and small queries.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pdg_internal.cuh"
+
+namespace pdg {
+
+int check_cuda(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return PDG_E_OOM;
+  }
+  return PDG_E_CUDA;
+}
+
+int grid_for(const Handle& h, int64_t work, int per_block) {
+  int64_t blocks = (work + per_block - 1) / per_block;
+  int64_t cap = (int64_t)h.num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+int device_alloc(Handle& h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return PDG_E_OOM;
+  }
+  h.allocs.push_back(*p);
+  h.device_bytes += bytes;
+  return PDG_OK;
+}
+
+static void device_release(Handle& h, void* p) {
+  if (!p) return;
+  auto it = std::find(h.allocs.begin(), h.allocs.end(), p);
+  if (it != h.allocs.end()) h.allocs.erase(it);
+  cudaFree(p);
+}
+
+template <typename T>
+static int alloc_n(Handle& h, T** p, int64_t count) {
+  return device_alloc(h, reinterpret_cast<void**>(p), sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+}
+
+namespace {
+
+__global__ void k_gather_rowptr(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ vtx_ptr, int32_t G,
+                                int64_t* __restrict__ out) {
+  for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += gridDim.x * blockDim.x) out[g] = row_ptr[vtx_ptr[g]];
+}
+
+__global__ void k_reset_recover(DevScalars* dsc) {
+  dsc->err = 0;
+  dsc->e_min = INT_MAX;
+  dsc->e_max = INT_MIN;
+}
+
+__global__ void k_reset_attempt(DevScalars* dsc) {
+  dsc->err &= ERR_RANGE;
+  dsc->rounds_used = 0;
+  dsc->n_cand = 0;
+  dsc->n_seg = 0;
+  dsc->n_warp_seg = 0;
+  dsc->n_big = 0;
+  dsc->n_big_seg = 0;
+  dsc->max_seg = 0;
+  dsc->big_regs = 0;
+  dsc->undecided = 0;
+  dsc->radix_sel = 0;
+  dsc->radix_skip = 0;
+  dsc->radix_len = 0;
+  dsc->n_warp_cand = 0;
+}
+
+// upper entries (col > row) per row: endpoints of canonical ids
+__global__ void k_upper_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n,
+                              int64_t* __restrict__ cnt) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = row_ptr[u], e = row_ptr[u + 1];
+    cnt[u] = e - lower_bound_i32(col, b, e, (int32_t)(u + 1));
+  }
+}
+
+__global__ void k_endpoints(const int64_t* __restrict__ up_ptr, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col, int64_t n, int64_t m, const int32_t* __restrict__ ids,
+                            int64_t count, int32_t* __restrict__ ou, int32_t* __restrict__ ov, DevScalars* dsc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t id = ids[i];
+    if (id < 0 || id >= m) {
+      atomicOr(&dsc->err, ERR_CAPACITY);
+      ou[i] = ov[i] = -1;
+      continue;
+    }
+    int64_t lo = 0, hi = n;  // up_ptr[lo] <= id < up_ptr[hi]
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (up_ptr[mid] <= id) lo = mid; else hi = mid;
+    }
+    const int64_t b = row_ptr[lo], e = row_ptr[lo + 1];
+    const int64_t first = lower_bound_i32(col, b, e, (int32_t)(lo + 1));
+    ou[i] = (int32_t)lo;
+    ov[i] = col[first + (id - up_ptr[lo])];
+  }
+}
+
+}  // namespace
+
+int ensure_candidates(Handle& h, int64_t R, int c) {
+  const int64_t Rmax = std::max<int64_t>(h.E_off, 1);
+  R = std::min<int64_t>(std::max<int64_t>(R, 1), Rmax);
+  int st;
+  if (R > h.Rcap) {
+    void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp, h.flags,
+                   h.radix_hist, h.radix_off, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
+                   h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg};
+    for (void* p : old) device_release(h, p);
+    const int64_t tiles = (R + kTile - 1) / kTile;
+    if ((st = alloc_n(h, &h.cand_idx, R)) || (st = alloc_n(h, &h.rk[0], R)) || (st = alloc_n(h, &h.rk[1], R)) ||
+        (st = alloc_n(h, &h.rv[0], R)) || (st = alloc_n(h, &h.rv[1], R)) || (st = alloc_n(h, &h.rank_cand, R)) ||
+        (st = alloc_n(h, &h.lsort_rank, R)) || (st = alloc_n(h, &h.scan_tmp, R + 1)) ||
+        (st = alloc_n(h, &h.flags, 2 * (R + 1))) || (st = alloc_n(h, &h.radix_hist, 256 * tiles)) ||
+        (st = alloc_n(h, &h.radix_off, 256 * tiles + 1)) || (st = alloc_n(h, &h.rec_u, R)) ||
+        (st = alloc_n(h, &h.rec_v, R)) || (st = alloc_n(h, &h.rec_anc, 2 * PDG_MAX_C * R)) ||
+        (st = alloc_n(h, &h.rec_du, R)) || (st = alloc_n(h, &h.rec_dv, R)) || (st = alloc_n(h, &h.rec_rank, R)) ||
+        (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
+        (st = alloc_n(h, &h.acc_flag, R)) || (st = alloc_n(h, &h.seg_begin, R + 1)) ||
+        (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R))) {
+      h.Rcap = 0;
+      return st;
+    }
+    h.Rcap = R;
+  }
+  const int64_t want_table = std::max<int64_t>(1024, 2 * (int64_t)(c + 1) * (c + 1) * h.Rcap);
+  if (want_table > h.table_cap) {
+    device_release(h, h.tkey);
+    device_release(h, h.tacc);
+    device_release(h, h.tund);
+    if ((st = alloc_n(h, &h.tkey, want_table)) || (st = alloc_n(h, &h.tacc, want_table)) ||
+        (st = alloc_n(h, &h.tund, want_table))) {
+      h.table_cap = 0;
+      return st;
+    }
+    h.table_cap = want_table;
+  }
+  return PDG_OK;
+}
+
+// Pinned host staging of the per-recovery parameters (kept alive for
+// asynchronous copies).
+struct HostStage {
+  GraphSel* sel = nullptr;
+  int64_t* k = nullptr;
+  int64_t* out_ptr = nullptr;
+  int32_t* gstat = nullptr;
+  int64_t* gcount = nullptr;
+  int32_t G = 0;
+};
+
+}  // namespace pdg
+
+using namespace pdg;
+
+struct pdg_sparsifier {
+  Handle h;
+  HostStage stage;
+  int64_t* up_ptr = nullptr;  // lazily built for pdg_edge_endpoints
+};
+
+extern "C" {
+
+void pdg_default_options(pdg_options* opt) {
+  if (!opt) return;
+  opt->score_mode = PDG_SCORE_STRETCH;
+  opt->warp_tier_max = 32;
+  opt->k_override = -1;
+  opt->candidate_factor = 1.5;
+  opt->max_rounds = 8;
+  opt->use_graph = 0;
+  opt->spin_limit = 1ll << 26;
+  opt->profile = 0;
+  opt->reserved = 0;
+}
+
+const char* pdg_status_string(int status) {
+  switch (status) {
+    case PDG_OK: return "ok";
+    case PDG_UNDER_BUDGET: return "fewer than k edges survive one pass; all survivors returned";
+    case PDG_E_INVALID_ARG: return "invalid argument";
+    case PDG_E_NOT_SYMMETRIC: return "CSR is not symmetric (structure or weights)";
+    case PDG_E_NOT_A_TREE: return "parent[] is not a spanning tree of the graph";
+    case PDG_E_BAD_WEIGHT: return "edge weight not finite or outside [2^-900, 2^900]";
+    case PDG_E_RANGE: return "exact root distances would overflow the 96-bit fixed point";
+    case PDG_E_CAPACITY: return "output capacity too small";
+    case PDG_E_OOM: return "device allocation failed";
+    case PDG_E_CUDA: return "CUDA runtime error";
+    case PDG_E_TIMEOUT: return "bounded device wait timed out";
+    case PDG_E_NOT_CSR: return "malformed CSR (row_ptr, range, self loop, order or duplicates)";
+    default: return "unknown status";
+  }
+}
+
+void sparsifier_free(pdg_handle hp) {
+  if (!hp) return;
+  Handle& h = hp->h;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h.device);
+  if (h.stream) cudaStreamSynchronize(h.stream);
+  for (void* p : h.allocs) cudaFree(p);
+  h.allocs.clear();
+  for (cudaEvent_t e : h.ev)
+    if (e) cudaEventDestroy(e);
+  if (h.hsc) cudaFreeHost(h.hsc);
+  HostStage& s = hp->stage;
+  if (s.sel) cudaFreeHost(s.sel);
+  if (s.k) cudaFreeHost(s.k);
+  if (s.out_ptr) cudaFreeHost(s.out_ptr);
+  if (s.gstat) cudaFreeHost(s.gstat);
+  if (s.gcount) cudaFreeHost(s.gcount);
+  cudaSetDevice(prev);
+  delete hp;
+}
+
+int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_ptr, const int64_t* row_ptr,
+                        const int32_t* col, const double* w, const int32_t* parent, int mem_kind,
+                        const pdg_options* opt, void* stream) {
+  if (!out) return PDG_E_INVALID_ARG;
+  *out = nullptr;
+  if (num_graphs < 1 || !vtx_ptr || !row_ptr || !parent || (mem_kind != PDG_MEM_HOST && mem_kind != PDG_MEM_DEVICE))
+    return PDG_E_INVALID_ARG;
+  if (vtx_ptr[0] != 0) return PDG_E_INVALID_ARG;
+  for (int32_t g = 0; g < num_graphs; g++)
+    if (vtx_ptr[g + 1] <= vtx_ptr[g]) return PDG_E_INVALID_ARG;
+  const int64_t n = vtx_ptr[num_graphs];
+  if (n < 1 || n >= (1ll << 30)) return PDG_E_INVALID_ARG;
+  pdg_sparsifier* hp = new (std::nothrow) pdg_sparsifier();
+  if (!hp) return PDG_E_OOM;
+  Handle& h = hp->h;
+  if (opt) h.opt = *opt; else pdg_default_options(&h.opt);
+  if (h.opt.warp_tier_max < 1 || h.opt.warp_tier_max > 32) h.opt.warp_tier_max = 32;
+  if (!(h.opt.candidate_factor >= 1.0)) h.opt.candidate_factor = 1.5;
+  if (h.opt.max_rounds < 1) h.opt.max_rounds = 1;
+  if (h.opt.max_rounds > 64) h.opt.max_rounds = 64;
+  cudaGetDevice(&h.device);
+  cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, h.device);
+  h.stream = (cudaStream_t)stream;
+  h.G = num_graphs;
+  h.n = n;
+  h.vtx_ptr_h.assign(vtx_ptr, vtx_ptr + num_graphs + 1);
+  int st = PDG_OK;
+  auto fail = [&](int code) {
+    sparsifier_free(hp);
+    return code;
+  };
+  const cudaMemcpyKind kind = (mem_kind == PDG_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  // nnz
+  int64_t ends[2];
+  if (mem_kind == PDG_MEM_HOST) {
+    ends[0] = row_ptr[0];
+    ends[1] = row_ptr[n];
+  } else {
+    if (cudaMemcpy(&ends[0], row_ptr, 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&ends[1], row_ptr + n, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(PDG_E_CUDA);
+  }
+  if (ends[0] != 0 || ends[1] < 0) return fail(PDG_E_NOT_CSR);
+  h.nnz = ends[1];
+  if (h.nnz > 0 && (!col || !w)) return fail(PDG_E_INVALID_ARG);
+  if (h.nnz % 2) return fail(PDG_E_NOT_SYMMETRIC);
+  h.m = h.nnz / 2;
+  if (h.m >= (1ll << 31)) return fail(PDG_E_INVALID_ARG);
+  if (cudaMallocHost(&h.hsc, sizeof(DevScalars)) != cudaSuccess) return fail(PDG_E_OOM);
+  if ((st = alloc_n(h, &h.dsc, 1))) return fail(st);
+  if ((st = alloc_n(h, &h.row_ptr, n + 1)) || (st = alloc_n(h, &h.col, h.nnz)) || (st = alloc_n(h, &h.w, h.nnz)) ||
+      (st = alloc_n(h, &h.parent, n)) || (st = alloc_n(h, &h.d_vtx_ptr, num_graphs + 1)) ||
+      (st = alloc_n(h, &h.blk_a, 10240)) || (st = alloc_n(h, &h.blk_b, 2048)))
+    return fail(st);
+  if (cudaMemcpyAsync(h.row_ptr, row_ptr, sizeof(int64_t) * (n + 1), kind, h.stream) != cudaSuccess ||
+      (h.nnz && cudaMemcpyAsync(h.col, col, sizeof(int32_t) * h.nnz, kind, h.stream) != cudaSuccess) ||
+      (h.nnz && cudaMemcpyAsync(h.w, w, sizeof(double) * h.nnz, kind, h.stream) != cudaSuccess) ||
+      cudaMemcpyAsync(h.parent, parent, sizeof(int32_t) * n, kind, h.stream) != cudaSuccess ||
+      cudaMemcpyAsync(h.d_vtx_ptr, vtx_ptr, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice, h.stream) !=
+          cudaSuccess)
+    return fail(PDG_E_CUDA);
+  h.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (h.nnz + kTile - 1) / kTile));
+  if ((st = validate_graph(h))) return fail(st);
+  // per-graph edge counts from the row offsets at the graph boundaries
+  std::vector<int64_t> rp_at(num_graphs + 1);
+  {
+    int64_t* tmp = nullptr;
+    if ((st = alloc_n(h, &tmp, num_graphs + 1))) return fail(st);
+    k_gather_rowptr<<<(num_graphs + 256) / 256, 256, 0, h.stream>>>(h.row_ptr, h.d_vtx_ptr, num_graphs, tmp);
+    if (cudaMemcpyAsync(rp_at.data(), tmp, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyDeviceToHost, h.stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h.stream) != cudaSuccess)
+      return fail(PDG_E_CUDA);
+    device_release(h, tmp);
+  }
+  h.edge_ptr_h.assign(num_graphs + 1, 0);
+  h.off_ptr_h.assign(num_graphs + 1, 0);
+  for (int32_t g = 0; g < num_graphs; g++) {
+    const int64_t entries = rp_at[g + 1] - rp_at[g];
+    if (entries % 2) return fail(PDG_E_NOT_SYMMETRIC);
+    const int64_t mg = entries / 2, ng = vtx_ptr[g + 1] - vtx_ptr[g];
+    if (mg < ng - 1) return fail(PDG_E_NOT_A_TREE);
+    h.edge_ptr_h[g + 1] = h.edge_ptr_h[g] + mg;
+    h.off_ptr_h[g + 1] = h.off_ptr_h[g] + (mg - ng + 1);
+  }
+  h.E_off = h.off_ptr_h[num_graphs];
+  h.J = 0;
+  while ((1ll << h.J) <= h.max_depth) h.J++;
+  // workspace
+  const int64_t E = std::max<int64_t>(h.E_off, 1);
+  if ((st = alloc_n(h, &h.d_edge_ptr, num_graphs + 1)) || (st = alloc_n(h, &h.d_off_ptr, num_graphs + 1)) ||
+      (st = alloc_n(h, &h.off_u, E)) || (st = alloc_n(h, &h.off_v, E)) || (st = alloc_n(h, &h.off_id, E)) ||
+      (st = alloc_n(h, &h.off_w, E)) || (st = alloc_n(h, &h.rtree, n)) || (st = alloc_n(h, &h.P[0], n)) ||
+      (st = alloc_n(h, &h.P[1], n)) || (st = alloc_n(h, &h.up, (int64_t)std::max(h.J - 1, 1) * n)) ||
+      (st = alloc_n(h, &h.key, E)) || (st = alloc_n(h, &h.lca, E)) ||
+      (st = alloc_n(h, &h.hist, (int64_t)num_graphs * kSelBins)) || (st = alloc_n(h, &h.sel, num_graphs)) ||
+      (st = alloc_n(h, &h.d_cand_ptr, num_graphs + 1)) || (st = alloc_n(h, &h.d_graph_tmp, num_graphs + 1)) ||
+      (st = alloc_n(h, &h.gstat, num_graphs)) || (st = alloc_n(h, &h.gcount, num_graphs)) ||
+      (st = alloc_n(h, &h.d_k, num_graphs)) || (st = alloc_n(h, &h.d_out_ptr, num_graphs + 1)) ||
+      (st = alloc_n(h, &h.radix_dtot, 256)))
+    return fail(st);
+  HostStage& s = hp->stage;
+  s.G = num_graphs;
+  if (cudaMallocHost(&s.sel, sizeof(GraphSel) * num_graphs) != cudaSuccess ||
+      cudaMallocHost(&s.k, sizeof(int64_t) * num_graphs) != cudaSuccess ||
+      cudaMallocHost(&s.out_ptr, sizeof(int64_t) * (num_graphs + 1)) != cudaSuccess ||
+      cudaMallocHost(&s.gstat, sizeof(int32_t) * num_graphs) != cudaSuccess ||
+      cudaMallocHost(&s.gcount, sizeof(int64_t) * num_graphs) != cudaSuccess)
+    return fail(PDG_E_OOM);
+  if (cudaMemcpyAsync(h.d_edge_ptr, h.edge_ptr_h.data(), sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice,
+                      h.stream) != cudaSuccess ||
+      cudaMemcpyAsync(h.d_off_ptr, h.off_ptr_h.data(), sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice,
+                      h.stream) != cudaSuccess ||
+      cudaMemsetAsync(h.hist, 0, sizeof(uint32_t) * (size_t)num_graphs * kSelBins, h.stream) != cudaSuccess ||
+      cudaMemsetAsync(h.radix_dtot, 0, sizeof(uint32_t) * 256, h.stream) != cudaSuccess ||
+      cudaStreamSynchronize(h.stream) != cudaSuccess)
+    return fail(PDG_E_CUDA);
+  h.want_h.assign(num_graphs, 0);
+  *out = hp;
+  return PDG_OK;
+}
+
+int sparsify_init(pdg_handle* out, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w,
+                  const int32_t* parent, int mem_kind, const pdg_options* opt, void* stream) {
+  if (!out) return PDG_E_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n >= (1ll << 30)) return PDG_E_INVALID_ARG;
+  const int64_t vp[2] = {0, n};
+  return sparsify_batch_init(out, 1, vp, row_ptr, col, w, parent, mem_kind, opt, stream);
+}
+
+}  // extern "C"
+
+namespace pdg {
+
+// The recovery driver shared by recover_offtree and recover_offtree_batch.
+static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, const int64_t* user_out_ptr,
+                        int32_t* out_ids, double* out_scores, int out_mem_kind, int64_t* out_count,
+                        int32_t* graph_status) {
+  Handle& h = hp->h;
+  HostStage& s = hp->stage;
+  const int32_t G = h.G;
+  if (c < 0 || c > PDG_MAX_C || (out_mem_kind != PDG_MEM_HOST && out_mem_kind != PDG_MEM_DEVICE))
+    return PDG_E_INVALID_ARG;
+  int prev_dev = 0;
+  cudaGetDevice(&prev_dev);
+  if (prev_dev != h.device) cudaSetDevice(h.device);
+  struct Restore {
+    int d, cur;
+    ~Restore() {
+      if (d != cur) cudaSetDevice(d);
+    }
+  } restore{prev_dev, h.device};
+  // budgets and initial prefix sizes
+  std::vector<int64_t> kg(G), eoff(G);
+  int64_t total_k = 0;
+  for (int32_t g = 0; g < G; g++) {
+    const int64_t ng = h.vtx_ptr_h[g + 1] - h.vtx_ptr_h[g];
+    eoff[g] = h.off_ptr_h[g + 1] - h.off_ptr_h[g];
+    int64_t k;
+    if (h.opt.k_override >= 0) {
+      k = h.opt.k_override;
+    } else {
+      const double a = alpha[g];
+      if (!(a >= 0.0) || !std::isfinite(a)) return PDG_E_INVALID_ARG;
+      const double kd = std::floor(a * (double)ng);
+      k = (kd >= 9.0e18) ? INT64_MAX / 4 : (int64_t)kd;
+    }
+    kg[g] = k;
+    const int64_t take = std::min(k, eoff[g]);
+    if (user_out_ptr[g + 1] - user_out_ptr[g] < take) return PDG_E_CAPACITY;
+    total_k += take;
+    int64_t want = (int64_t)std::ceil((double)k * h.opt.candidate_factor) + 32;
+    if (want < k) want = k;
+    h.want_h[g] = std::min(want, eoff[g]);
+    s.k[g] = k;
+    s.out_ptr[g] = user_out_ptr[g];
+  }
+  s.out_ptr[G] = user_out_ptr[G];
+  const int64_t out_total = user_out_ptr[G];
+  // output staging (device) when the caller's buffers are host memory
+  int32_t* dev_ids = out_ids;
+  double* dev_scores = out_scores;
+  int st;
+  if (out_mem_kind == PDG_MEM_HOST) {
+    if (out_total > h.out_cap) {
+      device_release(h, h.out_ids);
+      device_release(h, h.out_scores);
+      h.out_ids = nullptr;
+      h.out_scores = nullptr;
+      h.out_cap = 0;
+      if ((st = alloc_n(h, &h.out_ids, out_total)) || (st = alloc_n(h, &h.out_scores, out_total))) return st;
+      h.out_cap = out_total;
+    }
+    dev_ids = h.out_ids;
+    dev_scores = out_scores ? h.out_scores : nullptr;
+  }
+  PDG_CUDA(cudaMemcpyAsync(h.d_k, s.k, sizeof(int64_t) * G, cudaMemcpyHostToDevice, h.stream));
+  PDG_CUDA(cudaMemcpyAsync(h.d_out_ptr, s.out_ptr, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, h.stream));
+  const bool prof = h.opt.profile != 0;
+  if (prof && !h.ev[0])
+    for (cudaEvent_t& e : h.ev) PDG_CUDA(cudaEventCreate(&e));
+  auto mark = [&](int i) { if (prof) cudaEventRecord(h.ev[i], h.stream); };
+  float acc_ms[8] = {0};
+  // steps A1-A3 (independent of the prefix)
+  mark(0);
+  k_reset_recover<<<1, 1, 0, h.stream>>>(h.dsc);
+  if ((st = step_classify(h))) return st;
+  mark(1);
+  if ((st = step_tree(h))) return st;
+  mark(2);
+  if ((st = step_score(h, h.opt.score_mode))) return st;
+  mark(3);
+  int attempts = 0, retries = 0;
+  for (;;) {
+    if (++attempts > 40) return PDG_E_CUDA;
+    int64_t need = 0;
+    for (int32_t g = 0; g < G; g++) {
+      GraphSel& gs = s.sel[g];
+      std::memset(&gs, 0, sizeof(gs));
+      gs.want = h.want_h[g];
+      gs.take_all = (h.want_h[g] >= eoff[g]) ? 1 : 0;
+      need += gs.take_all ? eoff[g] : h.want_h[g];
+    }
+    if ((st = ensure_candidates(h, std::max<int64_t>(h.Rcap, need + need / 4 + 4096), c))) return st;
+    k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
+    PDG_CUDA(cudaMemcpyAsync(h.sel, s.sel, sizeof(GraphSel) * G, cudaMemcpyHostToDevice, h.stream));
+    mark(4);
+    if ((st = step_select(h))) return st;
+    mark(5);
+    if ((st = step_sort(h))) return st;
+    mark(6);
+    if ((st = step_accept(h, c))) return st;
+    mark(7);
+    if ((st = step_budget(h, dev_ids, dev_scores))) return st;
+    mark(8);
+    PDG_CUDA(cudaMemcpyAsync(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h.stream));
+    PDG_CUDA(cudaMemcpyAsync(s.gstat, h.gstat, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, h.stream));
+    PDG_CUDA(cudaMemcpyAsync(s.gcount, h.gcount, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, h.stream));
+    PDG_CUDA(cudaStreamSynchronize(h.stream));
+    if (prof) {
+      float t;
+      for (int i = 0; i < 4; i++) {
+        cudaEventElapsedTime(&t, h.ev[4 + i], h.ev[5 + i]);
+        acc_ms[3 + i] += t;
+      }
+    }
+    const int err = h.hsc->err;
+    if (err & ERR_RANGE) return PDG_E_RANGE;
+    if (err & ERR_TIMEOUT) return PDG_E_TIMEOUT;
+    if (err & ERR_CAPACITY) {
+      if (h.hsc->n_cand <= h.Rcap) return PDG_E_CUDA;  // inconsistent selection
+      if ((st = ensure_candidates(h, h.hsc->n_cand + h.hsc->n_cand / 8 + 4096, c))) return st;
+      continue;
+    }
+    if (err & ERR_TABLE) {
+      const int64_t want_table = std::max<int64_t>(2 * h.table_cap, 2 * h.hsc->big_regs + 1024);
+      device_release(h, h.tkey);
+      device_release(h, h.tacc);
+      device_release(h, h.tund);
+      if ((st = alloc_n(h, &h.tkey, want_table)) || (st = alloc_n(h, &h.tacc, want_table)) ||
+          (st = alloc_n(h, &h.tund, want_table))) {
+        h.table_cap = 0;
+        return st;
+      }
+      h.table_cap = want_table;
+      continue;
+    }
+    if (err) return PDG_E_CUDA;
+    bool again = false;
+    for (int32_t g = 0; g < G; g++)
+      if (s.gstat[g] == G_RETRY) {
+        h.want_h[g] = std::min(eoff[g], std::max<int64_t>(h.want_h[g] * 4, 64));
+        again = true;
+      }
+    if (!again) break;
+    retries++;
+  }
+  if (prof) {
+    mark(9);
+    PDG_CUDA(cudaStreamSynchronize(h.stream));
+    for (int i = 0; i < 3; i++) cudaEventElapsedTime(&acc_ms[i], h.ev[i], h.ev[i + 1]);
+    cudaEventElapsedTime(&acc_ms[7], h.ev[0], h.ev[9]);
+    for (int i = 0; i < 8; i++) h.timings[i] = acc_ms[i];
+  }
+  // statistics of the last attempt
+  h.stats[0] = h.hsc->n_cand;
+  h.stats[1] = h.hsc->n_seg;
+  h.stats[2] = h.hsc->max_seg;
+  h.stats[3] = h.hsc->n_cand - h.hsc->n_big;
+  h.stats[4] = h.hsc->n_big;
+  h.stats[5] = h.hsc->rounds_used;
+  h.stats[6] = retries;
+  h.stats[7] = attempts;
+  int result = PDG_OK;
+  for (int32_t g = 0; g < G; g++) {
+    out_count[g] = s.gcount[g];
+    const int gst = (s.gstat[g] == G_UNDER) ? PDG_UNDER_BUDGET : PDG_OK;
+    if (graph_status) graph_status[g] = gst;
+    if (gst == PDG_UNDER_BUDGET) result = PDG_UNDER_BUDGET;
+  }
+  if (out_mem_kind == PDG_MEM_HOST) {
+    const int64_t copy = (G == 1) ? out_count[0] : out_total;
+    if (copy > 0) {
+      PDG_CUDA(cudaMemcpyAsync(out_ids, h.out_ids, sizeof(int32_t) * copy, cudaMemcpyDeviceToHost, h.stream));
+      if (out_scores)
+        PDG_CUDA(cudaMemcpyAsync(out_scores, h.out_scores, sizeof(double) * copy, cudaMemcpyDeviceToHost, h.stream));
+    }
+    PDG_CUDA(cudaStreamSynchronize(h.stream));
+  }
+  return result;
+}
+
+}  // namespace pdg
+
+extern "C" {
+
+int recover_offtree(pdg_handle hp, double alpha, int32_t c, int32_t* out_edge_ids, int64_t out_capacity,
+                    int64_t* out_count, double* out_scores, int out_mem_kind) {
+  if (!hp || !out_count || out_capacity < 0 || (out_capacity > 0 && !out_edge_ids)) return PDG_E_INVALID_ARG;
+  if (hp->h.G != 1) return PDG_E_INVALID_ARG;
+  *out_count = 0;
+  const int64_t op[2] = {0, out_capacity};
+  return run_recovery(hp, &alpha, c, op, out_edge_ids, out_scores, out_mem_kind, out_count, nullptr);
+}
+
+int recover_offtree_batch(pdg_handle hp, const double* alpha, int32_t c, const int64_t* out_ptr, int32_t* out_edge_ids,
+                          int64_t* out_count, double* out_scores, int32_t* graph_status, int out_mem_kind) {
+  if (!hp || !alpha || !out_ptr || !out_count) return PDG_E_INVALID_ARG;
+  const int32_t G = hp->h.G;
+  if (out_ptr[0] != 0) return PDG_E_INVALID_ARG;
+  for (int32_t g = 0; g < G; g++)
+    if (out_ptr[g + 1] < out_ptr[g]) return PDG_E_INVALID_ARG;
+  if (out_ptr[G] > 0 && !out_edge_ids) return PDG_E_INVALID_ARG;
+  for (int32_t g = 0; g < G; g++) out_count[g] = 0;
+  return run_recovery(hp, alpha, c, out_ptr, out_edge_ids, out_scores, out_mem_kind, out_count, graph_status);
+}
+
+int pdg_handle_info(pdg_handle hp, int64_t* n, int64_t* m, int64_t* n_offtree, int32_t* num_graphs,
+                    int64_t* max_depth, int64_t* device_bytes) {
+  if (!hp) return PDG_E_INVALID_ARG;
+  Handle& h = hp->h;
+  if (n) *n = h.n;
+  if (m) *m = h.m;
+  if (n_offtree) *n_offtree = h.E_off;
+  if (num_graphs) *num_graphs = h.G;
+  if (max_depth) *max_depth = h.max_depth;
+  if (device_bytes) *device_bytes = (int64_t)h.device_bytes;
+  return PDG_OK;
+}
+
+int pdg_last_timings(pdg_handle hp, float* ms) {
+  if (!hp || !ms) return PDG_E_INVALID_ARG;
+  for (int i = 0; i < 8; i++) ms[i] = hp->h.timings[i];
+  return PDG_OK;
+}
+
+int pdg_last_stats(pdg_handle hp, int64_t* stats) {
+  if (!hp || !stats) return PDG_E_INVALID_ARG;
+  for (int i = 0; i < 8; i++) stats[i] = hp->h.stats[i];
+  return PDG_OK;
+}
+
+int pdg_edge_endpoints(pdg_handle hp, const int32_t* ids, int64_t count, int32_t* u, int32_t* v, int mem_kind) {
+  if (!hp || count < 0 || (count > 0 && (!ids || !u || !v)) || (mem_kind != PDG_MEM_HOST && mem_kind != PDG_MEM_DEVICE))
+    return PDG_E_INVALID_ARG;
+  if (count == 0) return PDG_OK;
+  Handle& h = hp->h;
+  int st;
+  if (!hp->up_ptr) {
+    int64_t* cnt = nullptr;
+    if ((st = alloc_n(h, &cnt, h.n)) || (st = alloc_n(h, &hp->up_ptr, h.n + 1))) return st;
+    k_upper_count<<<grid_for(h, h.n), kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.n, cnt);
+    if ((st = scan_excl_i64(h, cnt, hp->up_ptr, h.n, nullptr, h.n))) return st;
+    PDG_CUDA(cudaStreamSynchronize(h.stream));
+    device_release(h, cnt);
+  }
+  const int32_t* d_ids = ids;
+  int32_t* d_u = u;
+  int32_t* d_v = v;
+  int32_t* tmp = nullptr;
+  if (mem_kind == PDG_MEM_HOST) {
+    if ((st = alloc_n(h, &tmp, 3 * count))) return st;
+    PDG_CUDA(cudaMemcpyAsync(tmp, ids, sizeof(int32_t) * count, cudaMemcpyHostToDevice, h.stream));
+    d_ids = tmp;
+    d_u = tmp + count;
+    d_v = tmp + 2 * count;
+  }
+  k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
+  k_endpoints<<<grid_for(h, count), kBlock, 0, h.stream>>>(hp->up_ptr, h.row_ptr, h.col, h.n, h.m, d_ids, count, d_u,
+                                                           d_v, h.dsc);
+  if (mem_kind == PDG_MEM_HOST) {
+    PDG_CUDA(cudaMemcpyAsync(u, d_u, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, h.stream));
+    PDG_CUDA(cudaMemcpyAsync(v, d_v, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, h.stream));
+  }
+  PDG_CUDA(cudaMemcpyAsync(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h.stream));
+  PDG_CUDA(cudaStreamSynchronize(h.stream));
+  if (tmp) device_release(h, tmp);
+  return (h.hsc->err & ERR_CAPACITY) ? PDG_E_INVALID_ARG : PDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+// Internal declarations of the GB300 off-tree edge-recovery library.
+// Kernels live in one .cu file per step of Algorithm 1; this header carries
+// the device helpers they share and the handle layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "pdgrass.h"
+
+namespace pdg {
+
+typedef unsigned __int128 u128;
+
+constexpr int kBlock = 256;         // threads per block for streaming kernels
+constexpr int kItems = 8;           // items per thread in blocked tiles
+constexpr int kTile = kBlock * kItems;
+constexpr int kSelBins = 4096;      // 12-bit digits of the candidate selection
+constexpr uint64_t kEmptyKey = ~0ull;
+
+// error bits raised by validation kernels (mapped to a status on the host)
+enum : int {
+  ERR_NOT_CSR = 1,
+  ERR_BAD_WEIGHT = 2,
+  ERR_NOT_SYMMETRIC = 4,
+  ERR_NOT_A_TREE = 8,
+  ERR_CROSS_GRAPH = 16,
+  ERR_RANGE = 32,
+  ERR_TIMEOUT = 64,
+  ERR_CAPACITY = 128,
+  ERR_TABLE = 256,
+};
+
+// candidate state in the cooperative tier
+enum : uint8_t { ST_UNDECIDED = 0, ST_ACCEPTED = 1, ST_REJECTED = 2, ST_ACCEPTED_NEW = 3 };
+
+// per-graph outcome of the budget cut
+enum : int32_t { G_OK = 0, G_UNDER = 1, G_RETRY = 2 };
+
+// Scalars that kernels produce and the host reads back in one copy.
+struct DevScalars {
+  int32_t err;          // ERR_* bits
+  int32_t e_min;        // min / max binary exponent of r = 1/w over tree edges
+  int32_t e_max;
+  int32_t rounds_used;  // cooperative-tier rounds
+  int64_t n_cand;       // candidates selected (all graphs)
+  int64_t n_seg;        // subtasks among the candidates
+  int64_t n_warp_seg;   // subtasks handled by the warp tier
+  int64_t n_big;        // candidates in the cooperative tier
+  int64_t n_big_seg;    // subtasks in the cooperative tier
+  int64_t max_seg;      // largest subtask
+  int64_t big_regs;     // registrations the cooperative tier will make
+  int64_t undecided;    // cooperative tier: still undecided after a round
+  int64_t active;       // validation: vertices whose pointer jump is not done
+  int64_t max_depth;
+  int32_t radix_sel;    // radix sort: which ping-pong buffer holds the keys
+  int32_t radix_skip;   // radix sort: the current digit is uniform
+  int64_t radix_len;    // radix sort: histogram length (256 * tiles)
+  int64_t n_warp_cand;  // candidates in the warp tier
+  int64_t pad[2];
+};
+
+// Per-graph selection state (candidate prefix of the global order).
+struct GraphSel {
+  int64_t want;     // requested prefix size R0_g
+  int64_t above1;   // edges strictly above the level-1 bucket
+  int64_t above2;   // edges of the level-1 bucket strictly above the level-2 bucket
+  int64_t count;    // selected candidates
+  uint64_t thresh;  // selected = key >= thresh
+  int32_t b1, b2;
+  int32_t take_all;
+  int32_t pad;
+};
+
+struct Handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pdg_options opt;
+  int num_sms = 0;
+
+  // sizes
+  int64_t n = 0, nnz = 0, m = 0, E_off = 0, max_depth = 0;
+  int32_t G = 1;
+  int J = 0;  // pointer-jumping rounds = bit length of the max depth
+  std::vector<int64_t> vtx_ptr_h, edge_ptr_h, off_ptr_h;  // G+1 each
+
+  // resident graph
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* w = nullptr;
+  int32_t* parent = nullptr;
+  int64_t* d_vtx_ptr = nullptr;
+  int64_t* d_edge_ptr = nullptr;
+  int64_t* d_off_ptr = nullptr;
+
+  // step 1 outputs
+  int32_t* off_u = nullptr;
+  int32_t* off_v = nullptr;
+  int32_t* off_id = nullptr;
+  double* off_w = nullptr;
+  double* rtree = nullptr;  // r(v) = fl(1/w(v, parent v))
+  int64_t* blk_a = nullptr; // per-block counters (classification, scans)
+  int64_t* blk_b = nullptr;
+  int nblk = 0;
+
+  // tree: P(v) = D(v) * 2^32 + depth(v); D = exact root distance in units of 2^-S
+  u128* P[2] = {nullptr, nullptr};
+  int32_t* up = nullptr;  // levels 1..J-1 (level 0 is parent)
+  int p_final = 0;
+
+  // scores
+  uint64_t* key = nullptr;  // FP64 score bits (positive -> order preserving)
+  int32_t* lca = nullptr;
+
+  // selection
+  uint32_t* hist = nullptr;  // G * kSelBins
+  GraphSel* sel = nullptr;   // G
+  std::vector<int64_t> want_h;  // requested prefix per graph
+  int64_t* d_cand_ptr = nullptr;  // G+1
+  int64_t* d_graph_tmp = nullptr;  // G+1 scratch
+
+  // candidate buffers (grow-only, capacity Rcap)
+  int64_t Rcap = 0;
+  int32_t* cand_idx = nullptr;     // off-tree index of each candidate (id order within graph)
+  uint64_t* rk[2] = {nullptr, nullptr};  // radix keys ping-pong
+  int32_t* rv[2] = {nullptr, nullptr};   // radix values ping-pong
+  int32_t* rank_cand = nullptr;    // rank -> candidate index
+  int32_t* lsort_rank = nullptr;   // position in (lca, rank) order -> rank
+  int64_t* scan_tmp = nullptr;     // Rcap + 1
+  int32_t* flags = nullptr;        // Rcap + 1
+  uint32_t* radix_hist = nullptr;  // 256 * tiles
+  int64_t* radix_off = nullptr;    // 256 * tiles + 1
+  uint32_t* radix_dtot = nullptr;  // 256
+  // records in (lca, rank) order
+  int32_t* rec_u = nullptr;
+  int32_t* rec_v = nullptr;
+  int32_t* rec_anc = nullptr;  // 2 * PDG_MAX_C arrays of Rcap
+  int32_t* rec_du = nullptr;
+  int32_t* rec_dv = nullptr;
+  int32_t* rec_rank = nullptr;
+  int32_t* rec_lca = nullptr;
+  uint8_t* rec_b = nullptr;
+  uint8_t* state = nullptr;      // cooperative tier state per position
+  uint8_t* acc_flag = nullptr;   // accepted, by rank
+  int32_t* seg_begin = nullptr;  // Rcap + 1
+  int32_t* warp_seg = nullptr;   // subtasks of the warp tier
+  int32_t* big_pos = nullptr;    // positions of the cooperative tier
+  int32_t* big_seg = nullptr;    // subtasks of the cooperative tier
+  // hash table of the cooperative tier
+  int64_t table_cap = 0;
+  uint64_t* tkey = nullptr;
+  uint32_t* tacc = nullptr;
+  uint64_t* tund = nullptr;
+
+  // budget
+  int32_t* gstat = nullptr;      // G
+  int64_t* gcount = nullptr;     // G
+  int64_t* d_k = nullptr;        // G
+  int64_t* d_out_ptr = nullptr;  // G+1
+  int32_t* out_ids = nullptr;    // library-owned output staging
+  double* out_scores = nullptr;
+  int64_t out_cap = 0;
+
+  DevScalars* dsc = nullptr;   // device
+  DevScalars* hsc = nullptr;   // pinned host mirror
+  int64_t stats[8] = {0};
+  float timings[8] = {0};
+  cudaEvent_t ev[16] = {};
+  size_t device_bytes = 0;
+  std::vector<void*> allocs;
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ int64_t row_of(const int64_t* __restrict__ row_ptr, int64_t n, int64_t p) {
+  // largest u with row_ptr[u] <= p
+  int64_t lo = 0, hi = n;  // row_ptr[lo] <= p < row_ptr[hi] (row_ptr[n] = nnz > p)
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(row_ptr + mid) <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// index of the first entry >= x in a sorted int32 range, or end
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// graph owning position p of a contiguous partition ptr[0..G]
+__device__ __forceinline__ int32_t part_of(const int64_t* __restrict__ ptr, int32_t G, int64_t p) {
+  int32_t lo = 0, hi = G;
+  while (hi - lo > 1) {
+    int32_t mid = (lo + hi) >> 1;
+    if (ptr[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 31;
+  x *= 0x7fb5d329728ea185ull;
+  x ^= x >> 27;
+  x *= 0x81dadef4bc2dd44dull;
+  x ^= x >> 33;
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive block scan (blockDim.x == kBlock); returns the exclusive prefix,
+// *total receives the block sum.  smem must hold kBlock/32 + 1 values.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T x, T* smem, T* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T inc = warp_incl_scan(x);
+  if (lane == 31) smem[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T s = (lane < kBlock / 32) ? smem[lane] : T(0);
+    T si = warp_incl_scan(s);
+    if (lane < kBlock / 32) smem[lane] = si - s;
+    if (lane == kBlock / 32 - 1) smem[kBlock / 32] = si;
+  }
+  __syncthreads();
+  T res = smem[wid] + inc - x;
+  *total = smem[kBlock / 32];
+  __syncthreads();
+  return res;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T x, T* smem) {
+  T tot;
+  block_excl_scan(x, smem, &tot);
+  return tot;
+}
+
+// ---------------------------------------------------------------- host side
+
+int check_cuda(cudaError_t e);
+#define PDG_CUDA(call)                            \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return check_cuda(e_); \
+  } while (0)
+
+int grid_for(const Handle& h, int64_t work, int per_block = kBlock);
+
+// device-wide exclusive scan: out[i] = sum in[0..i), out[N] = total.
+// N may live on the device (n_dev != nullptr) or be given on the host.
+int scan_excl_i64(Handle& h, const int64_t* in, int64_t* out, int64_t n_host, const int64_t* n_dev, int64_t n_max);
+int scan_excl_i32(Handle& h, const int32_t* in, int64_t* out, int64_t n_host, const int64_t* n_dev, int64_t n_max);
+int scan_excl_u32(Handle& h, const uint32_t* in, int64_t* out, const int64_t* n_dev, int64_t n_max);
+int scan_excl_u8(Handle& h, const uint8_t* in, int64_t* out, const int64_t* n_dev, int64_t n_max);
+
+// steps
+int validate_graph(Handle& h);                  // sparsify_init checks + max depth
+int step_classify(Handle& h);                   // A1
+int step_tree(Handle& h);                       // A2
+int step_score(Handle& h, int score_mode);      // A3
+int step_select(Handle& h);                     // A4a: candidate prefix per graph
+int step_sort(Handle& h);                       // A4b: (graph, score desc, id asc) then (lca, rank)
+int step_accept(Handle& h, int c);              // A5 + A6
+int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7
+int ensure_candidates(Handle& h, int64_t R, int c);
+int device_alloc(Handle& h, void** p, size_t bytes);
+
+}  // namespace pdg

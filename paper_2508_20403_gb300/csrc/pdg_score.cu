@@ -1,0 +1,97 @@
+// Step A3: score every off-tree edge (Algorithm 1 step 1: LCA_query,
+// distance_query, compute_resistance).
+//
+//   l   = LCA_T(u, v) by binary lifting over the pointer-jumping table
+//   R_T = D(u) + D(v) - 2 D(l)                       (Eq. RT), exact integer
+//         then ONE round-to-nearest-even conversion to FP64
+//   score = fl(w * R_T) (STRETCH) or R_T (RESISTANCE)
+//
+// The score is positive, so its IEEE bit pattern read as an unsigned integer
+// orders like the score itself; key[i] stores those bits for the selection
+// and sort steps.
+#include "pdg_internal.cuh"
+
+namespace pdg {
+
+namespace {
+
+__device__ __forceinline__ int32_t up_level(const int32_t* __restrict__ parent, const int32_t* __restrict__ up,
+                                            int64_t n, int j, int32_t x) {
+  return j == 0 ? __ldg(parent + x) : __ldg(up + (int64_t)(j - 1) * n + x);
+}
+
+// x * 2^-S rounded to nearest, ties to even; x > 0 and the result is normal.
+__device__ __forceinline__ double fixed_to_double(u128 x, int S) {
+  const uint64_t hi = (uint64_t)(x >> 64), lo = (uint64_t)x;
+  int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  uint64_t q;
+  if (p <= 52) {
+    q = lo << (52 - p);
+  } else {
+    const int sh = p - 52;
+    q = (uint64_t)(x >> sh);
+    const u128 rem = x & ((((u128)1) << sh) - 1);
+    const u128 half = ((u128)1) << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) {
+      q++;
+      if (q == (1ull << 53)) {
+        q >>= 1;
+        p++;
+      }
+    }
+  }
+  const uint64_t bits = ((uint64_t)(p - S + 1023) << 52) | (q & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+__global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou, const int32_t* __restrict__ ov,
+                                                  const double* __restrict__ ow, const u128* __restrict__ P,
+                                                  const int32_t* __restrict__ parent,
+                                                  const int32_t* __restrict__ up, int64_t n, int64_t E,
+                                                  const DevScalars* __restrict__ dsc, int score_mode,
+                                                  uint64_t* __restrict__ key, int32_t* __restrict__ lca) {
+  const int S = 52 - dsc->e_min;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = ou[i], v = ov[i];
+    const u128 Pu = P[u], Pv = P[v];
+    int32_t a = u, b = v;
+    uint32_t da = (uint32_t)Pu, db = (uint32_t)Pv;
+    if (da < db) {
+      int32_t t = a; a = b; b = t;
+      uint32_t s = da; da = db; db = s;
+    }
+    uint32_t diff = da - db;
+    for (int j = 0; diff; j++, diff >>= 1)
+      if (diff & 1u) a = up_level(parent, up, n, j, a);
+    int32_t l = a;
+    if (a != b) {
+      for (int j = 31 - __clz((int)max(db, 1u)); j >= 0; j--) {
+        const int32_t ua = up_level(parent, up, n, j, a);
+        const int32_t ub = up_level(parent, up, n, j, b);
+        if (ua != ub) {
+          a = ua;
+          b = ub;
+        }
+      }
+      l = __ldg(parent + a);
+    }
+    const u128 Pl = P[l];
+    const u128 r_fixed = (Pu >> 32) + (Pv >> 32) - ((Pl >> 32) << 1);
+    const double R = fixed_to_double(r_fixed, S);
+    const double s = (score_mode == PDG_SCORE_RESISTANCE) ? R : __dmul_rn(ow[i], R);
+    key[i] = (uint64_t)__double_as_longlong(s);
+    lca[i] = l;
+  }
+}
+
+}  // namespace
+
+int step_score(Handle& h, int score_mode) {
+  if (h.E_off == 0) return PDG_OK;
+  k_score<<<grid_for(h, h.E_off), kBlock, 0, h.stream>>>(h.off_u, h.off_v, h.off_w, h.P[h.p_final], h.parent, h.up,
+                                                          h.n, h.E_off, h.dsc, score_mode, h.key, h.lca);
+  PDG_CUDA(cudaGetLastError());
+  return PDG_OK;
+}
+
+}  // namespace pdg

@@ -1,0 +1,224 @@
+"""Parity of the CUDA library (through the C ABI) against the CPU oracle.
+
+Recovered edge sets must be identical (ids and order); scores are compared
+bit for bit (both sides compute the exact path sum and round once), which is
+stricter than the 1e-12 relative tolerance the method allows.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2508_20403_gb300 import workloads as W
+from tests.helpers import handtree, random_small_graph
+
+pytestmark = pytest.mark.gpu
+
+SCORE_RTOL = 1e-12  # the stated tolerance; the implementation meets it exactly
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2508_20403_gb300 import binding, build
+
+    build.build()
+    binding.load()
+    return binding
+
+
+def _gpu_recover(B, g, alpha, c=2, mode=0, k_override=-1, **opt):
+    o = B.default_options(score_mode=mode, k_override=k_override, **opt)
+    with B.Sparsifier.from_graph(g, options=o) as sp:
+        st, ids, sc, k = sp.recover(alpha, c, capacity=max(1, g.m))
+        return st, np.array(ids), np.array(sc), sp.last_stats()
+
+
+def _compare(B, g, alpha, c=2, mode=0, k_override=-1, **opt):
+    st, ids, sc, stats = _gpu_recover(B, g, alpha, c, mode, k_override, **opt)
+    ost, oids, osc, _ = O.recover(g, alpha, c=c, score_mode=mode, k_override=k_override)
+    assert ids.tolist() == oids.tolist(), (g.name, alpha, c, mode, stats)
+    assert np.array_equal(sc, osc)
+    assert (st == B.PDG_UNDER_BUDGET) == (ost == O.UNDER_BUDGET)
+    return stats
+
+
+def test_handtree_golden(B):
+    g, d = handtree()
+    for key, c, mode in [("stretch_c2", 2, 0), ("stretch_c1", 1, 0), ("stretch_c0", 0, 0), ("resistance_c2", 2, 1)]:
+        st, ids, sc, _ = _gpu_recover(B, g, 0.0, c=c, mode=mode, k_override=8)
+        assert ids.tolist() == d["recovered"][key]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_small_graphs(B, seed):
+    rng = np.random.default_rng(1000 + seed)
+    for _ in range(40):
+        g = random_small_graph(rng, n_lo=2, n_hi=40, tree="mixed")
+        c = int(rng.integers(0, 4))
+        mode = int(rng.integers(0, 2))
+        k = int(rng.integers(0, g.m + 1))
+        wm = int(rng.choice([1, 2, 4, 32]))
+        _compare(B, g, 0.0, c=c, mode=mode, k_override=k, warp_tier_max=wm, candidate_factor=1.0)
+
+
+def test_scores_bit_exact_all_edges(B):
+    """All off-tree scores (via k = all edges, c = 0 so nothing is marked)."""
+    g = W.mesh3d_graph(16, seed=42)
+    st, ids, sc, _ = _gpu_recover(B, g, 0.0, c=0, k_override=g.n_offtree)
+    s = O.offtree_scores(g, c=0)
+    order = np.lexsort((s["id"], -s["score"]))
+    assert ids.tolist() == s["id"][order].tolist()
+    assert np.array_equal(sc, s["score"][order])
+    rel = np.abs(sc - s["score"][order]) / s["score"][order]
+    assert rel.max() <= SCORE_RTOL
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.05, 0.10])
+def test_grid100(B, alpha):
+    _compare(B, W.grid_graph(100), alpha)
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.10])
+def test_mesh32_wide_weights(B, alpha):
+    _compare(B, W.mesh3d_graph(32), alpha)
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.10, 0.5])
+def test_rmat_small_skewed(B, alpha):
+    g = W.rmat_graph(13, seed=77)
+    stats = _compare(B, g, alpha)
+    assert stats["max_subtask"] > 32  # exercises the cooperative tier
+
+
+@pytest.mark.parametrize("c", [0, 1, 2, 3])
+def test_rmat_all_c_full_pass(B, c):
+    """k = every off-tree edge: the whole order goes through the greedy."""
+    g = W.rmat_graph(11, seed=5)
+    _compare(B, g, 0.0, c=c, k_override=g.n_offtree, max_rounds=2)
+
+
+def test_resistance_mode_and_ties(B):
+    eu, ev = W.grid2d_edges(20, 20)
+    g = W.build_graph(400, eu, ev, np.ones(eu.shape[0]))  # every score ties
+    _compare(B, g, 0.3, c=2, mode=1)
+    _compare(B, g, 0.3, c=2, mode=0)
+
+
+def test_retry_path_small_factor(B):
+    """candidate_factor 1.0 forces prefix retries; the result must not change."""
+    g = W.grid_graph(60, seed=3)
+    stats = _compare(B, g, 0.2, candidate_factor=1.0)
+    assert stats["attempts"] >= 1
+
+
+def test_under_budget(B):
+    g = W.grid_graph(10, seed=4)
+    st, ids, sc, _ = _gpu_recover(B, g, 0.0, c=2, k_override=g.n_offtree + 5)
+    ost, oids, _, _ = O.recover(g, 0.0, c=2, k_override=g.n_offtree + 5)
+    assert st == B.PDG_UNDER_BUDGET and ost == O.UNDER_BUDGET
+    assert ids.tolist() == oids.tolist()
+
+
+def test_device_buffers_in_and_out(B):
+    import torch
+
+    g = W.grid_graph(50, seed=8)
+    sp = B.Sparsifier.from_graph(g, device=True)
+    k = int(np.floor(0.05 * g.n))
+    out = torch.zeros(k, dtype=torch.int32, device="cuda")
+    outs = torch.zeros(k, dtype=torch.float64, device="cuda")
+    st, ids, sc, cnt = sp.recover(0.05, 2, out_ids=out, out_scores=outs)
+    ost, oids, osc, _ = O.recover(g, 0.05, c=2)
+    assert ids.cpu().numpy().tolist() == oids.tolist()
+    assert np.array_equal(sc.cpu().numpy(), osc)
+    u, v = sp.endpoints(ids)
+    eu, ev, _ = g.edges()
+    assert u.cpu().numpy().tolist() == eu[oids].tolist()
+    assert v.cpu().numpy().tolist() == ev[oids].tolist()
+    sp.close()
+
+
+def test_repeated_calls_deterministic(B):
+    g = W.mesh3d_graph(20, seed=9)
+    with B.Sparsifier.from_graph(g) as sp:
+        first = sp.recover(0.1, 2)[1].copy()
+        for a in (0.02, 0.1, 0.05, 0.1):
+            st, ids, _, _ = sp.recover(a, 2)
+            if a == 0.1:
+                assert ids.tolist() == first.tolist()
+
+
+# ------------------------------------------------------------------ batches
+
+def test_batch_equals_single(B):
+    graphs = [W.batch_member(i, seed=123, n_lo=200, n_hi=3000, side_lo=5, side_hi=40) for i in range(24)]
+    pk = W.pack_graphs(graphs)
+    alphas = np.array([[0.02, 0.05, 0.10][i % 3] for i in range(len(graphs))])
+    with B.BatchSparsifier.from_packed(pk) as bs:
+        st, op, ids, sc, cnt, gst = bs.recover_batch(alphas, c=2)
+    for i, g in enumerate(graphs):
+        ost, oids, osc, _ = O.recover(g, alphas[i], c=2)
+        got = ids[op[i]:op[i] + cnt[i]]
+        assert got.tolist() == oids.tolist(), i
+        assert np.array_equal(sc[op[i]:op[i] + cnt[i]], osc)
+
+
+# ------------------------------------------------------------------ errors
+
+def _init_status(B, n, rp, col, w, par):
+    try:
+        B.Sparsifier(n, rp, col, w, par).close()
+        return B.PDG_OK
+    except B.PdgError as e:
+        return e.status
+
+
+def test_init_rejects_bad_inputs(B):
+    g, _ = handtree()
+    rp, col, w, par = g.row_ptr.copy(), g.col.copy(), g.w.copy(), g.parent.copy()
+    assert _init_status(B, g.n, rp, col, w, par) == B.PDG_OK
+    bad = par.copy(); bad[1] = 7
+    assert _init_status(B, g.n, rp, col, w, bad) == B.PDG_E_NOT_A_TREE
+    bad = par.copy(); bad[0] = 1  # no root
+    assert _init_status(B, g.n, rp, col, w, bad) == B.PDG_E_NOT_A_TREE
+    bad = par.copy(); bad[9] = 0  # (9, 0) is not an edge of G
+    assert _init_status(B, g.n, rp, col, w, bad) == B.PDG_E_NOT_A_TREE
+    bw = w.copy(); bw[0] = 3.0  # asymmetric weight
+    assert _init_status(B, g.n, rp, col, bw, par) == B.PDG_E_NOT_SYMMETRIC
+    bw = w.copy(); bw[0] = np.nan
+    assert _init_status(B, g.n, rp, col, bw, par) == B.PDG_E_BAD_WEIGHT
+    bc = col.copy(); bc[0], bc[1] = bc[1], bc[0]  # unsorted row
+    assert _init_status(B, g.n, rp, bc, w, par) == B.PDG_E_NOT_CSR
+
+
+def test_range_error(B):
+    # a path 0-1-2 with resistances 2^900 and 2^-900 cannot share one 96-bit fixed point
+    from tests.helpers import graph_from_edges
+
+    g = graph_from_edges(3, [(0, 1, 2.0 ** -900), (1, 2, 2.0 ** 900), (0, 2, 1.0)], [-1, 0, 1])
+    assert _init_status(B, g.n, g.row_ptr, g.col, g.w, g.parent) == B.PDG_E_RANGE
+
+
+def test_bad_c_and_capacity(B):
+    g = W.grid_graph(10, seed=1)
+    with B.Sparsifier.from_graph(g) as sp:
+        with pytest.raises(B.PdgError) as e:
+            sp.recover(0.1, 4)
+        assert e.value.status == B.PDG_E_INVALID_ARG
+        with pytest.raises(B.PdgError) as e:
+            sp.recover(0.5, 2, out_ids=np.zeros(3, dtype=np.int32))
+        assert e.value.status == B.PDG_E_CAPACITY
+
+
+def test_single_vertex_and_tree_only(B):
+    from tests.helpers import graph_from_edges
+
+    g = graph_from_edges(1, [], [-1])
+    with B.Sparsifier.from_graph(g) as sp:
+        st, ids, _, k = sp.recover(0.5, 2, capacity=1)
+        assert k == 0
+    g = graph_from_edges(5, [(i, i + 1, 1.0) for i in range(4)], [-1, 0, 1, 2, 3])
+    with B.Sparsifier.from_graph(g) as sp:
+        st, ids, _, k = sp.recover(0.5, 2, capacity=4)
+        assert k == 0 and st == B.PDG_UNDER_BUDGET

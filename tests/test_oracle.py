@@ -341,3 +341,36 @@ def test_oracle_rejects_non_tree():
     g2 = W.Graph(n=g.n, row_ptr=g.row_ptr, col=g.col, w=g.w, parent=bad)
     with pytest.raises(RuntimeError):
         O.recover(g2, 0.1)
+
+
+# ---------------------------------------------------------------- the two scoring methods
+
+@pytest.mark.parametrize("maker", [lambda: W.mesh3d_graph(14, seed=21), lambda: W.rmat_graph(12, seed=22),
+                                   lambda: W.grid_graph(40, seed=23)])
+def test_walk_and_dists_methods_agree(maker):
+    """Algorithm 1's route (dists + skip table) equals the path-walk definition bit for bit."""
+    g = maker()
+    for mode in (O.SCORE_STRETCH, O.SCORE_RESISTANCE):
+        a = O.offtree_scores(g, c=2, score_mode=mode, method=O.METHOD_WALK)
+        b = O.offtree_scores(g, c=2, score_mode=mode, method=O.METHOD_DISTS)
+        for key in a:
+            assert np.array_equal(a[key], b[key]), key
+
+
+def test_dists_method_wide_weights_random():
+    rng = np.random.default_rng(31)
+    for _ in range(30):
+        g = random_small_graph(rng, n_lo=3, n_hi=30, tree="mixed", weights="wide")
+        a = O.offtree_scores(g, c=3, method=O.METHOD_WALK)
+        b = O.offtree_scores(g, c=3, method=O.METHOD_DISTS)
+        for key in a:
+            assert np.array_equal(a[key], b[key]), key
+
+
+def test_prefix_restart_matches_full_pass():
+    """The prefix-bounded greedy returns the same edges as a run over the whole order."""
+    g = W.mesh3d_graph(12, seed=24)
+    for k in (5, 50, 400, 2000):
+        st, ids, _, full = O.recover(g, 0.0, c=2, k_override=k, full_count=True)
+        st2, ids2, _, _ = O.recover(g, 0.0, c=2, k_override=k)
+        assert ids.tolist() == ids2.tolist()
