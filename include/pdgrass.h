@@ -193,7 +193,8 @@ int pdg_handle_info(pdg_handle h, int64_t* n, int64_t* m, int64_t* n_offtree, in
  * pdg_last_stats -- counters of the last recovery: candidates examined (the
  * prefix of the global order that was scored into subtasks), subtasks,
  * largest subtask, candidates in the warp tier / cooperative tier, rounds of
- * the cooperative tier, prefix retries.  stats must hold 8 int64.
+ * the cooperative tier, prefix retries, attempts, kernels launched by the
+ * recovery, and three reserved zeros.  stats must hold 12 int64.
  */
 int pdg_last_stats(pdg_handle h, int64_t* stats);
 

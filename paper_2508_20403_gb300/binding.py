@@ -186,10 +186,10 @@ class Sparsifier:
                     device_bytes=db.value)
 
     def last_stats(self) -> dict:
-        a = np.zeros(8, dtype=np.int64)
+        a = np.zeros(12, dtype=np.int64)
         self._L.pdg_last_stats(self._h, a.ctypes.data)
         keys = ("candidates", "subtasks", "max_subtask", "warp_or_single", "coop_candidates", "coop_rounds",
-                "retries", "attempts")
+                "retries", "attempts", "launches")
         return dict(zip(keys, (int(x) for x in a)))
 
     def last_timings(self) -> dict:

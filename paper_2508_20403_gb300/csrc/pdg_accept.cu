@@ -430,47 +430,62 @@ int step_accept(Handle& h, int c) {
   const int64_t cap = h.Rcap;
   const int32_t* up1 = (h.J >= 2) ? h.up : nullptr;
   int st;
+  ++h.launches;
   k_build_records<<<grid, kBlock, 0, h.stream>>>(h.lsort_rank, h.rank_cand, h.cand_idx, h.off_u, h.off_v, h.lca,
                                                   h.P[h.p_final], h.parent, up1, c, h.dsc, cap, h.rec_u, h.rec_v,
                                                   h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.rec_lca);
+  ++h.launches;
   k_seg_flags<<<grid, kBlock, 0, h.stream>>>(h.rec_lca, h.dsc, h.flags);
   PDG_CUDA(cudaGetLastError());
   // segment starts -> seg_begin[0..n_seg], seg_begin[n_seg] = N
   if ((st = scan_excl_i32(h, h.flags, h.scan_tmp, 0, &h.dsc->n_cand, cap))) return st;
+  ++h.launches;
   k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(h.flags, h.scan_tmp, &h.dsc->n_cand, h.seg_begin, &h.dsc->n_seg, 1);
   // tiers per segment
   int32_t* fw = h.flags;              // reuse: n_seg <= N
   int32_t* fb = h.flags + cap + 1;    // second half of the flag buffer
+  ++h.launches;
   k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, fw, fb);
   PDG_CUDA(cudaGetLastError());
   if ((st = scan_excl_i32(h, fw, h.scan_tmp, 0, &h.dsc->n_seg, cap))) return st;
+  ++h.launches;
   k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fw, h.scan_tmp, &h.dsc->n_seg, h.warp_seg, &h.dsc->n_warp_seg, -1);
   if ((st = scan_excl_i32(h, fb, h.scan_tmp, 0, &h.dsc->n_seg, cap))) return st;
+  ++h.launches;
   k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fb, h.scan_tmp, &h.dsc->n_seg, h.big_seg, &h.dsc->n_big_seg, -1);
   // per position: singletons, cooperative-tier membership
   int32_t* fpos = h.flags;
+  ++h.launches;
   k_pos_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.rec_rank, h.rec_b, h.acc_flag,
                                             fpos, h.state);
   PDG_CUDA(cudaGetLastError());
   if ((st = scan_excl_i32(h, fpos, h.scan_tmp, 0, &h.dsc->n_cand, cap))) return st;
+  ++h.launches;
   k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fpos, h.scan_tmp, &h.dsc->n_cand, h.big_pos, &h.dsc->n_big, -1);
   // warp tier
+  ++h.launches;
   k_accept_warp<<<grid, kBlock, 0, h.stream>>>(h.warp_seg, h.dsc, h.seg_begin, c, cap, h.rec_u, h.rec_v, h.rec_anc,
                                                h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
   // cooperative tier
-  uint64_t* d_cap = reinterpret_cast<uint64_t*>(h.blk_a + 9000);
-  int64_t* und_count = h.blk_a + 9100;  // [0 .. max_rounds]
+  // blk_a[9800..9916) is reserved for this step (other steps use [0, 9729))
+  uint64_t* d_cap = reinterpret_cast<uint64_t*>(h.blk_a + 9800);
+  int64_t* und_count = h.blk_a + 9850;  // [0 .. max_rounds], max_rounds <= 64
   const int R = std::max(1, std::min(h.opt.max_rounds, 64));
   PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
+  ++h.launches;
   k_table_clear<<<grid, kBlock, 0, h.stream>>>(h.tkey, h.tacc, h.tund, h.dsc, h.table_cap, d_cap);
   BigArgs a{h.big_pos, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.state,
             h.tkey, h.tacc, h.tund, d_cap, und_count, cap, c};
   for (int r = 1; r <= R; r++) {
+    ++h.launches;
     k_big_register<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+    ++h.launches;
     k_big_probe<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
   }
+  ++h.launches;
   k_big_finish<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.big_seg, h.seg_begin, R);
+  ++h.launches;
   k_big_flags<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;

@@ -301,6 +301,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
   {
     int64_t* tmp = nullptr;
     if ((st = alloc_n(h, &tmp, num_graphs + 1))) return fail(st);
+    ++h.launches;
     k_gather_rowptr<<<(num_graphs + 256) / 256, 256, 0, h.stream>>>(h.row_ptr, h.d_vtx_ptr, num_graphs, tmp);
     if (cudaMemcpyAsync(rp_at.data(), tmp, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyDeviceToHost, h.stream) !=
             cudaSuccess ||
@@ -432,6 +433,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
   }
   PDG_CUDA(cudaMemcpyAsync(h.d_k, s.k, sizeof(int64_t) * G, cudaMemcpyHostToDevice, h.stream));
   PDG_CUDA(cudaMemcpyAsync(h.d_out_ptr, s.out_ptr, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, h.stream));
+  h.launches = 0;
   const bool prof = h.opt.profile != 0;
   if (prof && !h.ev[0])
     for (cudaEvent_t& e : h.ev) PDG_CUDA(cudaEventCreate(&e));
@@ -439,6 +441,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
   float acc_ms[8] = {0};
   // steps A1-A3 (independent of the prefix)
   mark(0);
+  ++h.launches;
   k_reset_recover<<<1, 1, 0, h.stream>>>(h.dsc);
   if ((st = step_classify(h))) return st;
   mark(1);
@@ -458,6 +461,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
       need += gs.take_all ? eoff[g] : h.want_h[g];
     }
     if ((st = ensure_candidates(h, std::max<int64_t>(h.Rcap, need + need / 4 + 4096), c))) return st;
+    ++h.launches;
     k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
     PDG_CUDA(cudaMemcpyAsync(h.sel, s.sel, sizeof(GraphSel) * G, cudaMemcpyHostToDevice, h.stream));
     mark(4);
@@ -484,8 +488,9 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
     if (err & ERR_RANGE) return PDG_E_RANGE;
     if (err & ERR_TIMEOUT) return PDG_E_TIMEOUT;
     if (err & ERR_CAPACITY) {
-      if (h.hsc->n_cand <= h.Rcap) return PDG_E_CUDA;  // inconsistent selection
-      if ((st = ensure_candidates(h, h.hsc->n_cand + h.hsc->n_cand / 8 + 4096, c))) return st;
+      const int64_t wanted = h.hsc->n_cand_wanted;
+      if (wanted <= h.Rcap) return PDG_E_CUDA;  // inconsistent selection
+      if ((st = ensure_candidates(h, wanted + wanted / 8 + 4096, c))) return st;
       continue;
     }
     if (err & ERR_TABLE) {
@@ -527,6 +532,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
   h.stats[5] = h.hsc->rounds_used;
   h.stats[6] = retries;
   h.stats[7] = attempts;
+  h.stats[8] = h.launches;
   int result = PDG_OK;
   for (int32_t g = 0; g < G; g++) {
     out_count[g] = s.gcount[g];
@@ -592,7 +598,7 @@ int pdg_last_timings(pdg_handle hp, float* ms) {
 
 int pdg_last_stats(pdg_handle hp, int64_t* stats) {
   if (!hp || !stats) return PDG_E_INVALID_ARG;
-  for (int i = 0; i < 8; i++) stats[i] = hp->h.stats[i];
+  for (int i = 0; i < 12; i++) stats[i] = hp->h.stats[i];
   return PDG_OK;
 }
 
@@ -605,6 +611,7 @@ int pdg_edge_endpoints(pdg_handle hp, const int32_t* ids, int64_t count, int32_t
   if (!hp->up_ptr) {
     int64_t* cnt = nullptr;
     if ((st = alloc_n(h, &cnt, h.n)) || (st = alloc_n(h, &hp->up_ptr, h.n + 1))) return st;
+    ++h.launches;
     k_upper_count<<<grid_for(h, h.n), kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.n, cnt);
     if ((st = scan_excl_i64(h, cnt, hp->up_ptr, h.n, nullptr, h.n))) return st;
     PDG_CUDA(cudaStreamSynchronize(h.stream));
@@ -621,7 +628,9 @@ int pdg_edge_endpoints(pdg_handle hp, const int32_t* ids, int64_t count, int32_t
     d_u = tmp + count;
     d_v = tmp + 2 * count;
   }
+  ++h.launches;
   k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
+  ++h.launches;
   k_endpoints<<<grid_for(h, count), kBlock, 0, h.stream>>>(hp->up_ptr, h.row_ptr, h.col, h.n, h.m, d_ids, count, d_u,
                                                            d_v, h.dsc);
   if (mem_kind == PDG_MEM_HOST) {

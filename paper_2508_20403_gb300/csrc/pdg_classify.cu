@@ -144,6 +144,7 @@ int step_classify(Handle& h) {
   int64_t* cnt_off = h.blk_a + 2560;
   int64_t* off_up = h.blk_a + 5120;
   int64_t* off_off = h.blk_a + 7680;
+  ++h.launches;
   k_classify<false><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.parent, h.n, h.nnz, cnt_up, cnt_off,
                                                  nullptr, nullptr, h.rtree, nullptr, nullptr, nullptr, nullptr);
   PDG_CUDA(cudaGetLastError());
@@ -151,6 +152,7 @@ int step_classify(Handle& h) {
   if (st) return st;
   st = scan_excl_i64(h, cnt_off, off_off, nb, nullptr, nb);
   if (st) return st;
+  ++h.launches;
   k_classify<true><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.parent, h.n, h.nnz, nullptr, nullptr,
                                                 off_up, off_off, nullptr, h.off_u, h.off_v, h.off_id, h.off_w);
   PDG_CUDA(cudaGetLastError());

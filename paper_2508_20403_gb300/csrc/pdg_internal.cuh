@@ -59,7 +59,8 @@ struct DevScalars {
   int32_t radix_skip;   // radix sort: the current digit is uniform
   int64_t radix_len;    // radix sort: histogram length (256 * tiles)
   int64_t n_warp_cand;  // candidates in the warp tier
-  int64_t pad[2];
+  int64_t n_cand_wanted;  // candidates the selection produced (may exceed capacity)
+  int64_t pad[1];
 };
 
 // Per-graph selection state (candidate prefix of the global order).
@@ -165,7 +166,8 @@ struct Handle {
 
   DevScalars* dsc = nullptr;   // device
   DevScalars* hsc = nullptr;   // pinned host mirror
-  int64_t stats[8] = {0};
+  int64_t stats[12] = {0};
+  int64_t launches = 0;  // kernels launched by the current recovery
   float timings[8] = {0};
   cudaEvent_t ev[16] = {};
   size_t device_bytes = 0;

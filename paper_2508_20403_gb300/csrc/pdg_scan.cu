@@ -87,8 +87,11 @@ int scan_impl(Handle& h, const T* in, int64_t* out, int64_t n_host, const int64_
   if (n_max <= 0) n_max = 1;
   int nb = (int)std::min<int64_t>(kScanBlocksMax, (n_max + kTile - 1) / kTile);
   if (nb < 1) nb = 1;
+  ++h.launches;
   k_scan_reduce<T><<<nb, kBlock, 0, h.stream>>>(in, n_host, n_dev, h.blk_b);
+  ++h.launches;
   k_scan_top<<<1, 1024, 0, h.stream>>>(h.blk_b, nb, n_host, n_dev, out);
+  ++h.launches;
   k_scan_down<T><<<nb, kBlock, 0, h.stream>>>(in, out, n_host, n_dev, h.blk_b);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;

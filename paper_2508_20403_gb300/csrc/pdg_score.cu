@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
 
 int step_score(Handle& h, int score_mode) {
   if (h.E_off == 0) return PDG_OK;
+  ++h.launches;
   k_score<<<grid_for(h, h.E_off), kBlock, 0, h.stream>>>(h.off_u, h.off_v, h.off_w, h.P[h.p_final], h.parent, h.up,
                                                           h.n, h.E_off, h.dsc, score_mode, h.key, h.lca);
   PDG_CUDA(cudaGetLastError());

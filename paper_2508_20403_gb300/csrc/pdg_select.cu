@@ -184,8 +184,14 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
 __global__ void k_sel_total(const int64_t* __restrict__ boff, int nb, const int64_t* __restrict__ cand_ptr,
                             int32_t G, int64_t cap, DevScalars* dsc) {
   const int64_t total = boff[nb];
-  dsc->n_cand = total;
-  if (total > cap || total != cand_ptr[G]) atomicOr(&dsc->err, ERR_CAPACITY);
+  dsc->n_cand_wanted = total;
+  if (total > cap || total != cand_ptr[G]) {
+    // nothing downstream may touch more than `cap` candidates: run it empty
+    dsc->n_cand = 0;
+    atomicOr(&dsc->err, ERR_CAPACITY);
+  } else {
+    dsc->n_cand = total;
+  }
 }
 
 }  // namespace
@@ -199,7 +205,11 @@ int step_select(Handle& h) {
   for (int32_t g = 0; g < h.G; g++)
     if (h.want_h[g] < h.off_ptr_h[g + 1] - h.off_ptr_h[g]) any_select = true;
   for (int lvl = 0; lvl < 2; lvl++) {
-    if (any_select) k_sel_hist<<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, lvl, h.hist);
+    if (any_select) {
+      ++h.launches;
+      k_sel_hist<<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, lvl, h.hist);
+    }
+    ++h.launches;
     k_sel_pick<<<pick_grid, warps_per_block * 32, 0, h.stream>>>(h.hist, h.sel, h.d_off_ptr, h.G, lvl, h.d_graph_tmp);
   }
   PDG_CUDA(cudaGetLastError());
@@ -207,12 +217,15 @@ int step_select(Handle& h) {
   if (st) return st;
   int64_t* bcount = h.blk_a;
   int64_t* boff = h.blk_a + 2560;
+  ++h.launches;
   k_sel_compact<false><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, nullptr, 0, nullptr,
                                                     nullptr, nullptr);
   st = scan_excl_i64(h, bcount, boff, nb, nullptr, nb);
   if (st) return st;
+  ++h.launches;
   k_sel_compact<true><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, nullptr, boff, h.Rcap,
                                                    h.cand_idx, h.rk[0], h.rv[0]);
+  ++h.launches;
   k_sel_total<<<1, 1, 0, h.stream>>>(boff, nb, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;

@@ -166,12 +166,15 @@ int scan_excl_u32(Handle& h, const uint32_t* in, int64_t* out, const int64_t* n_
 static int radix_pass_full(Handle& h, int shift) {
   const int grid = h.num_sms * 4;
   const int64_t tiles_max = (h.Rcap + kTile - 1) / kTile;
+  ++h.launches;
   k_rdx_hist<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.dsc, shift, h.radix_hist, h.radix_dtot);
   PDG_CUDA(cudaGetLastError());
   int st = scan_excl_u32(h, h.radix_hist, h.radix_off, &h.dsc->radix_len, kRdxBins * tiles_max);
   if (st) return st;
+  ++h.launches;
   k_rdx_scatter<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1],
                                                h.dsc, shift, h.radix_off, h.radix_dtot);
+  ++h.launches;
   k_rdx_flip<<<1, kRdxBins, 0, h.stream>>>(h.dsc, shift, h.rk[0], h.rk[1], h.radix_dtot);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
@@ -184,16 +187,19 @@ int step_sort(Handle& h) {
   for (int shift = 0; shift < 64; shift += 8)
     if ((st = radix_pass_full(h, shift))) return st;
   if (h.G > 1) {
+    ++h.launches;
     k_key_graph<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.d_cand_ptr, h.G, h.dsc);
     PDG_CUDA(cudaGetLastError());
     for (int shift = 0; (1ll << shift) < h.G; shift += 8)
       if ((st = radix_pass_full(h, shift))) return st;
   }
   // 2. group ranks by LCA
+  ++h.launches;
   k_key_lca<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.cand_idx, h.lca, h.rank_cand, h.dsc);
   PDG_CUDA(cudaGetLastError());
   for (int shift = 0; (1ll << shift) < h.n; shift += 8)
     if ((st = radix_pass_full(h, shift))) return st;
+  ++h.launches;
   k_copy_vals<<<grid, kBlock, 0, h.stream>>>(h.rv[0], h.rv[1], h.lsort_rank, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;

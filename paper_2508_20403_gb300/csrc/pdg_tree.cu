@@ -90,15 +90,18 @@ __global__ void __launch_bounds__(kBlock) k_tree_jump(const u128* __restrict__ P
 int step_tree(Handle& h) {
   const int64_t n = h.n;
   const int grid = grid_for(h, n);
+  ++h.launches;
   k_rexp<<<grid, kBlock, 0, h.stream>>>(h.parent, h.rtree, n, h.dsc);
   int dep_bits = 0;
   while ((1ll << dep_bits) <= h.max_depth) dep_bits++;
+  ++h.launches;
   k_tree_init<<<grid, kBlock, 0, h.stream>>>(h.parent, h.rtree, n, dep_bits, h.dsc, h.P[0]);
   PDG_CUDA(cudaGetLastError());
   int cur = 0;
   for (int j = 0; j < h.J; j++) {
     const int32_t* jin = (j == 0) ? h.parent : h.up + (int64_t)(j - 1) * n;
     int32_t* jout = (j + 1 < h.J) ? h.up + (int64_t)j * n : nullptr;
+    ++h.launches;
     k_tree_jump<<<grid, kBlock, 0, h.stream>>>(h.P[cur], h.P[cur ^ 1], jin, jout, n);
     cur ^= 1;
   }
