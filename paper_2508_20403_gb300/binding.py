@@ -124,7 +124,10 @@ def _mem_kind(arrays) -> int:
 
 def _host_arr(a, dtype):
     if _is_torch(a):
-        return a if a.dtype == dtype else a.to(dtype)
+        import torch
+
+        tdt = {np.int64: torch.int64, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        return (a if a.dtype == tdt else a.to(tdt)).contiguous()
     return np.ascontiguousarray(a, dtype=dtype)
 
 
