@@ -86,6 +86,8 @@ def load(path: Optional[str] = None):
     L.pdg_last_stats.restype = c_int
     L.pdg_last_timings.argtypes = [P, P]
     L.pdg_last_timings.restype = c_int
+    L.pdg_edge_endpoints_noalloc.argtypes = [i64, P, P, P, i64, P, P, P]
+    L.pdg_edge_endpoints_noalloc.restype = c_int
     if path is None:
         _lib = L
     return L
@@ -251,6 +253,19 @@ class Sparsifier:
 
     def __exit__(self, *a):
         self.close()
+
+
+NOALLOC_MAX_N = 1 << 21
+
+
+def edge_endpoints_noalloc(n: int, row_ptr, col, ids, u, v, stream=None) -> int:
+    """pdg_edge_endpoints_noalloc on caller-owned DEVICE tensors: maps
+    canonical edge ids to endpoints without allocating device memory (for
+    callers restricted to their own memory pool or that must not stall on
+    the allocator).  Calls on one device share the library's fixed scratch
+    array and must not overlap.  Returns the status code."""
+    return load().pdg_edge_endpoints_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(ids), int(ids.shape[0]),
+                                             _ptr(u), _ptr(v), _stream_ptr(stream))
 
 
 class BatchSparsifier(Sparsifier):
