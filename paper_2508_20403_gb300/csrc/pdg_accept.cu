@@ -19,22 +19,31 @@
 //                     as a 32-step shuffle loop -- the sequential semantics
 //                     without any shared-memory round trip;
 //   larger            the cooperative tier: all candidates of all large
-//                     subtasks at once, in rounds over an exact hash index.
+//                     subtasks at once, in two phases over hash indexes.
 //
-// Cooperative tier.  A candidate e registers keys (anc_j(u), anc_j'(v), j, j')
-// for j, j' <= beta*_e.  A candidate e' = (x, y) (both orientations) probes
-// keys (anc_i(x), anc_i'(y), j, j'): such a key can only come from an edge e
-// of the same subtask (the key determines the LCA) with
-// hops(u, l) = j + hops(x, l) - i and hops(v, l) = j' + hops(y, l) - i', so
-// the prober knows beta*_e exactly and probes only keys for which
-// i + j <= beta*_e and i' + j' <= beta*_e -- every hit is a true marker.
-// Each key slot keeps the smallest rank of an accepted registrant and the
-// smallest rank of a still-undecided registrant (tagged with the round).
-// Per round: undecided e' is REJECTED if a hit has an accepted rank below its
-// own, ACCEPTED if no hit has an undecided rank below its own, else it waits.
-// The earliest undecided candidate of every subtask always decides, so the
-// rounds converge to the sequential result; after max_rounds a serial
-// finisher (one thread per subtask, in rank order) completes the rest.
+// Cooperative tier.  Candidate e = (u, v) "registers" the ancestor pairs
+// (anc_j(u), anc_j'(v)) for j, j' <= beta*_e.  If e marks e' = (x, y), then
+// for one orientation and some i, i' <= c the pair (anc_i(x), anc_i'(y)) is
+// one of e's registered pairs, and rank(e) < rank(e').
+//   Phase A (one pass).  A pair table keeps, per pair, the smallest rank that
+//   registered it.  Each candidate probes its <= 2(c+1)^2 pairs: if none was
+//   registered by an earlier rank, no earlier edge can mark it and it is
+//   recovered ("free").  Every pair that did show an earlier registrant is
+//   flagged and given a block of exact entries, one per (j, j').
+//   Phase B (rounds over the remaining "constrained" candidates).  Exact
+//   entries keep the smallest rank of an ACCEPTED registrant and the smallest
+//   rank of a still-UNDECIDED registrant (tagged with the round).  A probe of
+//   pair (z1, z2) at (i, i') reads entry (j, j') only when the registrant
+//   would reach it: hops(u, l) = j + hops(x, l) - i and hops(v, l) =
+//   j' + hops(y, l) - i' fix beta*_e, and the entry is read iff i + j <= beta*_e
+//   and i' + j' <= beta*_e -- so every hit is a true marker.  Per round an
+//   undecided candidate is REJECTED if some hit has an accepted rank below its
+//   own, ACCEPTED if no hit has an undecided rank below its own, else it
+//   waits.  The earliest undecided candidate of every subtask always decides,
+//   so the rounds reproduce the sequential result; after max_rounds a serial
+//   finisher (one thread per subtask, in rank order) completes what is left.
+// Keys determine their subtask (they sit at or below its LCA on the two
+// sides), so one global table serves all subtasks at once.
 #include "pdg_internal.cuh"
 
 namespace pdg {
@@ -42,27 +51,36 @@ namespace pdg {
 namespace {
 
 constexpr int kA = PDG_MAX_C + 1;  // ancestors anc_0..anc_c per endpoint
+constexpr uint32_t kNone = 0xffffffffu;
 
 struct Rec {
   int32_t U[kA], V[kA];
   int32_t du, dv, b, rank;
 };
 
-__device__ __forceinline__ void load_rec(const Handle* hp, int64_t s, int c, Rec& r, const int32_t* rec_u,
-                                         const int32_t* rec_v, const int32_t* rec_anc, const int32_t* rec_du,
-                                         const int32_t* rec_dv, const uint8_t* rec_b, const int32_t* rec_rank,
-                                         int64_t cap) {
-  r.U[0] = rec_u[s];
-  r.V[0] = rec_v[s];
+struct RecArrays {
+  const int32_t* u;
+  const int32_t* v;
+  const int32_t* anc;
+  const int32_t* du;
+  const int32_t* dv;
+  const uint8_t* b;
+  const int32_t* rank;
+  int64_t cap;
+};
+
+__device__ __forceinline__ void load_rec(const RecArrays& ra, int64_t s, int c, Rec& r) {
+  r.U[0] = ra.u[s];
+  r.V[0] = ra.v[s];
 #pragma unroll
   for (int j = 1; j < kA; j++) {
-    r.U[j] = (j <= c) ? rec_anc[(int64_t)(j - 1) * cap + s] : -1;
-    r.V[j] = (j <= c) ? rec_anc[(int64_t)(c + j - 1) * cap + s] : -1;
+    r.U[j] = (j <= c) ? ra.anc[(int64_t)(j - 1) * ra.cap + s] : -1;
+    r.V[j] = (j <= c) ? ra.anc[(int64_t)(c + j - 1) * ra.cap + s] : -1;
   }
-  r.du = rec_du[s];
-  r.dv = rec_dv[s];
-  r.b = rec_b[s];
-  r.rank = rec_rank[s];
+  r.du = ra.du[s];
+  r.dv = ra.dv[s];
+  r.b = ra.b[s];
+  r.rank = ra.rank[s];
 }
 
 // hops(x', x) <= b, given anc_0..b of both (X[j] is valid for j <= b)
@@ -189,11 +207,10 @@ __global__ void k_pos_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
 
 // ------------------------------------------------------------------ warp tier
 
-__global__ void __launch_bounds__(kBlock) k_accept_warp(
-    const int32_t* __restrict__ warp_seg, const DevScalars* __restrict__ dsc, const int32_t* __restrict__ seg_begin,
-    int c, int64_t cap, const int32_t* __restrict__ rec_u, const int32_t* __restrict__ rec_v,
-    const int32_t* __restrict__ rec_anc, const int32_t* __restrict__ rec_du, const int32_t* __restrict__ rec_dv,
-    const uint8_t* __restrict__ rec_b, const int32_t* __restrict__ rec_rank, uint8_t* __restrict__ acc_flag) {
+__global__ void __launch_bounds__(kBlock) k_accept_warp(const int32_t* __restrict__ warp_seg,
+                                                        const DevScalars* __restrict__ dsc,
+                                                        const int32_t* __restrict__ seg_begin, int c, RecArrays ra,
+                                                        uint8_t* __restrict__ acc_flag) {
   const int64_t nw = dsc->n_warp_seg;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_accept_warp(
     const int32_t b0 = seg_begin[q];
     const int sz = seg_begin[q + 1] - b0;
     Rec me;
-    if (lane < sz) load_rec(nullptr, b0 + lane, c, me, rec_u, rec_v, rec_anc, rec_du, rec_dv, rec_b, rec_rank, cap);
+    if (lane < sz) load_rec(ra, b0 + lane, c, me);
     else {
 #pragma unroll
       for (int j = 0; j < kA; j++) me.U[j] = me.V[j] = -1;
@@ -232,21 +249,21 @@ __global__ void __launch_bounds__(kBlock) k_accept_warp(
 
 // ------------------------------------------------------------- cooperative tier
 
-__device__ __forceinline__ uint64_t pack_key(int32_t z1, int32_t z2, int j, int jp) {
-  return ((uint64_t)(uint32_t)z1 << 34) | ((uint64_t)(uint32_t)z2 << 4) | ((uint64_t)j << 2) | (uint64_t)jp;
+__device__ __forceinline__ uint64_t pair_key(int32_t z1, int32_t z2) {
+  return ((uint64_t)(uint32_t)z1 << 32) | (uint64_t)(uint32_t)z2;
 }
 
 __device__ __forceinline__ int64_t slot_of(uint64_t key, uint64_t cap) {
   return (int64_t)__umul64hi(mix64(key), cap);
 }
 
-__device__ int64_t table_insert(uint64_t* __restrict__ tkey, uint64_t cap, uint64_t key, DevScalars* dsc) {
+__device__ int64_t pair_insert(PairSlot* __restrict__ tab, uint64_t cap, uint64_t key, DevScalars* dsc) {
   int64_t s = slot_of(key, cap);
   for (uint64_t probe = 0; probe < cap; probe++) {
-    uint64_t k = tkey[s];
+    unsigned long long k = tab[s].key;
     if (k == key) return s;
     if (k == kEmptyKey) {
-      k = atomicCAS((unsigned long long*)&tkey[s], (unsigned long long)kEmptyKey, (unsigned long long)key);
+      k = atomicCAS(&tab[s].key, (unsigned long long)kEmptyKey, (unsigned long long)key);
       if (k == kEmptyKey || k == key) return s;
     }
     if (++s == (int64_t)cap) s = 0;
@@ -255,10 +272,10 @@ __device__ int64_t table_insert(uint64_t* __restrict__ tkey, uint64_t cap, uint6
   return -1;
 }
 
-__device__ __forceinline__ int64_t table_find(const uint64_t* __restrict__ tkey, uint64_t cap, uint64_t key) {
+__device__ __forceinline__ int64_t pair_find(const PairSlot* __restrict__ tab, uint64_t cap, uint64_t key) {
   int64_t s = slot_of(key, cap);
   for (uint64_t probe = 0; probe < cap; probe++) {
-    const uint64_t k = tkey[s];
+    const unsigned long long k = tab[s].key;
     if (k == key) return s;
     if (k == kEmptyKey) return -1;
     if (++s == (int64_t)cap) s = 0;
@@ -268,8 +285,22 @@ __device__ __forceinline__ int64_t table_find(const uint64_t* __restrict__ tkey,
 
 __device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
 
-__global__ void k_table_clear(uint64_t* __restrict__ tkey, uint32_t* __restrict__ tacc, uint64_t* __restrict__ tund,
-                              DevScalars* dsc, int64_t table_cap, uint64_t* __restrict__ cap_out) {
+struct CoopArgs {
+  RecArrays ra;
+  const int32_t* big_pos;
+  uint8_t* state;
+  uint32_t* pmask;     // per position: probe bits (o, i, i') that showed an earlier registrant
+  int32_t* reg_slot;   // per position: pair slot of each registered (j, j'), 16 per position
+  PairSlot* ptab;
+  ExactEnt* xtab;      // 16 entries (j * 4 + j') per flagged pair
+  const uint64_t* cap;  // effective pair-table capacity (device)
+  int64_t* n_flag;     // flagged pairs (exact blocks handed out)
+  int64_t xcap;        // exact blocks available
+  int64_t* und_count;  // per round: candidates still waiting
+};
+
+__global__ void k_coop_clear(PairSlot* __restrict__ tab, DevScalars* dsc, int64_t table_cap,
+                             uint64_t* __restrict__ cap_out, int64_t* __restrict__ n_flag) {
   // effective capacity: twice the registrations (load <= 0.5), at least 1024
   int64_t want = 2 * dsc->big_regs;
   if (want < 1024) want = 1024;
@@ -277,124 +308,189 @@ __global__ void k_table_clear(uint64_t* __restrict__ tkey, uint32_t* __restrict_
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&dsc->err, ERR_TABLE);
     want = table_cap;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *cap_out = (uint64_t)want;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *cap_out = (uint64_t)want;
+    *n_flag = 0;
+  }
   if (dsc->n_big == 0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < want; i += (int64_t)gridDim.x * blockDim.x) {
-    tkey[i] = kEmptyKey;
-    tacc[i] = 0xffffffffu;
-    tund[i] = ~0ull;
+  uint4* t4 = reinterpret_cast<uint4*>(tab);
+  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < want; i += (int64_t)gridDim.x * blockDim.x)
+    t4[i] = ones;
+}
+
+// Phase A1: register every (anc_j(u), anc_j'(v)), j, j' <= beta*, with its rank
+template <int C>
+__global__ void __launch_bounds__(kBlock) k_pair_register(CoopArgs a, DevScalars* dsc) {
+  const int64_t nb = dsc->n_big;
+  const uint64_t cap = *a.cap;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = a.big_pos[q];
+    Rec r;
+    load_rec(a.ra, s, C, r);
+#pragma unroll
+    for (int j = 0; j <= C; j++)
+#pragma unroll
+      for (int jp = 0; jp <= C; jp++) {
+        if (j > r.b || jp > r.b) continue;
+        const int64_t slot = pair_insert(a.ptab, cap, pair_key(r.U[j], r.V[jp]), dsc);
+        if (slot < 0) return;
+        atomicMin(&a.ptab[slot].minr, (uint32_t)r.rank);
+        a.reg_slot[(int64_t)s * 16 + j * 4 + jp] = (int32_t)slot;
+      }
   }
 }
 
-struct BigArgs {
-  const int32_t* big_pos;
-  const int32_t* rec_u;
-  const int32_t* rec_v;
-  const int32_t* rec_anc;
-  const int32_t* rec_du;
-  const int32_t* rec_dv;
-  const uint8_t* rec_b;
-  const int32_t* rec_rank;
-  uint8_t* state;
-  uint64_t* tkey;
-  uint32_t* tacc;
-  uint64_t* tund;
-  const uint64_t* cap;
-  int64_t* und_count;  // per round
-  int64_t rec_cap;
-  int c;
-};
+// Phase A2: free candidates are recovered; probed pairs with an earlier
+// registrant are flagged and get a block of exact entries
+template <int C>
+__global__ void __launch_bounds__(kBlock) k_pair_probe(CoopArgs a, DevScalars* dsc) {
+  const int64_t nb = dsc->n_big;
+  const uint64_t cap = *a.cap;
+  unsigned long long cons = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = a.big_pos[q];
+    Rec r;
+    load_rec(a.ra, s, C, r);
+    uint32_t pm = 0;
+#pragma unroll
+    for (int o = 0; o < 2; o++) {
+      const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
+#pragma unroll
+      for (int i = 0; i <= C; i++)
+#pragma unroll
+        for (int ip = 0; ip <= C; ip++) {
+          if (i > dx || ip > dy) continue;
+          const int32_t z1 = o ? r.V[i] : r.U[i];
+          const int32_t z2 = o ? r.U[ip] : r.V[ip];
+          const int64_t slot = pair_find(a.ptab, cap, pair_key(z1, z2));
+          if (slot < 0 || a.ptab[slot].minr >= (uint32_t)r.rank) continue;
+          pm |= 1u << (o * 16 + i * 4 + ip);
+          if (a.ptab[slot].xidx == kNone) {
+            const unsigned long long xi = atomicAdd((unsigned long long*)a.n_flag, 1ull);
+            if ((int64_t)xi >= a.xcap) {
+              atomicOr(&dsc->err, ERR_TABLE);
+              continue;
+            }
+            if (atomicCAS(&a.ptab[slot].xidx, kNone, (uint32_t)xi) == kNone) {
+              ExactEnt* e = a.xtab + xi * 16;
+              for (int t = 0; t < 16; t++) {
+                e[t].acc = kNone;
+                e[t].und = ~0ull;
+              }
+            }
+          }
+        }
+    }
+    a.pmask[s] = pm;
+    a.state[s] = pm ? ST_UNDECIDED : ST_ACCEPTED_NEW;
+    cons += pm ? 1 : 0;
+  }
+  for (int o = 16; o; o >>= 1) cons += __shfl_down_sync(0xffffffffu, cons, o);
+  if ((threadIdx.x & 31) == 0 && cons) atomicAdd((unsigned long long*)&dsc->n_constrained, cons);
+}
 
-__device__ __forceinline__ void register_keys(const BigArgs& a, const Rec& r, bool accepted, uint64_t und_val,
-                                              uint64_t cap, DevScalars* dsc) {
-  for (int j = 0; j <= r.b; j++)
-    for (int jp = 0; jp <= r.b; jp++) {
-      const int64_t s = table_insert(a.tkey, cap, pack_key(r.U[j], r.V[jp], j, jp), dsc);
-      if (s < 0) return;
-      if (accepted) atomicMin(&a.tacc[s], (uint32_t)r.rank);
-      else atomicMin((unsigned long long*)&a.tund[s], (unsigned long long)und_val);
+// exact registration of one candidate's flagged pairs
+template <int C>
+__device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, const Rec& r, bool accepted,
+                                               uint64_t und_val) {
+#pragma unroll
+  for (int j = 0; j <= C; j++)
+#pragma unroll
+    for (int jp = 0; jp <= C; jp++) {
+      if (j > r.b || jp > r.b) continue;
+      const int32_t slot = a.reg_slot[(int64_t)s * 16 + j * 4 + jp];
+      const uint32_t xi = a.ptab[slot].xidx;
+      if (xi == kNone) continue;
+      ExactEnt* e = a.xtab + (int64_t)xi * 16 + j * 4 + jp;
+      if (accepted) atomicMin(&e->acc, (uint32_t)r.rank);
+      else atomicMin(&e->und, (unsigned long long)und_val);
     }
 }
 
-// probe outcome: 2 = rejected, 1 = must wait, 0 = free
-template <bool WITH_UND>
-__device__ __forceinline__ int probe_all(const BigArgs& a, const Rec& r, uint64_t tag, uint64_t cap) {
+// exact probes: 2 = rejected, 1 = must wait, 0 = free of earlier markers
+template <int C, bool WITH_UND>
+__device__ __forceinline__ int exact_probe(const CoopArgs& a, const Rec& r, uint32_t pm, uint64_t cap, uint64_t tag) {
   int res = 0;
-  const int c = a.c;
+#pragma unroll
   for (int o = 0; o < 2; o++) {
-    const int32_t* X = o ? r.V : r.U;
-    const int32_t* Y = o ? r.U : r.V;
     const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
-    for (int i = 0; i <= min(c, dx); i++) {
-      const int h1 = dx - i;
-      for (int ip = 0; ip <= min(c, dy); ip++) {
-        const int h2 = dy - ip;
-        for (int j = 0; j + i <= c; j++)
-          for (int jp = 0; jp + ip <= c; jp++) {
-            const int bb = min(min(j + h1, jp + h2), c);
+#pragma unroll
+    for (int i = 0; i <= C; i++)
+#pragma unroll
+      for (int ip = 0; ip <= C; ip++) {
+        if (!(pm & (1u << (o * 16 + i * 4 + ip)))) continue;
+        const int32_t z1 = o ? r.V[i] : r.U[i];
+        const int32_t z2 = o ? r.U[ip] : r.V[ip];
+        const int64_t slot = pair_find(a.ptab, cap, pair_key(z1, z2));
+        if (slot < 0) continue;
+        const uint32_t xi = a.ptab[slot].xidx;
+        if (xi == kNone) continue;
+        const int h1 = dx - i, h2 = dy - ip;
+#pragma unroll
+        for (int j = 0; j + i <= C; j++)
+#pragma unroll
+          for (int jp = 0; jp + ip <= C; jp++) {
+            const int bb = min(min(j + h1, jp + h2), C);
             if (i + j > bb || ip + jp > bb) continue;
-            const int64_t s = table_find(a.tkey, cap, pack_key(X[i], Y[ip], j, jp));
-            if (s < 0) continue;
-            if (a.tacc[s] < (uint32_t)r.rank) return 2;
-            if (WITH_UND) {
-              const uint64_t uv = a.tund[s];
-              if ((uv & 0xffffffff00000000ull) == tag && (uint32_t)uv < (uint32_t)r.rank) res = 1;
-            }
+            const ExactEnt e = a.xtab[(int64_t)xi * 16 + j * 4 + jp];
+            if (e.acc < (uint32_t)r.rank) return 2;
+            if (WITH_UND && (e.und & 0xffffffff00000000ull) == tag && (uint32_t)e.und < (uint32_t)r.rank) res = 1;
           }
       }
-    }
   }
   return res;
 }
 
-__device__ __forceinline__ void load_big(const BigArgs& a, int64_t s, Rec& r) {
-  load_rec(nullptr, s, a.c, r, a.rec_u, a.rec_v, a.rec_anc, a.rec_du, a.rec_dv, a.rec_b, a.rec_rank, a.rec_cap);
-}
-
-__global__ void __launch_bounds__(kBlock) k_big_register(BigArgs a, DevScalars* dsc, int round) {
+template <int C>
+__global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalars* dsc, int round) {
+  if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
   const int64_t nb = dsc->n_big;
-  const uint64_t cap = *a.cap;
+  const uint64_t tag = und_tag(round);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.big_pos[q];
     const uint8_t st = a.state[s];
     if (st != ST_UNDECIDED && st != ST_ACCEPTED_NEW) continue;
     Rec r;
-    load_big(a, s, r);
+    load_rec(a.ra, s, C, r);
     if (st == ST_UNDECIDED) {
-      register_keys(a, r, false, und_tag(round) | (uint64_t)(uint32_t)r.rank, cap, dsc);
+      exact_register<C>(a, s, r, false, tag | (uint64_t)(uint32_t)r.rank);
     } else {
-      register_keys(a, r, true, 0, cap, dsc);
+      exact_register<C>(a, s, r, true, 0);
       a.state[s] = ST_ACCEPTED;
     }
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_big_probe(BigArgs a, DevScalars* dsc, int round) {
+template <int C>
+__global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* dsc, int round) {
+  if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
   const int64_t nb = dsc->n_big;
   const uint64_t cap = *a.cap;
   const uint64_t tag = und_tag(round);
-  int64_t waiting = 0;
+  unsigned long long waiting = 0;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.big_pos[q];
     if (a.state[s] != ST_UNDECIDED) continue;
     Rec r;
-    load_big(a, s, r);
-    const int res = probe_all<true>(a, r, tag, cap);
+    load_rec(a.ra, s, C, r);
+    const int res = exact_probe<C, true>(a, r, a.pmask[s], cap, tag);
     if (res == 2) a.state[s] = ST_REJECTED;
     else if (res == 0) a.state[s] = ST_ACCEPTED_NEW;
     else waiting++;
   }
   for (int o = 16; o; o >>= 1) waiting += __shfl_down_sync(0xffffffffu, waiting, o);
-  if ((threadIdx.x & 31) == 0 && waiting) atomicAdd((unsigned long long*)&a.und_count[round], (unsigned long long)waiting);
+  if ((threadIdx.x & 31) == 0 && waiting) atomicAdd((unsigned long long*)&a.und_count[round], waiting);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&dsc->rounds_used, round);
 }
 
 // serial completion in rank order, one thread per cooperative subtask
-__global__ void k_big_finish(BigArgs a, DevScalars* dsc, const int32_t* __restrict__ big_seg,
-                             const int32_t* __restrict__ seg_begin, int last_round) {
-  if (a.und_count[last_round] == 0) return;
+template <int C>
+__global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __restrict__ big_seg,
+                               const int32_t* __restrict__ seg_begin, int last_round) {
+  if (dsc->n_constrained == 0 || a.und_count[last_round] == 0) return;
   const int64_t ns = dsc->n_big_seg;
   const uint64_t cap = *a.cap;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ns; x += (int64_t)gridDim.x * blockDim.x) {
@@ -403,24 +499,44 @@ __global__ void k_big_finish(BigArgs a, DevScalars* dsc, const int32_t* __restri
       const uint8_t st = a.state[s];
       if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
       Rec r;
-      load_big(a, s, r);
-      if (st == ST_UNDECIDED && probe_all<false>(a, r, 0, cap) == 2) {
+      load_rec(a.ra, s, C, r);
+      if (st == ST_UNDECIDED && exact_probe<C, false>(a, r, a.pmask[s], cap, 0) == 2) {
         a.state[s] = ST_REJECTED;
         continue;
       }
-      register_keys(a, r, true, 0, cap, dsc);
+      exact_register<C>(a, s, r, true, 0);
       a.state[s] = ST_ACCEPTED;
     }
   }
 }
 
-__global__ void k_big_flags(BigArgs a, DevScalars* dsc, uint8_t* __restrict__ acc_flag) {
+__global__ void k_big_flags(const int32_t* __restrict__ big_pos, const uint8_t* __restrict__ state,
+                            const int32_t* __restrict__ rec_rank, const DevScalars* __restrict__ dsc,
+                            uint8_t* __restrict__ acc_flag) {
   const int64_t nb = dsc->n_big;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t s = a.big_pos[q];
-    const uint8_t st = a.state[s];
-    acc_flag[a.rec_rank[s]] = (st == ST_ACCEPTED || st == ST_ACCEPTED_NEW) ? 1 : 0;
+    const int32_t s = big_pos[q];
+    const uint8_t st = state[s];
+    acc_flag[rec_rank[s]] = (st == ST_ACCEPTED || st == ST_ACCEPTED_NEW) ? 1 : 0;
   }
+}
+
+template <int C>
+int run_coop(Handle& h, const CoopArgs& a, int grid, int rounds) {
+  ++h.launches;
+  k_pair_register<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
+  ++h.launches;
+  k_pair_probe<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
+  for (int r = 1; r <= rounds; r++) {
+    ++h.launches;
+    k_exact_register<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+    ++h.launches;
+    k_exact_probe<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+  }
+  ++h.launches;
+  k_exact_finish<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.big_seg, h.seg_begin, rounds);
+  PDG_CUDA(cudaGetLastError());
+  return PDG_OK;
 }
 
 }  // namespace
@@ -462,31 +578,29 @@ int step_accept(Handle& h, int c) {
   if ((st = scan_excl_i32(h, fpos, h.scan_tmp, 0, &h.dsc->n_cand, cap))) return st;
   ++h.launches;
   k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fpos, h.scan_tmp, &h.dsc->n_cand, h.big_pos, &h.dsc->n_big, -1);
+  const RecArrays ra{h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, cap};
   // warp tier
   ++h.launches;
-  k_accept_warp<<<grid, kBlock, 0, h.stream>>>(h.warp_seg, h.dsc, h.seg_begin, c, cap, h.rec_u, h.rec_v, h.rec_anc,
-                                               h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.acc_flag);
+  k_accept_warp<<<grid, kBlock, 0, h.stream>>>(h.warp_seg, h.dsc, h.seg_begin, c, ra, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
-  // cooperative tier
-  // blk_a[9800..9916) is reserved for this step (other steps use [0, 9729))
+  // cooperative tier; blk_a[9800..9916) is reserved for it (other steps use [0, 9729))
   uint64_t* d_cap = reinterpret_cast<uint64_t*>(h.blk_a + 9800);
+  int64_t* n_flag = h.blk_a + 9801;
   int64_t* und_count = h.blk_a + 9850;  // [0 .. max_rounds], max_rounds <= 64
   const int R = std::max(1, std::min(h.opt.max_rounds, 64));
   PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
   ++h.launches;
-  k_table_clear<<<grid, kBlock, 0, h.stream>>>(h.tkey, h.tacc, h.tund, h.dsc, h.table_cap, d_cap);
-  BigArgs a{h.big_pos, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.state,
-            h.tkey, h.tacc, h.tund, d_cap, und_count, cap, c};
-  for (int r = 1; r <= R; r++) {
-    ++h.launches;
-    k_big_register<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
-    ++h.launches;
-    k_big_probe<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+  k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.dsc, h.table_cap, d_cap, n_flag);
+  const CoopArgs a{ra, h.big_pos, h.state, h.pmask, h.reg_slot, h.ptab, h.xtab, d_cap, n_flag, h.xcap, und_count};
+  switch (c) {
+    case 0: st = run_coop<0>(h, a, grid, R); break;
+    case 1: st = run_coop<1>(h, a, grid, R); break;
+    case 2: st = run_coop<2>(h, a, grid, R); break;
+    default: st = run_coop<3>(h, a, grid, R); break;
   }
+  if (st) return st;
   ++h.launches;
-  k_big_finish<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.big_seg, h.seg_begin, R);
-  ++h.launches;
-  k_big_flags<<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.acc_flag);
+  k_big_flags<<<grid, kBlock, 0, h.stream>>>(h.big_pos, h.state, h.rec_rank, h.dsc, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

@@ -82,6 +82,7 @@ __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->radix_skip = 0;
   dsc->radix_len = 0;
   dsc->n_warp_cand = 0;
+  dsc->n_constrained = 0;
 }
 
 // upper entries (col > row) per row: endpoints of canonical ids
@@ -124,7 +125,8 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
   if (R > h.Rcap) {
     void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp, h.flags,
                    h.radix_hist, h.radix_off, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
-                   h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg};
+                   h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg,
+                   h.pmask, h.reg_slot};
     for (void* p : old) device_release(h, p);
     const int64_t tiles = (R + kTile - 1) / kTile;
     if ((st = alloc_n(h, &h.cand_idx, R)) || (st = alloc_n(h, &h.rk[0], R)) || (st = alloc_n(h, &h.rk[1], R)) ||
@@ -136,23 +138,37 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
         (st = alloc_n(h, &h.rec_du, R)) || (st = alloc_n(h, &h.rec_dv, R)) || (st = alloc_n(h, &h.rec_rank, R)) ||
         (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
         (st = alloc_n(h, &h.acc_flag, R)) || (st = alloc_n(h, &h.seg_begin, R + 1)) ||
-        (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R))) {
+        (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) ||
+        (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R))) {
       h.Rcap = 0;
       return st;
     }
     h.Rcap = R;
   }
-  const int64_t want_table = std::max<int64_t>(1024, 2 * (int64_t)(c + 1) * (c + 1) * h.Rcap);
-  if (want_table > h.table_cap) {
-    device_release(h, h.tkey);
-    device_release(h, h.tacc);
-    device_release(h, h.tund);
-    if ((st = alloc_n(h, &h.tkey, want_table)) || (st = alloc_n(h, &h.tacc, want_table)) ||
-        (st = alloc_n(h, &h.tund, want_table))) {
+  return grow_tables(h, std::max<int64_t>(1024, 2 * (int64_t)(c + 1) * (c + 1) * h.Rcap), 0);
+}
+
+// pair table of `slots` slots; exact entries for slots / 16 flagged pairs (or `xblocks`)
+int grow_tables(Handle& h, int64_t slots, int64_t xblocks) {
+  int st;
+  if (slots > h.table_cap) {
+    device_release(h, h.ptab);
+    h.ptab = nullptr;
+    if ((st = alloc_n(h, &h.ptab, slots))) {
       h.table_cap = 0;
       return st;
     }
-    h.table_cap = want_table;
+    h.table_cap = slots;
+  }
+  xblocks = std::max<int64_t>(xblocks, std::max<int64_t>(64, h.table_cap / 16));
+  if (xblocks > h.xcap) {
+    device_release(h, h.xtab);
+    h.xtab = nullptr;
+    if ((st = alloc_n(h, &h.xtab, 16 * xblocks))) {
+      h.xcap = 0;
+      return st;
+    }
+    h.xcap = xblocks;
   }
   return PDG_OK;
 }
@@ -494,16 +510,9 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
       continue;
     }
     if (err & ERR_TABLE) {
-      const int64_t want_table = std::max<int64_t>(2 * h.table_cap, 2 * h.hsc->big_regs + 1024);
-      device_release(h, h.tkey);
-      device_release(h, h.tacc);
-      device_release(h, h.tund);
-      if ((st = alloc_n(h, &h.tkey, want_table)) || (st = alloc_n(h, &h.tacc, want_table)) ||
-          (st = alloc_n(h, &h.tund, want_table))) {
-        h.table_cap = 0;
-        return st;
-      }
-      h.table_cap = want_table;
+      // pair table too small for the registrations, or too few exact blocks
+      const int64_t slots = std::max<int64_t>(h.table_cap, 2 * h.hsc->big_regs + 1024);
+      if ((st = grow_tables(h, slots, 4 * h.xcap))) return st;
       continue;
     }
     if (err) return PDG_E_CUDA;

@@ -60,7 +60,20 @@ struct DevScalars {
   int64_t radix_len;    // radix sort: histogram length (256 * tiles)
   int64_t n_warp_cand;  // candidates in the warp tier
   int64_t n_cand_wanted;  // candidates the selection produced (may exceed capacity)
-  int64_t pad[1];
+  int64_t n_constrained;  // cooperative tier: candidates with a possible earlier marker
+};
+
+// Cooperative tier: pair table slot (16 bytes; all-ones = empty) and exact
+// entry (16 bytes; 16 per flagged pair, indexed j * 4 + j').
+struct PairSlot {
+  unsigned long long key;  // (z1 << 32) | z2
+  uint32_t minr;           // smallest rank that registered the pair
+  uint32_t xidx;           // block of exact entries, or all-ones
+};
+struct ExactEnt {
+  uint32_t acc;            // smallest accepted rank
+  uint32_t pad;
+  unsigned long long und;  // round tag (high 32) | smallest undecided rank
 };
 
 // Per-graph selection state (candidate prefix of the global order).
@@ -149,11 +162,13 @@ struct Handle {
   int32_t* warp_seg = nullptr;   // subtasks of the warp tier
   int32_t* big_pos = nullptr;    // positions of the cooperative tier
   int32_t* big_seg = nullptr;    // subtasks of the cooperative tier
-  // hash table of the cooperative tier
+  // cooperative tier: pair table, exact entries, per-position probe masks and slots
   int64_t table_cap = 0;
-  uint64_t* tkey = nullptr;
-  uint32_t* tacc = nullptr;
-  uint64_t* tund = nullptr;
+  int64_t xcap = 0;
+  PairSlot* ptab = nullptr;
+  ExactEnt* xtab = nullptr;
+  uint32_t* pmask = nullptr;
+  int32_t* reg_slot = nullptr;
 
   // budget
   int32_t* gstat = nullptr;      // G
@@ -281,6 +296,7 @@ int step_sort(Handle& h);                       // A4b: (graph, score desc, id a
 int step_accept(Handle& h, int c);              // A5 + A6
 int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7
 int ensure_candidates(Handle& h, int64_t R, int c);
+int grow_tables(Handle& h, int64_t slots, int64_t xblocks);
 int device_alloc(Handle& h, void** p, size_t bytes);
 
 }  // namespace pdg

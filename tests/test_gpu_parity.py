@@ -222,3 +222,29 @@ def test_single_vertex_and_tree_only(B):
     with B.Sparsifier.from_graph(g) as sp:
         st, ids, _, k = sp.recover(0.5, 2, capacity=4)
         assert k == 0 and st == B.PDG_UNDER_BUDGET
+
+
+# ------------------------------------------------------------------ full-size configurations
+
+@pytest.fixture(scope="module")
+def mesh128():
+    return W.mesh3d_graph(128)
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.10])
+def test_mesh128_full_size(B, mesh128, alpha):
+    """The benchmark's workload in the benchmark's launch configuration."""
+    stats = _compare(B, mesh128, alpha)
+    assert stats["coop_candidates"] > 0 and stats["max_subtask"] > 1000
+
+
+def test_mesh48_cooperative_tier_only(B):
+    """warp_tier_max = 1 sends every non-singleton subtask to the cooperative tier."""
+    g = W.mesh3d_graph(48, seed=44)
+    _compare(B, g, 0.1, warp_tier_max=1)
+    _compare(B, g, 0.1, warp_tier_max=1, max_rounds=1)
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.10])
+def test_rmat16(B, alpha):
+    _compare(B, W.rmat_graph(16, seed=16), alpha)
