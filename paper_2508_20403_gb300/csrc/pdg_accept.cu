@@ -283,6 +283,45 @@ __device__ __forceinline__ int64_t pair_find(const PairSlot* __restrict__ tab, u
   return -1;
 }
 
+// Continue a linear-probing insert or lookup after the home slot `s0` held
+// another key (the home slots of a candidate are read together first, so
+// that a thread has all of its independent memory requests in flight).
+__device__ int64_t pair_insert_after(PairSlot* __restrict__ tab, uint64_t cap, uint64_t key, int64_t s0,
+                                     DevScalars* dsc) {
+  int64_t s = (s0 + 1 == (int64_t)cap) ? 0 : s0 + 1;
+  for (uint64_t probe = 1; probe < cap; probe++) {
+    unsigned long long k = tab[s].key;
+    if (k == key) return s;
+    if (k == kEmptyKey) {
+      k = atomicCAS(&tab[s].key, (unsigned long long)kEmptyKey, (unsigned long long)key);
+      if (k == kEmptyKey || k == key) return s;
+    }
+    if (++s == (int64_t)cap) s = 0;
+  }
+  atomicOr(&dsc->err, ERR_TABLE);
+  return -1;
+}
+
+__device__ int64_t pair_find_after(const PairSlot* __restrict__ tab, uint64_t cap, uint64_t key, int64_t s0) {
+  int64_t s = (s0 + 1 == (int64_t)cap) ? 0 : s0 + 1;
+  for (uint64_t probe = 1; probe < cap; probe++) {
+    const unsigned long long k = tab[s].key;
+    if (k == key) return s;
+    if (k == kEmptyKey) return -1;
+    if (++s == (int64_t)cap) s = 0;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ PairSlot load_slot(const PairSlot* tab, int64_t s) {
+  const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(tab + s);
+  PairSlot p;
+  p.key = v.x;
+  p.minr = (uint32_t)v.y;
+  p.xidx = (uint32_t)(v.y >> 32);
+  return p;
+}
+
 __device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
 
 struct CoopArgs {
@@ -291,6 +330,7 @@ struct CoopArgs {
   uint8_t* state;
   uint32_t* pmask;     // per position: probe bits (o, i, i') that showed an earlier registrant
   int32_t* reg_slot;   // per position: pair slot of each registered (j, j'), 16 per position
+  int32_t* pslot;      // per position: pair slot of each flagged probe (o, i, i'), 32 per position
   PairSlot* ptab;
   ExactEnt* xtab;      // 16 entries (j * 4 + j') per flagged pair
   const uint64_t* cap;  // effective pair-table capacity (device)
@@ -328,16 +368,29 @@ __global__ void __launch_bounds__(kBlock) k_pair_register(CoopArgs a, DevScalars
     const int32_t s = a.big_pos[q];
     Rec r;
     load_rec(a.ra, s, C, r);
+    constexpr int NP = (C + 1) * (C + 1);
+    uint64_t key[NP];
+    int64_t slot[NP];
+    unsigned long long old[NP];
+    // all home-slot claims in flight at once
 #pragma unroll
-    for (int j = 0; j <= C; j++)
+    for (int t = 0; t < NP; t++) {
+      const int j = t / (C + 1), jp = t % (C + 1);
+      key[t] = pair_key(r.U[j], r.V[jp]);
+      slot[t] = slot_of(key[t], cap);
+      old[t] = (j <= r.b && jp <= r.b)
+                   ? atomicCAS(&a.ptab[slot[t]].key, (unsigned long long)kEmptyKey, (unsigned long long)key[t])
+                   : (unsigned long long)key[t];
+    }
 #pragma unroll
-      for (int jp = 0; jp <= C; jp++) {
-        if (j > r.b || jp > r.b) continue;
-        const int64_t slot = pair_insert(a.ptab, cap, pair_key(r.U[j], r.V[jp]), dsc);
-        if (slot < 0) return;
-        atomicMin(&a.ptab[slot].minr, (uint32_t)r.rank);
-        a.reg_slot[(int64_t)s * 16 + j * 4 + jp] = (int32_t)slot;
-      }
+    for (int t = 0; t < NP; t++) {
+      const int j = t / (C + 1), jp = t % (C + 1);
+      if (j > r.b || jp > r.b) continue;
+      if (old[t] != kEmptyKey && old[t] != key[t]) slot[t] = pair_insert_after(a.ptab, cap, key[t], slot[t], dsc);
+      if (slot[t] < 0) return;
+      atomicMin(&a.ptab[slot[t]].minr, (uint32_t)r.rank);
+      a.reg_slot[(int64_t)s * 16 + j * 4 + jp] = (int32_t)slot[t];
+    }
   }
 }
 
@@ -353,34 +406,54 @@ __global__ void __launch_bounds__(kBlock) k_pair_probe(CoopArgs a, DevScalars* d
     Rec r;
     load_rec(a.ra, s, C, r);
     uint32_t pm = 0;
+    constexpr int NQ = (C + 1) * (C + 1);
 #pragma unroll
     for (int o = 0; o < 2; o++) {
       const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
+      uint64_t key[NQ];
+      int64_t slot[NQ];
+      PairSlot ps[NQ];
+      // all home slots of this orientation read at once
 #pragma unroll
-      for (int i = 0; i <= C; i++)
+      for (int t = 0; t < NQ; t++) {
+        const int i = t / (C + 1), ip = t % (C + 1);
+        const int32_t z1 = o ? r.V[i] : r.U[i];
+        const int32_t z2 = o ? r.U[ip] : r.V[ip];
+        key[t] = pair_key(z1, z2);
+        slot[t] = slot_of(key[t], cap);
+        if (i <= dx && ip <= dy) ps[t] = load_slot(a.ptab, slot[t]);
+        else ps[t].key = kEmptyKey;
+      }
 #pragma unroll
-        for (int ip = 0; ip <= C; ip++) {
-          if (i > dx || ip > dy) continue;
-          const int32_t z1 = o ? r.V[i] : r.U[i];
-          const int32_t z2 = o ? r.U[ip] : r.V[ip];
-          const int64_t slot = pair_find(a.ptab, cap, pair_key(z1, z2));
-          if (slot < 0 || a.ptab[slot].minr >= (uint32_t)r.rank) continue;
-          pm |= 1u << (o * 16 + i * 4 + ip);
-          if (a.ptab[slot].xidx == kNone) {
-            const unsigned long long xi = atomicAdd((unsigned long long*)a.n_flag, 1ull);
-            if ((int64_t)xi >= a.xcap) {
-              atomicOr(&dsc->err, ERR_TABLE);
-              continue;
-            }
-            if (atomicCAS(&a.ptab[slot].xidx, kNone, (uint32_t)xi) == kNone) {
-              ExactEnt* e = a.xtab + xi * 16;
-              for (int t = 0; t < 16; t++) {
-                e[t].acc = kNone;
-                e[t].und = ~0ull;
-              }
+      for (int t = 0; t < NQ; t++) {
+        const int i = t / (C + 1), ip = t % (C + 1);
+        if (i > dx || ip > dy) continue;
+        if (ps[t].key != key[t]) {
+          if (ps[t].key == kEmptyKey) continue;
+          slot[t] = pair_find_after(a.ptab, cap, key[t], slot[t]);
+          if (slot[t] < 0) continue;
+          ps[t] = load_slot(a.ptab, slot[t]);
+        }
+        if (ps[t].minr >= (uint32_t)r.rank) continue;
+        pm |= 1u << (o * 16 + i * 4 + ip);
+        const int64_t slt = slot[t];
+        a.pslot[(int64_t)s * 32 + o * 16 + i * 4 + ip] = (int32_t)slt;
+        // flag the pair: the first claimant hands it a block of exact entries
+        if (ps[t].xidx == kNone && *reinterpret_cast<volatile uint32_t*>(&a.ptab[slt].xidx) == kNone) {
+          const unsigned long long xi = atomicAdd((unsigned long long*)a.n_flag, 1ull);
+          if ((int64_t)xi >= a.xcap) {
+            atomicOr(&dsc->err, ERR_TABLE);
+            continue;
+          }
+          if (atomicCAS(&a.ptab[slt].xidx, kNone, (uint32_t)xi) == kNone) {
+            ExactEnt* e = a.xtab + xi * 16;
+            for (int w = 0; w < 16; w++) {
+              e[w].acc = kNone;
+              e[w].und = ~0ull;
             }
           }
         }
+      }
     }
     a.pmask[s] = pm;
     a.state[s] = pm ? ST_UNDECIDED : ST_ACCEPTED_NEW;
@@ -408,10 +481,21 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, con
     }
 }
 
-// exact probes: 2 = rejected, 1 = must wait, 0 = free of earlier markers
+// exact probes: 2 = rejected, 1 = must wait, 0 = free of earlier markers.
+// The pair slots of the flagged probes were saved by phase A2 (pslot).
 template <int C, bool WITH_UND>
-__device__ __forceinline__ int exact_probe(const CoopArgs& a, const Rec& r, uint32_t pm, uint64_t cap, uint64_t tag) {
+__device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const Rec& r, uint32_t pm, uint64_t tag) {
   int res = 0;
+  uint32_t xis[2][C + 1][C + 1];
+#pragma unroll
+  for (int o = 0; o < 2; o++)
+#pragma unroll
+    for (int i = 0; i <= C; i++)
+#pragma unroll
+      for (int ip = 0; ip <= C; ip++) {
+        const int bit = o * 16 + i * 4 + ip;
+        xis[o][i][ip] = (pm & (1u << bit)) ? a.ptab[a.pslot[(int64_t)s * 32 + bit]].xidx : kNone;
+      }
 #pragma unroll
   for (int o = 0; o < 2; o++) {
     const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
@@ -419,12 +503,7 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, const Rec& r, uint
     for (int i = 0; i <= C; i++)
 #pragma unroll
       for (int ip = 0; ip <= C; ip++) {
-        if (!(pm & (1u << (o * 16 + i * 4 + ip)))) continue;
-        const int32_t z1 = o ? r.V[i] : r.U[i];
-        const int32_t z2 = o ? r.U[ip] : r.V[ip];
-        const int64_t slot = pair_find(a.ptab, cap, pair_key(z1, z2));
-        if (slot < 0) continue;
-        const uint32_t xi = a.ptab[slot].xidx;
+        const uint32_t xi = xis[o][i][ip];
         if (xi == kNone) continue;
         const int h1 = dx - i, h2 = dy - ip;
 #pragma unroll
@@ -476,7 +555,7 @@ __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* 
     if (a.state[s] != ST_UNDECIDED) continue;
     Rec r;
     load_rec(a.ra, s, C, r);
-    const int res = exact_probe<C, true>(a, r, a.pmask[s], cap, tag);
+    const int res = exact_probe<C, true>(a, s, r, a.pmask[s], tag);
     if (res == 2) a.state[s] = ST_REJECTED;
     else if (res == 0) a.state[s] = ST_ACCEPTED_NEW;
     else waiting++;
@@ -500,7 +579,7 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
       if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
       Rec r;
       load_rec(a.ra, s, C, r);
-      if (st == ST_UNDECIDED && exact_probe<C, false>(a, r, a.pmask[s], cap, 0) == 2) {
+      if (st == ST_UNDECIDED && exact_probe<C, false>(a, s, r, a.pmask[s], 0) == 2) {
         a.state[s] = ST_REJECTED;
         continue;
       }
@@ -591,7 +670,8 @@ int step_accept(Handle& h, int c) {
   PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
   ++h.launches;
   k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.dsc, h.table_cap, d_cap, n_flag);
-  const CoopArgs a{ra, h.big_pos, h.state, h.pmask, h.reg_slot, h.ptab, h.xtab, d_cap, n_flag, h.xcap, und_count};
+  const CoopArgs a{ra,     h.big_pos, h.state, h.pmask, h.reg_slot, h.pslot, h.ptab,
+                   h.xtab, d_cap,     n_flag,  h.xcap,  und_count};
   switch (c) {
     case 0: st = run_coop<0>(h, a, grid, R); break;
     case 1: st = run_coop<1>(h, a, grid, R); break;

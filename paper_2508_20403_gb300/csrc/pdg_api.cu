@@ -126,7 +126,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
     void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp, h.flags,
                    h.radix_hist, h.radix_off, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
                    h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg,
-                   h.pmask, h.reg_slot};
+                   h.pmask, h.reg_slot, h.pslot};
     for (void* p : old) device_release(h, p);
     const int64_t tiles = (R + kTile - 1) / kTile;
     if ((st = alloc_n(h, &h.cand_idx, R)) || (st = alloc_n(h, &h.rk[0], R)) || (st = alloc_n(h, &h.rk[1], R)) ||
@@ -139,7 +139,8 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
         (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
         (st = alloc_n(h, &h.acc_flag, R)) || (st = alloc_n(h, &h.seg_begin, R + 1)) ||
         (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) ||
-        (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R))) {
+        (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R)) ||
+        (st = alloc_n(h, &h.pslot, 32 * R))) {
       h.Rcap = 0;
       return st;
     }

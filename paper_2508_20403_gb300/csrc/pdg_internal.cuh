@@ -169,6 +169,7 @@ struct Handle {
   ExactEnt* xtab = nullptr;
   uint32_t* pmask = nullptr;
   int32_t* reg_slot = nullptr;
+  int32_t* pslot = nullptr;
 
   // budget
   int32_t* gstat = nullptr;      // G
