@@ -401,14 +401,20 @@ __global__ void __launch_bounds__(kBlock) k_pair_probe(CoopArgs a, DevScalars* d
   const int64_t nb = dsc->n_big;
   const uint64_t cap = *a.cap;
   unsigned long long cons = 0;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t s = a.big_pos[q];
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop: every lane of a warp runs the same iterations
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); q0 < nb;
+       q0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = q0 + lane;
+    const bool valid = q < nb;
+    const int32_t s = valid ? a.big_pos[q] : 0;
     Rec r;
-    load_rec(a.ra, s, C, r);
+    if (valid) load_rec(a.ra, s, C, r);
     uint32_t pm = 0;
+    int nclaim = 0;
     constexpr int NQ = (C + 1) * (C + 1);
 #pragma unroll
-    for (int o = 0; o < 2; o++) {
+    for (int o = 0; o < 2 && valid; o++) {
       const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
       uint64_t key[NQ];
       int64_t slot[NQ];
@@ -436,28 +442,41 @@ __global__ void __launch_bounds__(kBlock) k_pair_probe(CoopArgs a, DevScalars* d
         }
         if (ps[t].minr >= (uint32_t)r.rank) continue;
         pm |= 1u << (o * 16 + i * 4 + ip);
-        const int64_t slt = slot[t];
-        a.pslot[(int64_t)s * 32 + o * 16 + i * 4 + ip] = (int32_t)slt;
-        // flag the pair: the first claimant hands it a block of exact entries
-        if (ps[t].xidx == kNone && *reinterpret_cast<volatile uint32_t*>(&a.ptab[slt].xidx) == kNone) {
-          const unsigned long long xi = atomicAdd((unsigned long long*)a.n_flag, 1ull);
-          if ((int64_t)xi >= a.xcap) {
-            atomicOr(&dsc->err, ERR_TABLE);
-            continue;
-          }
-          if (atomicCAS(&a.ptab[slt].xidx, kNone, (uint32_t)xi) == kNone) {
-            ExactEnt* e = a.xtab + xi * 16;
-            for (int w = 0; w < 16; w++) {
-              e[w].acc = kNone;
-              e[w].und = ~0ull;
-            }
-          }
-        }
+        a.pslot[(int64_t)s * 32 + o * 16 + i * 4 + ip] = (int32_t)slot[t];
+        if (ps[t].xidx == kNone) nclaim++;
       }
     }
-    a.pmask[s] = pm;
-    a.state[s] = pm ? ST_UNDECIDED : ST_ACCEPTED_NEW;
-    cons += pm ? 1 : 0;
+    if (valid) a.pmask[s] = pm;
+    // flag the probed pairs: the first claimant hands a pair a block of exact
+    // entries; block indices come from one atomic per warp
+    int pre = warp_incl_scan(nclaim);
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    unsigned long long base = 0;
+    if (lane == 0 && total) base = atomicAdd((unsigned long long*)a.n_flag, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    unsigned long long xi = base + (unsigned long long)(pre - nclaim);
+    for (int bit = 0; nclaim && bit < 32; bit++) {
+      if (!(pm & (1u << bit))) continue;
+      const int32_t slt = a.pslot[(int64_t)s * 32 + bit];
+      if (*reinterpret_cast<volatile uint32_t*>(&a.ptab[slt].xidx) != kNone) continue;
+      nclaim--;
+      if ((int64_t)xi >= a.xcap) {
+        atomicOr(&dsc->err, ERR_TABLE);
+        break;
+      }
+      if (atomicCAS(&a.ptab[slt].xidx, kNone, (uint32_t)xi) == kNone) {
+        ExactEnt* e = a.xtab + xi * 16;
+        for (int w = 0; w < 16; w++) {
+          e[w].acc = kNone;
+          e[w].und = ~0ull;
+        }
+      }
+      xi++;
+    }
+    if (valid) {
+      a.state[s] = pm ? ST_UNDECIDED : ST_ACCEPTED_NEW;
+      cons += pm ? 1 : 0;
+    }
   }
   for (int o = 16; o; o >>= 1) cons += __shfl_down_sync(0xffffffffu, cons, o);
   if ((threadIdx.x & 31) == 0 && cons) atomicAdd((unsigned long long*)&dsc->n_constrained, cons);

@@ -18,6 +18,8 @@ namespace pdg {
 
 namespace {
 
+constexpr int kRowWin = kTile;  // rows of the shared row_ptr window (a tile spans <= kTile non-empty rows)
+
 __device__ __forceinline__ int64_t cls_chunk(int64_t nnz, int nb) {
   int64_t c = (nnz + nb - 1) / nb;
   return (c + kTile - 1) / kTile * kTile;
@@ -61,6 +63,8 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
                                                      int32_t* __restrict__ ov, int32_t* __restrict__ oid,
                                                      double* __restrict__ ow) {
   __shared__ int64_t sm[kBlock / 32 + 1];
+  __shared__ int64_t srp[kRowWin + 1];  // row_ptr window of the current tile
+  __shared__ int64_t s_ra, s_rb;
   const int64_t chunk = cls_chunk(nnz, gridDim.x);
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(nnz, b0 + chunk);
@@ -68,6 +72,15 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
   int64_t run_off = WRITE ? off_off[blockIdx.x] : 0;
   int64_t tot_up = 0, tot_off = 0;
   for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
+    // rows spanned by the tile: one global search each, then a shared window
+    if (threadIdx.x == 0) s_ra = row_of(row_ptr, n, t0);
+    if (threadIdx.x == 32) s_rb = row_of(row_ptr, n, min(b1, t0 + kTile) - 1);
+    __syncthreads();
+    const int64_t ra = s_ra, span = s_rb - s_ra + 2;  // row_ptr[ra .. rb+1]
+    const bool win = span <= kRowWin + 1;
+    if (win)
+      for (int64_t i = threadIdx.x; i < span; i += kBlock) srp[i] = __ldg(row_ptr + ra + i);
+    __syncthreads();
     const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
     int32_t c[kItems];
     double x[kItems];
@@ -75,7 +88,17 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
     int32_t rows[kItems];
     if (base < b1) {
       load_entries(col, w, base, b1, c, x);
-      int64_t u = row_of(row_ptr, n, base);
+      int64_t u;
+      if (win) {  // largest local row r with srp[r] <= base
+        int64_t lo = 0, hi = span - 1;
+        while (hi - lo > 1) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (srp[mid] <= base) lo = mid; else hi = mid;
+        }
+        u = ra + lo;
+      } else {
+        u = row_of(row_ptr, n, base);
+      }
       int64_t next = __ldg(row_ptr + u + 1);
       const int32_t pu0 = __ldg(parent + u);
       int32_t pu = pu0;
