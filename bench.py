@@ -138,7 +138,8 @@ def run_ours(args, rank, world, local_rank):
     g = W.mesh3d_graph(128)
     log(f"[rank {rank}] generated {g.name} n={g.n} m={g.m} E_off={g.n_offtree} in {time.time() - t0:.1f}s")
     k = int(math.floor(args.alpha * g.n))
-    opt = B.default_options(profile=1)
+    # timed handle: the recovery is captured once and replayed as a CUDA graph
+    opt = B.default_options(use_graph=0 if args.no_graph else 1)
     sp = B.Sparsifier.from_graph(g, device=True, options=opt, stream=stream)
     info = sp.info()
     out_ids = torch.zeros(max(k, 1), dtype=torch.int32, device=dev)
@@ -165,12 +166,19 @@ def run_ours(args, rank, world, local_rank):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-            step_ms.append(sp.last_timings())
             launches.append(sp.last_stats()["launches"])
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     stats = sp.last_stats()
+    sp.close()
+    # per-step breakdown: a second handle, launched step by step with CUDA events
+    sp = B.Sparsifier.from_graph(g, device=True, options=B.default_options(profile=1), stream=stream)
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i & 0xff)
+        one()
+        if i >= args.warmup:
+            step_ms.append(sp.last_timings())
     mean_ms = float(np.mean(times))
     t_max = mean_ms
     if world > 1:
@@ -303,6 +311,7 @@ def main():
     ap.add_argument("--c", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

@@ -113,20 +113,42 @@ __device__ __forceinline__ int32_t anc_step(const int32_t* __restrict__ parent, 
   return y < 0 ? -1 : parent[y];
 }
 
+// k-th ancestor by binary lifting (level 0 = parent, level j >= 1 in up)
+__device__ __forceinline__ int32_t anc_k(const int32_t* __restrict__ parent, const int32_t* __restrict__ up, int64_t n,
+                                         int32_t x, int k) {
+  for (int j = 0; k && x >= 0; j++, k >>= 1)
+    if (k & 1) x = (j == 0) ? parent[x] : up[(int64_t)(j - 1) * n + x];
+  return x;
+}
+
+// Records in (LCA, rank) order.  Each record is oriented so that the child
+// of the LCA above the first endpoint has the smaller id ("side" order; an
+// endpoint equal to the LCA is its own side).  A marker with beta* >= 1 has
+// both endpoints strictly inside the two child subtrees, so it can only mark
+// an edge whose endpoints sit in the same two subtrees in the same order:
+// one probe orientation suffices unless the prober has an endpoint on the LCA.
 __global__ void __launch_bounds__(kBlock) k_build_records(
     const int32_t* __restrict__ lsort_rank, const int32_t* __restrict__ rank_cand, const int32_t* __restrict__ cand_idx,
     const int32_t* __restrict__ ou, const int32_t* __restrict__ ov, const int32_t* __restrict__ lca,
-    const u128* __restrict__ P, const int32_t* __restrict__ parent, const int32_t* __restrict__ up1, int c,
-    const DevScalars* __restrict__ dsc, int64_t cap, int32_t* __restrict__ rec_u, int32_t* __restrict__ rec_v,
+    const u128* __restrict__ P, const int32_t* __restrict__ parent, const int32_t* __restrict__ up, int64_t n,
+    int c, const DevScalars* __restrict__ dsc, int64_t cap, int32_t* __restrict__ rec_u, int32_t* __restrict__ rec_v,
     int32_t* __restrict__ rec_anc, int32_t* __restrict__ rec_du, int32_t* __restrict__ rec_dv,
     uint8_t* __restrict__ rec_b, int32_t* __restrict__ rec_rank, int32_t* __restrict__ rec_lca) {
   const int64_t N = dsc->n_cand;
+  const int32_t* up1 = up;  // level 1 (anc_2), nullptr for trees of depth <= 1
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = lsort_rank[s];
     const int32_t i = cand_idx[rank_cand[r]];
-    const int32_t u = ou[i], v = ov[i], l = lca[i];
+    int32_t u = ou[i], v = ov[i];
+    const int32_t l = lca[i];
     const int32_t dl = (int32_t)(uint32_t)P[l];
-    const int32_t du = (int32_t)(uint32_t)P[u] - dl, dv = (int32_t)(uint32_t)P[v] - dl;
+    int32_t du = (int32_t)(uint32_t)P[u] - dl, dv = (int32_t)(uint32_t)P[v] - dl;
+    const int32_t su = du > 0 ? anc_k(parent, up, n, u, du - 1) : l;
+    const int32_t sv = dv > 0 ? anc_k(parent, up, n, v, dv - 1) : l;
+    if (sv < su) {
+      int32_t t = u; u = v; v = t;
+      t = du; du = dv; dv = t;
+    }
     rec_u[s] = u;
     rec_v[s] = v;
     for (int j = 1; j <= c; j++) {
@@ -197,7 +219,7 @@ __global__ void k_pos_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
       big = 1;
       state[s] = ST_UNDECIDED;
       const unsigned b = rec_b[s];
-      regs += (unsigned long long)(b + 1) * (b + 1);
+      if (b > 0) regs += (unsigned long long)(b + 1) * (b + 1);
     }
     fbig[s] = big;
   }
@@ -368,6 +390,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_register(CoopArgs a, DevScalars
     const int32_t s = a.big_pos[q];
     Rec r;
     load_rec(a.ra, s, C, r);
+    if (r.b == 0) continue;  // a 0-hop neighbourhood pair only matches the edge itself
     constexpr int NP = (C + 1) * (C + 1);
     uint64_t key[NP];
     int64_t slot[NP];
@@ -397,7 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_register(CoopArgs a, DevScalars
 // Phase A2: free candidates are recovered; probed pairs with an earlier
 // registrant are flagged and get a block of exact entries
 template <int C>
-__global__ void __launch_bounds__(kBlock) k_pair_probe(CoopArgs a, DevScalars* dsc) {
+__global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars* dsc) {
   const int64_t nb = dsc->n_big;
   const uint64_t cap = *a.cap;
   unsigned long long cons = 0;
@@ -415,6 +438,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_probe(CoopArgs a, DevScalars* d
     constexpr int NQ = (C + 1) * (C + 1);
 #pragma unroll
     for (int o = 0; o < 2 && valid; o++) {
+      if (o == 1 && r.du > 0 && r.dv > 0) break;  // records are side-ordered: one orientation suffices
       const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
       uint64_t key[NQ];
       int64_t slot[NQ];
@@ -486,6 +510,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_probe(CoopArgs a, DevScalars* d
 template <int C>
 __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, const Rec& r, bool accepted,
                                                uint64_t und_val) {
+  if (r.b == 0) return;  // never registered (matches only itself)
 #pragma unroll
   for (int j = 0; j <= C; j++)
 #pragma unroll
@@ -646,8 +671,9 @@ int step_accept(Handle& h, int c) {
   int st;
   ++h.launches;
   k_build_records<<<grid, kBlock, 0, h.stream>>>(h.lsort_rank, h.rank_cand, h.cand_idx, h.off_u, h.off_v, h.lca,
-                                                  h.P[h.p_final], h.parent, up1, c, h.dsc, cap, h.rec_u, h.rec_v,
-                                                  h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.rec_lca);
+                                                  h.P[h.p_final], h.parent, up1, h.n, c, h.dsc, cap, h.rec_u,
+                                                  h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank,
+                                                  h.rec_lca);
   ++h.launches;
   k_seg_flags<<<grid, kBlock, 0, h.stream>>>(h.rec_lca, h.dsc, h.flags);
   PDG_CUDA(cudaGetLastError());

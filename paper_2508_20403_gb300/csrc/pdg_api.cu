@@ -239,6 +239,9 @@ void sparsifier_free(pdg_handle hp) {
   h.allocs.clear();
   for (cudaEvent_t e : h.ev)
     if (e) cudaEventDestroy(e);
+  if (h.gexec) cudaGraphExecDestroy(h.gexec);
+  if (h.ev_order) cudaEventDestroy(h.ev_order);
+  if (h.gstream) cudaStreamDestroy(h.gstream);
   if (h.hsc) cudaFreeHost(h.hsc);
   HostStage& s = hp->stage;
   if (s.sel) cudaFreeHost(s.sel);
@@ -273,6 +276,13 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
   cudaGetDevice(&h.device);
   cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, h.device);
   h.stream = (cudaStream_t)stream;
+  if (h.opt.use_graph) {
+    if (cudaStreamCreateWithFlags(&h.gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h.ev_order, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      h.opt.use_graph = 0;  // replay is an optimisation; run without it
+    }
+  }
   h.G = num_graphs;
   h.n = n;
   h.vtx_ptr_h.assign(vtx_ptr, vtx_ptr + num_graphs + 1);
@@ -448,58 +458,88 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
     dev_ids = h.out_ids;
     dev_scores = out_scores ? h.out_scores : nullptr;
   }
-  PDG_CUDA(cudaMemcpyAsync(h.d_k, s.k, sizeof(int64_t) * G, cudaMemcpyHostToDevice, h.stream));
-  PDG_CUDA(cudaMemcpyAsync(h.d_out_ptr, s.out_ptr, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, h.stream));
   h.launches = 0;
   const bool prof = h.opt.profile != 0;
   if (prof && !h.ev[0])
     for (cudaEvent_t& e : h.ev) PDG_CUDA(cudaEventCreate(&e));
-  auto mark = [&](int i) { if (prof) cudaEventRecord(h.ev[i], h.stream); };
+  bool capturing = false;
+  auto mark = [&](int i) {
+    if (prof && !capturing) cudaEventRecord(h.ev[i], h.stream);
+  };
   float acc_ms[8] = {0};
-  // steps A1-A3 (independent of the prefix)
-  mark(0);
-  ++h.launches;
-  k_reset_recover<<<1, 1, 0, h.stream>>>(h.dsc);
-  if ((st = step_classify(h))) return st;
-  mark(1);
-  if ((st = step_tree(h))) return st;
-  mark(2);
-  if ((st = step_score(h, h.opt.score_mode))) return st;
-  mark(3);
+  // Enqueue one attempt on h.stream: steps A1-A3 (first attempt only; they
+  // do not depend on the prefix), then A4-A7 and the read-back of the status.
+  auto enqueue = [&](bool first) -> int {
+    int e;
+    if (first) {
+      PDG_CUDA(cudaMemcpyAsync(h.d_k, s.k, sizeof(int64_t) * G, cudaMemcpyHostToDevice, h.stream));
+      PDG_CUDA(cudaMemcpyAsync(h.d_out_ptr, s.out_ptr, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, h.stream));
+      mark(0);
+      ++h.launches;
+      k_reset_recover<<<1, 1, 0, h.stream>>>(h.dsc);
+      if ((e = step_classify(h))) return e;
+      mark(1);
+      if ((e = step_tree(h))) return e;
+      mark(2);
+      if ((e = step_score(h, h.opt.score_mode))) return e;
+      mark(3);
+    }
+    ++h.launches;
+    k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
+    PDG_CUDA(cudaMemcpyAsync(h.sel, s.sel, sizeof(GraphSel) * G, cudaMemcpyHostToDevice, h.stream));
+    mark(4);
+    if ((e = step_select(h))) return e;
+    mark(5);
+    if ((e = step_sort(h))) return e;
+    mark(6);
+    if ((e = step_accept(h, c))) return e;
+    mark(7);
+    if ((e = step_budget(h, dev_ids, dev_scores))) return e;
+    mark(8);
+    PDG_CUDA(cudaMemcpyAsync(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h.stream));
+    PDG_CUDA(cudaMemcpyAsync(s.gstat, h.gstat, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, h.stream));
+    PDG_CUDA(cudaMemcpyAsync(s.gcount, h.gcount, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, h.stream));
+    return PDG_OK;
+  };
   int attempts = 0, retries = 0;
+  bool first = true;
   for (;;) {
     if (++attempts > 40) return PDG_E_CUDA;
     int64_t need = 0;
+    bool any_select = false;
     for (int32_t g = 0; g < G; g++) {
       GraphSel& gs = s.sel[g];
       std::memset(&gs, 0, sizeof(gs));
       gs.want = h.want_h[g];
       gs.take_all = (h.want_h[g] >= eoff[g]) ? 1 : 0;
       need += gs.take_all ? eoff[g] : h.want_h[g];
+      if (!gs.take_all) any_select = true;
     }
     if ((st = ensure_candidates(h, std::max<int64_t>(h.Rcap, need + need / 4 + 4096), c))) return st;
-    ++h.launches;
-    k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
-    PDG_CUDA(cudaMemcpyAsync(h.sel, s.sel, sizeof(GraphSel) * G, cudaMemcpyHostToDevice, h.stream));
-    mark(4);
-    if ((st = step_select(h))) return st;
-    mark(5);
-    if ((st = step_sort(h))) return st;
-    mark(6);
-    if ((st = step_accept(h, c))) return st;
-    mark(7);
-    if ((st = step_budget(h, dev_ids, dev_scores))) return st;
-    mark(8);
-    PDG_CUDA(cudaMemcpyAsync(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h.stream));
-    PDG_CUDA(cudaMemcpyAsync(s.gstat, h.gstat, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, h.stream));
-    PDG_CUDA(cudaMemcpyAsync(s.gcount, h.gcount, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, h.stream));
-    PDG_CUDA(cudaStreamSynchronize(h.stream));
-    if (prof) {
+    // the launch sequence a CUDA graph bakes in
+    const GraphKey key{c, h.opt.score_mode, any_select ? 1 : 0, h.Rcap, h.table_cap, h.xcap,
+                       (void*)dev_ids, (void*)dev_scores, out_total};
+    bool replayed = false;
+    if (first && h.opt.use_graph && h.gexec && key == h.gkey) {
+      // replay on the private stream, ordered after the caller's stream
+      PDG_CUDA(cudaEventRecord(h.ev_order, h.stream));
+      PDG_CUDA(cudaStreamWaitEvent(h.gstream, h.ev_order, 0));
+      PDG_CUDA(cudaGraphLaunch(h.gexec, h.gstream));
+      PDG_CUDA(cudaStreamSynchronize(h.gstream));
+      h.launches = h.glaunches;
+      replayed = true;
+    } else {
+      if ((st = enqueue(first))) return st;
+      PDG_CUDA(cudaStreamSynchronize(h.stream));
+    }
+    if (prof && !replayed) {
       float t;
       for (int i = 0; i < 4; i++) {
         cudaEventElapsedTime(&t, h.ev[4 + i], h.ev[5 + i]);
         acc_ms[3 + i] += t;
       }
+      if (first)
+        for (int i = 0; i < 3; i++) cudaEventElapsedTime(&acc_ms[i], h.ev[i], h.ev[i + 1]);
     }
     const int err = h.hsc->err;
     if (err & ERR_RANGE) return PDG_E_RANGE;
@@ -523,14 +563,44 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
         h.want_h[g] = std::min(eoff[g], std::max<int64_t>(h.want_h[g] * 4, 64));
         again = true;
       }
-    if (!again) break;
+    if (!again) {
+      if (first && !replayed && h.opt.use_graph && attempts == 1) {
+        // this call needed one attempt: capture it for replay by later calls
+        const cudaStream_t user = h.stream;
+        const int64_t launched = h.launches;
+        h.stream = h.gstream;
+        capturing = true;
+        h.launches = 0;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(h.gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          const int cst = enqueue(true);
+          const cudaError_t ce = cudaStreamEndCapture(h.gstream, &graph);
+          if (cst == PDG_OK && ce == cudaSuccess && graph) {
+            if (h.gexec) cudaGraphExecDestroy(h.gexec);
+            h.gexec = nullptr;
+            if (cudaGraphInstantiate(&h.gexec, graph, 0) == cudaSuccess) {
+              h.gkey = key;
+              h.glaunches = h.launches;
+            } else {
+              h.gexec = nullptr;
+            }
+          }
+          if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();  // a failed capture only disables replay
+        capturing = false;
+        h.stream = user;
+        h.launches = launched;
+      }
+      break;
+    }
+    first = false;
     retries++;
   }
   if (prof) {
-    mark(9);
-    PDG_CUDA(cudaStreamSynchronize(h.stream));
-    for (int i = 0; i < 3; i++) cudaEventElapsedTime(&acc_ms[i], h.ev[i], h.ev[i + 1]);
-    cudaEventElapsedTime(&acc_ms[7], h.ev[0], h.ev[9]);
+    float total = 0;
+    for (int i = 0; i < 7; i++) total += acc_ms[i];
+    acc_ms[7] = total;
     for (int i = 0; i < 8; i++) h.timings[i] = acc_ms[i];
   }
   // statistics of the last attempt

@@ -4,36 +4,43 @@
 //
 // Canonical id of {u, v}, u < v: rank of the CSR entry (u, v) among all
 // entries with row < col in row-major order.  Edge (u, v) is a tree edge iff
-// parent[v] == u or parent[u] == v.  The same pass records, for every
+// parent[v] == u or parent[u] == v.  The write pass also records, for every
 // non-root vertex u, r(u) = fl(1/w(u, parent u)) (the resistive weight
 // W_re = 1/w of Eq. RT).
 //
 // Layout: each block owns a contiguous chunk of CSR entries; each thread
-// reads kItems consecutive entries (col and w as vectors) and follows the row
-// index incrementally from one binary search, so skewed rows cost the same
-// as short ones.  Two passes (count, then write at scanned offsets).
+// reads kItems consecutive entries (vector loads) and follows the row index
+// incrementally from one binary search, so skewed rows cost the same as
+// short ones.  Two passes: the count pass streams only the column indices,
+// the write pass also the weights.
 #include "pdg_internal.cuh"
 
 namespace pdg {
 
 namespace {
 
-constexpr int kRowWin = kTile;  // rows of the shared row_ptr window (a tile spans <= kTile non-empty rows)
-
 __device__ __forceinline__ int64_t cls_chunk(int64_t nnz, int nb) {
   int64_t c = (nnz + nb - 1) / nb;
   return (c + kTile - 1) / kTile * kTile;
 }
 
-// Loads kItems entries starting at base (base is a multiple of kItems).
-__device__ __forceinline__ void load_entries(const int32_t* __restrict__ col, const double* __restrict__ w,
-                                             int64_t base, int64_t end, int32_t (&c)[kItems],
-                                             double (&x)[kItems]) {
+// Loads kItems column indices starting at base (base is a multiple of kItems).
+__device__ __forceinline__ void load_cols(const int32_t* __restrict__ col, int64_t base, int64_t end,
+                                          int32_t (&c)[kItems]) {
   if (base + kItems <= end) {
     const int4* c4 = reinterpret_cast<const int4*>(col + base);
     int4 a = __ldg(c4), b = __ldg(c4 + 1);
     c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
     c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < kItems; i++) c[i] = (base + i < end) ? __ldg(col + base + i) : 0;
+  }
+}
+
+__device__ __forceinline__ void load_weights(const double* __restrict__ w, int64_t base, int64_t end,
+                                             double (&x)[kItems]) {
+  if (base + kItems <= end) {
     const double2* w2 = reinterpret_cast<const double2*>(w + base);
 #pragma unroll
     for (int i = 0; i < kItems / 2; i++) {
@@ -43,10 +50,7 @@ __device__ __forceinline__ void load_entries(const int32_t* __restrict__ col, co
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < kItems; i++) {
-      c[i] = (base + i < end) ? __ldg(col + base + i) : 0;
-      x[i] = (base + i < end) ? __ldg(w + base + i) : 0.0;
-    }
+    for (int i = 0; i < kItems; i++) x[i] = (base + i < end) ? __ldg(w + base + i) : 0.0;
   }
 }
 
@@ -63,8 +67,6 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
                                                      int32_t* __restrict__ ov, int32_t* __restrict__ oid,
                                                      double* __restrict__ ow) {
   __shared__ int64_t sm[kBlock / 32 + 1];
-  __shared__ int64_t srp[kRowWin + 1];  // row_ptr window of the current tile
-  __shared__ int64_t s_ra, s_rb;
   const int64_t chunk = cls_chunk(nnz, gridDim.x);
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(nnz, b0 + chunk);
@@ -72,36 +74,17 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
   int64_t run_off = WRITE ? off_off[blockIdx.x] : 0;
   int64_t tot_up = 0, tot_off = 0;
   for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
-    // rows spanned by the tile: one global search each, then a shared window
-    if (threadIdx.x == 0) s_ra = row_of(row_ptr, n, t0);
-    if (threadIdx.x == 32) s_rb = row_of(row_ptr, n, min(b1, t0 + kTile) - 1);
-    __syncthreads();
-    const int64_t ra = s_ra, span = s_rb - s_ra + 2;  // row_ptr[ra .. rb+1]
-    const bool win = span <= kRowWin + 1;
-    if (win)
-      for (int64_t i = threadIdx.x; i < span; i += kBlock) srp[i] = __ldg(row_ptr + ra + i);
-    __syncthreads();
     const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
     int32_t c[kItems];
     double x[kItems];
     uint32_t is_up = 0, is_off = 0;
     int32_t rows[kItems];
     if (base < b1) {
-      load_entries(col, w, base, b1, c, x);
-      int64_t u;
-      if (win) {  // largest local row r with srp[r] <= base
-        int64_t lo = 0, hi = span - 1;
-        while (hi - lo > 1) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (srp[mid] <= base) lo = mid; else hi = mid;
-        }
-        u = ra + lo;
-      } else {
-        u = row_of(row_ptr, n, base);
-      }
+      load_cols(col, base, b1, c);
+      if (WRITE) load_weights(w, base, b1, x);
+      int64_t u = row_of(row_ptr, n, base);
       int64_t next = __ldg(row_ptr + u + 1);
-      const int32_t pu0 = __ldg(parent + u);
-      int32_t pu = pu0;
+      int32_t pu = __ldg(parent + u);
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
         const int64_t p = base + i;
@@ -113,7 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
           }
           rows[i] = (int32_t)u;
           const int32_t v = c[i];
-          if (!WRITE && pu == v) rtree[u] = 1.0 / x[i];
+          if (WRITE && pu == v) rtree[u] = 1.0 / x[i];
           if (u < v) {
             is_up |= 1u << i;
             const bool tree = (__ldg(parent + v) == (int32_t)u) || (pu == v);
@@ -169,7 +152,7 @@ int step_classify(Handle& h) {
   int64_t* off_off = h.blk_a + 7680;
   ++h.launches;
   k_classify<false><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.parent, h.n, h.nnz, cnt_up, cnt_off,
-                                                 nullptr, nullptr, h.rtree, nullptr, nullptr, nullptr, nullptr);
+                                                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
   PDG_CUDA(cudaGetLastError());
   int st = scan_excl_i64(h, cnt_up, off_up, nb, nullptr, nb);
   if (st) return st;
@@ -177,7 +160,7 @@ int step_classify(Handle& h) {
   if (st) return st;
   ++h.launches;
   k_classify<true><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.parent, h.n, h.nnz, nullptr, nullptr,
-                                                off_up, off_off, nullptr, h.off_u, h.off_v, h.off_id, h.off_w);
+                                                off_up, off_off, h.rtree, h.off_u, h.off_v, h.off_id, h.off_w);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

@@ -88,6 +88,21 @@ struct GraphSel {
   int32_t pad;
 };
 
+// What a captured recovery graph depends on besides the pinned parameters it
+// reads at replay time (budgets, prefix sizes, output offsets).
+struct GraphKey {
+  int c = -1, score_mode = -1, any_select = -1;
+  int64_t Rcap = -1, table_cap = -1, xcap = -1;
+  void* out_ids = nullptr;
+  void* out_scores = nullptr;
+  int64_t out_total = -1;
+  bool operator==(const GraphKey& o) const {
+    return c == o.c && score_mode == o.score_mode && any_select == o.any_select && Rcap == o.Rcap &&
+           table_cap == o.table_cap && xcap == o.xcap && out_ids == o.out_ids && out_scores == o.out_scores &&
+           out_total == o.out_total;
+  }
+};
+
 struct Handle {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -184,6 +199,12 @@ struct Handle {
   DevScalars* hsc = nullptr;   // pinned host mirror
   int64_t stats[12] = {0};
   int64_t launches = 0;  // kernels launched by the current recovery
+  // CUDA-graph replay of a whole recovery (opt.use_graph)
+  cudaStream_t gstream = nullptr;  // private stream: capture and replay
+  cudaEvent_t ev_order = nullptr;  // orders gstream after the caller's stream
+  cudaGraphExec_t gexec = nullptr;
+  GraphKey gkey;
+  int64_t glaunches = 0;
   float timings[8] = {0};
   cudaEvent_t ev[16] = {};
   size_t device_bytes = 0;

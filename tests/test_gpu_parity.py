@@ -149,6 +149,29 @@ def test_repeated_calls_deterministic(B):
                 assert ids.tolist() == first.tolist()
 
 
+def test_graph_replay_matches_oracle(B):
+    """use_graph: the first call runs and captures, later calls replay the
+    CUDA graph; every result must equal the oracle's, also when the budget
+    changes between calls (new prefix sizes, same launch sequence) and when
+    the output buffers move (a new capture)."""
+    import torch
+
+    g = W.mesh3d_graph(24, seed=12)
+    o = B.default_options(use_graph=1)
+    with B.Sparsifier.from_graph(g, options=o) as sp:
+        for alpha in (0.1, 0.1, 0.05, 0.1, 0.02, 0.02):
+            st, ids, sc, k = sp.recover(alpha, 2)
+            ost, oids, osc, _ = O.recover(g, alpha, c=2)
+            assert np.array_equal(np.asarray(ids), oids), alpha
+            assert np.array_equal(np.asarray(sc), osc)
+        kk = int(np.floor(0.1 * g.n))
+        for _ in range(3):
+            out = torch.zeros(kk, dtype=torch.int32, device="cuda")
+            st, ids, sc, k = sp.recover(0.1, 2, out_ids=out)
+            ost, oids, _, _ = O.recover(g, 0.1, c=2)
+            assert ids.cpu().numpy().tolist() == oids.tolist()
+
+
 # ------------------------------------------------------------------ batches
 
 def test_batch_equals_single(B):
