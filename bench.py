@@ -121,7 +121,7 @@ def step_bytes(n, nnz, E, J, R, k):
     }
 
 
-def run_ours(args, rank, world, local_rank):
+def run_ours(args, rank, world, local_rank, batch_graphs=None):
     import torch
 
     from paper_2508_20403_gb300 import binding as B, build as BLD, workloads as W
@@ -221,10 +221,75 @@ def run_ours(args, rank, world, local_rank):
     del flush
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e_leg(args, g, dev, B, torch)
+    if batch_graphs is not None:
+        t0 = time.time()
+        result["batch"] = batch_leg(args, batch_graphs, dev, B, torch)
+        log(f"[rank {rank}] batch leg {time.time() - t0:.1f}s")
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_leg(args)
     result["clocks"] = clk.summary()
     return result
+
+
+def batch_leg(args, graphs, dev, B, torch):
+    """Config 4: 2,000 graphs of the batching mix.  Batched = ONE
+    recover_offtree_batch over the packed CSR (CUDA-graph replay); per-graph =
+    the same graphs each resident in its own handle, one recover_offtree each
+    (plain launches).  Outputs must be identical."""
+    from paper_2508_20403_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream(dev)
+    pk = W.pack_graphs(graphs)
+    G = len(graphs)
+    alphas = np.full(G, args.batch_alpha)
+    e_off = int(sum(g.n_offtree for g in graphs))
+    opt = B.default_options(use_graph=1)
+    bs = B.BatchSparsifier.from_packed(pk, device=True, options=opt, stream=stream)
+    op = bs.out_ptr_for(alphas)
+    out = torch.zeros(max(int(op[-1]), 1), dtype=torch.int32, device=dev)
+    outs = torch.zeros(max(int(op[-1]), 1), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        bs.recover_batch(alphas, c=args.c, out_ptr=op, out_ids=out, out_scores=outs)
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, _, _, _, counts, gst = bs.recover_batch(alphas, c=args.c, out_ptr=op, out_ids=out, out_scores=outs)
+        e1.record(stream)
+        e1.synchronize()
+        tb.append(e0.elapsed_time(e1))
+    bstats = bs.last_stats()
+    batch_ids = out.cpu().numpy()
+    bs.close()
+    # per-graph plain launches on resident handles
+    handles = [B.Sparsifier.from_graph(g, device=True, stream=stream) for g in graphs]
+    kk = [int(math.floor(args.batch_alpha * g.n)) for g in graphs]
+    outs_pg = [torch.zeros(max(min(k, g.n_offtree), 1), dtype=torch.int32, device=dev) for k, g in zip(kk, graphs)]
+    for sp, o in zip(handles, outs_pg):
+        sp.recover(args.batch_alpha, args.c, out_ids=o)
+    torch.cuda.synchronize()
+    tp = []
+    for _ in range(max(1, min(args.steps, 3))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [sp.recover(args.batch_alpha, args.c, out_ids=o) for sp, o in zip(handles, outs_pg)]
+        e1.record(stream)
+        e1.synchronize()
+        tp.append(e0.elapsed_time(e1))
+    identical = all(
+        np.array_equal(batch_ids[op[i]:op[i] + counts[i]], outs_pg[i][:res[i][3]].cpu().numpy()) and
+        counts[i] == res[i][3] for i in range(G))
+    for sp in handles:
+        sp.close()
+    mb, mp = float(np.mean(tb)), float(np.mean(tp))
+    return {"graphs": G, "n": int(pk.n), "m": int(sum(g.m for g in graphs)), "n_offtree": e_off,
+            "alpha": args.batch_alpha, "c": args.c, "identical_output": bool(identical),
+            "batched": {"ms": mb, "graphs_per_s": G / (mb / 1e3), "edges_per_s": e_off / (mb / 1e3),
+                        "launch": "one recover_offtree_batch (CUDA graph replay)", "stats": bstats},
+            "per_graph": {"ms": mp, "graphs_per_s": G / (mp / 1e3), "edges_per_s": e_off / (mp / 1e3),
+                          "launch": f"{G} x recover_offtree, graphs resident, plain launches"},
+            "batched_over_per_graph": mp / mb}
 
 
 def e2e_leg(args, g, dev, B, torch):
@@ -312,6 +377,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=2000)
+    ap.add_argument("--batch-alpha", type=float, default=0.05)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -322,11 +390,20 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
+    batch_graphs = None
+    if not args.no_batch:
+        # generated in a spawn pool before any CUDA call in this process
+        from paper_2508_20403_gb300 import workloads as W
+
+        t0 = time.time()
+        batch_graphs = W.batch_graphs(args.batch_graphs, seed=W.SEED_BASE + 3 + 1000 * rank,
+                                      workers=min(16, os.cpu_count() or 1))
+        log(f"[rank {rank}] generated {len(batch_graphs)} batch graphs in {time.time() - t0:.1f}s")
     if world > 1:
         import torch
 
         torch.distributed.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank)
+    res = run_ours(args, rank, world, local_rank, batch_graphs)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -38,29 +38,33 @@ __global__ void __launch_bounds__(kBlock) k_sel_hist(const uint64_t* __restrict_
   if (b0 >= b1) return;
   const int32_t g0 = (G == 1) ? 0 : part_of(off_ptr, G, b0);
   const int32_t g1 = (G == 1) ? 0 : part_of(off_ptr, G, b1 - 1);
-  if (g0 == g1) {
-    const GraphSel s = sel[g0];
-    if (s.take_all) return;
+  // one graph at a time: a shared-memory histogram for long ranges, direct
+  // global atomics for short ones (many small graphs per chunk)
+  for (int32_t g = g0; g <= g1; g++) {
+    const int64_t r0 = (G == 1) ? b0 : max(b0, off_ptr[g]);
+    const int64_t r1 = (G == 1) ? b1 : min(b1, off_ptr[g + 1]);
+    const GraphSel s = sel[g];
+    if (s.take_all || r0 >= r1) continue;
+    uint32_t* hg = hist + (int64_t)g * kSelBins;
+    if (r1 - r0 < 2 * kSelBins) {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const uint64_t k = key[i];
+        if (lvl == 0) atomicAdd(&hg[k >> 52], 1u);
+        else if ((int32_t)(k >> 52) == s.b1) atomicAdd(&hg[(k >> 40) & 0xfff], 1u);
+      }
+      continue;
+    }
     for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       const uint64_t k = key[i];
       if (lvl == 0) atomicAdd(&sh[k >> 52], 1u);
       else if ((int32_t)(k >> 52) == s.b1) atomicAdd(&sh[(k >> 40) & 0xfff], 1u);
     }
     __syncthreads();
-    uint32_t* hg = hist + (int64_t)g0 * kSelBins;
     for (int i = threadIdx.x; i < kSelBins; i += blockDim.x)
       if (sh[i]) atomicAdd(&hg[i], sh[i]);
-  } else {
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-      const int32_t g = part_of(off_ptr, G, i);
-      const GraphSel& s = sel[g];
-      if (s.take_all) continue;
-      const uint64_t k = key[i];
-      if (lvl == 0) atomicAdd(&hist[(int64_t)g * kSelBins + (k >> 52)], 1u);
-      else if ((int32_t)(k >> 52) == s.b1) atomicAdd(&hist[(int64_t)g * kSelBins + ((k >> 40) & 0xfff)], 1u);
-    }
+    __syncthreads();
   }
 }
 
@@ -145,14 +149,22 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
     const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
     uint32_t pick = 0;
     uint64_t k[kItems];
+    // graph of the first item, then advanced item by item
+    int32_t g = (G == 1 || base >= b1) ? 0 : part_of(off_ptr, G, base);
+    int64_t g_end = (G == 1) ? INT64_MAX : off_ptr[g + 1];
+    uint64_t th = sel[g].thresh;
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
       const int64_t p = base + i;
       k[i] = 0;
       if (p < b1) {
+        while (p >= g_end) {
+          g++;
+          g_end = off_ptr[g + 1];
+          th = sel[g].thresh;
+        }
         k[i] = key[p];
-        const int32_t g = (G == 1) ? 0 : part_of(off_ptr, G, p);
-        if (k[i] >= sel[g].thresh) pick |= 1u << i;
+        if (k[i] >= th) pick |= 1u << i;
       }
     }
     const int64_t cnt = __popc(pick);
