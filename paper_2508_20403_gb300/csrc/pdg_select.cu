@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kBlock) k_sel_hist(const uint64_t* __restrict_
     const GraphSel s = sel[g];
     if (s.take_all || r0 >= r1) continue;
     uint32_t* hg = hist + (int64_t)g * kSelBins;
-    if (r1 - r0 < 2 * kSelBins) {
+    if (r1 - r0 < 256) {  // too short to amortise clearing and flushing 4096 shared bins
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         const uint64_t k = key[i];
         if (lvl == 0) atomicAdd(&hg[k >> 52], 1u);
