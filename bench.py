@@ -121,7 +121,7 @@ def step_bytes(n, nnz, E, J, R, k):
     }
 
 
-def run_ours(args, rank, world, local_rank, batch_graphs=None):
+def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None):
     import torch
 
     from paper_2508_20403_gb300 import binding as B, build as BLD, workloads as W
@@ -225,6 +225,10 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None):
         t0 = time.time()
         result["batch"] = batch_leg(args, batch_graphs, dev, B, torch)
         log(f"[rank {rank}] batch leg {time.time() - t0:.1f}s")
+    if serve_graphs is not None:
+        t0 = time.time()
+        result["serve"] = serve_leg(args, serve_graphs, dev, torch)
+        log(f"[rank {rank}] serve leg {time.time() - t0:.1f}s")
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_leg(args)
     result["clocks"] = clk.summary()
@@ -290,6 +294,44 @@ def batch_leg(args, graphs, dev, B, torch):
             "per_graph": {"ms": mp, "graphs_per_s": G / (mp / 1e3), "edges_per_s": e_off / (mp / 1e3),
                           "launch": f"{G} x recover_offtree, graphs resident, plain launches"},
             "batched_over_per_graph": mp / mb}
+
+
+def serve_pool(args, workers):
+    """Config 5's graph pool: half from the batching mix, half Delaunay
+    triangulations with n log-uniform in [1e4, 1e6] (requests draw from it)."""
+    import functools
+    import multiprocessing as mp
+
+    from paper_2508_20403_gb300 import workloads as W
+
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        return pool.map(functools.partial(W.serve_member, seed=W.SEED_BASE + 4), range(args.serve_pool),
+                        chunksize=1)
+
+
+def serve_leg(args, pool, dev, torch):
+    """Config 5: Poisson arrivals at --serve-rate for --serve-seconds into the
+    continuous-batching server; latency = completion - arrival."""
+    from paper_2508_20403_gb300 import serve as S
+
+    srv = S.Server(mem_budget_bytes=args.serve_mem_gb << 30, slots=args.serve_slots, device=dev.index).start()
+    # warm the library (first-call set-up) outside the measured stream
+    S.run_stream(srv, pool[:4], rate=50.0, duration=0.2, seed=1)
+    srv.completed.clear()
+    srv.batch_sizes.clear()
+    srv.max_inflight = 0
+    t0 = time.perf_counter()
+    reqs = S.run_stream(srv, pool, rate=args.serve_rate, duration=args.serve_seconds)
+    wall = time.perf_counter() - t0
+    srv.stop()
+    out = S.summarize(reqs, wall)
+    out.update({"rate_req_s": args.serve_rate, "seconds": args.serve_seconds, "pool_graphs": len(pool),
+                "slots": args.serve_slots, "mem_budget_gb": args.serve_mem_gb, "batches": len(srv.batch_sizes),
+                "mean_batch": float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0,
+                "max_batches_in_flight": srv.max_inflight, "errors": len(srv.errors),
+                "alphas": [0.02, 0.05, 0.10], "c": args.c})
+    return out
 
 
 def e2e_leg(args, g, dev, B, torch):
@@ -380,6 +422,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=2000)
     ap.add_argument("--batch-alpha", type=float, default=0.05)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-mem-gb", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -399,11 +447,16 @@ def main():
         batch_graphs = W.batch_graphs(args.batch_graphs, seed=W.SEED_BASE + 3 + 1000 * rank,
                                       workers=min(16, os.cpu_count() or 1))
         log(f"[rank {rank}] generated {len(batch_graphs)} batch graphs in {time.time() - t0:.1f}s")
+    serve_graphs = None
+    if not args.no_serve:
+        t0 = time.time()
+        serve_graphs = serve_pool(args, workers=min(16, os.cpu_count() or 1))
+        log(f"[rank {rank}] generated {len(serve_graphs)} serving-pool graphs in {time.time() - t0:.1f}s")
     if world > 1:
         import torch
 
         torch.distributed.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank, batch_graphs)
+    res = run_ours(args, rank, world, local_rank, batch_graphs, serve_graphs)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

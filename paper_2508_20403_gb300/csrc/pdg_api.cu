@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "pdg_internal.cuh"
 
@@ -28,10 +30,30 @@ int grid_for(const Handle& h, int64_t work, int per_block) {
   return (int)blocks;
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// handle's stream): handles on different streams never synchronise each
+// other through the allocator, which keeps concurrent batches overlapping.
+// The device's default pool keeps freed memory cached for reuse.
+static std::mutex g_pool_mutex;
+static bool g_pool_ready[64] = {false};
+
+static void prepare_pool(int device) {
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (device < 0 || device >= 64 || g_pool_ready[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  g_pool_ready[device] = true;
+}
+
 int device_alloc(Handle& h, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~(size_t)255;
-  cudaError_t e = cudaMalloc(p, bytes);
+  prepare_pool(h.device);
+  cudaError_t e = cudaMallocAsync(p, bytes, h.stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -46,7 +68,38 @@ static void device_release(Handle& h, void* p) {
   if (!p) return;
   auto it = std::find(h.allocs.begin(), h.allocs.end(), p);
   if (it != h.allocs.end()) h.allocs.erase(it);
-  cudaFree(p);
+  cudaFreeAsync(p, h.stream);
+}
+
+// Pinned host staging is recycled across handles (cudaFreeHost would
+// synchronise the whole device).
+static std::mutex g_pinned_mutex;
+static std::vector<std::pair<size_t, void*>> g_pinned_free;
+
+static void* pinned_alloc(size_t bytes) {
+  bytes = (bytes + 63) & ~(size_t)63;
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mutex);
+    for (size_t i = 0; i < g_pinned_free.size(); i++)
+      if (g_pinned_free[i].first == bytes) {
+        void* p = g_pinned_free[i].second;
+        g_pinned_free.erase(g_pinned_free.begin() + i);
+        return p;
+      }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void pinned_release(void* p, size_t bytes) {
+  if (!p) return;
+  bytes = (bytes + 63) & ~(size_t)63;
+  std::lock_guard<std::mutex> lock(g_pinned_mutex);
+  g_pinned_free.emplace_back(bytes, p);
 }
 
 template <typename T>
@@ -234,21 +287,23 @@ void sparsifier_free(pdg_handle hp) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(h.device);
-  if (h.stream) cudaStreamSynchronize(h.stream);
-  for (void* p : h.allocs) cudaFree(p);
+  for (void* p : h.allocs) cudaFreeAsync(p, h.stream);
   h.allocs.clear();
+  cudaStreamSynchronize(h.stream);  // pinned staging below may be reused at once
   for (cudaEvent_t e : h.ev)
     if (e) cudaEventDestroy(e);
   if (h.gexec) cudaGraphExecDestroy(h.gexec);
   if (h.ev_order) cudaEventDestroy(h.ev_order);
   if (h.gstream) cudaStreamDestroy(h.gstream);
-  if (h.hsc) cudaFreeHost(h.hsc);
+  pinned_release(h.hsc, sizeof(DevScalars));
   HostStage& s = hp->stage;
-  if (s.sel) cudaFreeHost(s.sel);
-  if (s.k) cudaFreeHost(s.k);
-  if (s.out_ptr) cudaFreeHost(s.out_ptr);
-  if (s.gstat) cudaFreeHost(s.gstat);
-  if (s.gcount) cudaFreeHost(s.gcount);
+  const size_t G = (size_t)std::max(s.G, 1);
+  pinned_release(s.sel, sizeof(GraphSel) * G);
+  pinned_release(s.k, sizeof(int64_t) * G);
+  pinned_release(s.out_ptr, sizeof(int64_t) * (G + 1));
+  pinned_release(s.gstat, sizeof(int32_t) * G);
+  pinned_release(s.gcount, sizeof(int64_t) * G);
+  cudaGetLastError();
   cudaSetDevice(prev);
   delete hp;
 }
@@ -298,8 +353,9 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
     ends[0] = row_ptr[0];
     ends[1] = row_ptr[n];
   } else {
-    if (cudaMemcpy(&ends[0], row_ptr, 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(&ends[1], row_ptr + n, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpyAsync(&ends[0], row_ptr, 8, cudaMemcpyDeviceToHost, h.stream) != cudaSuccess ||
+        cudaMemcpyAsync(&ends[1], row_ptr + n, 8, cudaMemcpyDeviceToHost, h.stream) != cudaSuccess ||
+        cudaStreamSynchronize(h.stream) != cudaSuccess)
       return fail(PDG_E_CUDA);
   }
   if (ends[0] != 0 || ends[1] < 0) return fail(PDG_E_NOT_CSR);
@@ -308,7 +364,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
   if (h.nnz % 2) return fail(PDG_E_NOT_SYMMETRIC);
   h.m = h.nnz / 2;
   if (h.m >= (1ll << 31)) return fail(PDG_E_INVALID_ARG);
-  if (cudaMallocHost(&h.hsc, sizeof(DevScalars)) != cudaSuccess) return fail(PDG_E_OOM);
+  if (!(h.hsc = static_cast<DevScalars*>(pinned_alloc(sizeof(DevScalars))))) return fail(PDG_E_OOM);
   if ((st = alloc_n(h, &h.dsc, 1))) return fail(st);
   if ((st = alloc_n(h, &h.row_ptr, n + 1)) || (st = alloc_n(h, &h.col, h.nnz)) || (st = alloc_n(h, &h.w, h.nnz)) ||
       (st = alloc_n(h, &h.parent, n)) || (st = alloc_n(h, &h.d_vtx_ptr, num_graphs + 1)) ||
@@ -364,12 +420,12 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
     return fail(st);
   HostStage& s = hp->stage;
   s.G = num_graphs;
-  if (cudaMallocHost(&s.sel, sizeof(GraphSel) * num_graphs) != cudaSuccess ||
-      cudaMallocHost(&s.k, sizeof(int64_t) * num_graphs) != cudaSuccess ||
-      cudaMallocHost(&s.out_ptr, sizeof(int64_t) * (num_graphs + 1)) != cudaSuccess ||
-      cudaMallocHost(&s.gstat, sizeof(int32_t) * num_graphs) != cudaSuccess ||
-      cudaMallocHost(&s.gcount, sizeof(int64_t) * num_graphs) != cudaSuccess)
-    return fail(PDG_E_OOM);
+  s.sel = static_cast<GraphSel*>(pinned_alloc(sizeof(GraphSel) * num_graphs));
+  s.k = static_cast<int64_t*>(pinned_alloc(sizeof(int64_t) * num_graphs));
+  s.out_ptr = static_cast<int64_t*>(pinned_alloc(sizeof(int64_t) * (num_graphs + 1)));
+  s.gstat = static_cast<int32_t*>(pinned_alloc(sizeof(int32_t) * num_graphs));
+  s.gcount = static_cast<int64_t*>(pinned_alloc(sizeof(int64_t) * num_graphs));
+  if (!s.sel || !s.k || !s.out_ptr || !s.gstat || !s.gcount) return fail(PDG_E_OOM);
   if (cudaMemcpyAsync(h.d_edge_ptr, h.edge_ptr_h.data(), sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice,
                       h.stream) != cudaSuccess ||
       cudaMemcpyAsync(h.d_off_ptr, h.off_ptr_h.data(), sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice,

@@ -132,42 +132,45 @@ __global__ void k_val_active_reset(DevScalars* dsc) { dsc->active = 0; }
 int validate_graph(Handle& h) {
   const int64_t n = h.n;
   const int grid = grid_for(h, std::max<int64_t>(n, h.nnz));
+  // read the device scalars back on the handle's stream (no legacy-stream sync)
+  auto fetch = [&]() -> bool {
+    return cudaMemcpyAsync(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h.stream) == cudaSuccess &&
+           cudaStreamSynchronize(h.stream) == cudaSuccess;
+  };
   k_val_reset<<<1, 1, 0, h.stream>>>(h.dsc);
   k_val_rowptr<<<grid, kBlock, 0, h.stream>>>(h.row_ptr, n, h.dsc);
-  PDG_CUDA(cudaStreamSynchronize(h.stream));
-  PDG_CUDA(cudaMemcpy(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+  if (!fetch()) return check_cuda(cudaGetLastError());
   if (h.hsc->err) return PDG_E_NOT_CSR;
   if (h.nnz > 0) k_val_entries<<<grid, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, n, h.nnz, h.d_vtx_ptr, h.G, h.dsc);
-  // temporaries for the acyclicity check
+  // temporaries for the acyclicity check (stream-ordered)
   int32_t* jmp[2] = {nullptr, nullptr};
   int64_t* dep[2] = {nullptr, nullptr};
   int64_t* roots = nullptr;
   int st = PDG_OK;
   auto cleanup = [&]() {
-    cudaFree(jmp[0]);
-    cudaFree(jmp[1]);
-    cudaFree(dep[0]);
-    cudaFree(dep[1]);
-    cudaFree(roots);
+    void* ps[] = {jmp[0], jmp[1], dep[0], dep[1], roots};
+    for (void* p : ps)
+      if (p) cudaFreeAsync(p, h.stream);
   };
-  if (cudaMalloc(&jmp[0], sizeof(int32_t) * n) != cudaSuccess || cudaMalloc(&jmp[1], sizeof(int32_t) * n) != cudaSuccess ||
-      cudaMalloc(&dep[0], sizeof(int64_t) * n) != cudaSuccess || cudaMalloc(&dep[1], sizeof(int64_t) * n) != cudaSuccess ||
-      cudaMalloc(&roots, sizeof(int64_t) * h.G) != cudaSuccess) {
-    cleanup();
+  if (cudaMallocAsync((void**)&jmp[0], sizeof(int32_t) * n, h.stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&jmp[1], sizeof(int32_t) * n, h.stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&dep[0], sizeof(int64_t) * n, h.stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&dep[1], sizeof(int64_t) * n, h.stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&roots, sizeof(int64_t) * h.G, h.stream) != cudaSuccess) {
     cudaGetLastError();
+    cleanup();
     return PDG_E_OOM;
   }
   cudaMemsetAsync(roots, 0, sizeof(int64_t) * h.G, h.stream);
   k_val_parent<<<grid, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.parent, n, h.d_vtx_ptr, h.G, h.dsc, roots,
                                               jmp[0], dep[0]);
-  if (cudaStreamSynchronize(h.stream) != cudaSuccess) {
+  std::vector<int64_t> roots_h(h.G);
+  if (cudaMemcpyAsync(roots_h.data(), roots, sizeof(int64_t) * h.G, cudaMemcpyDeviceToHost, h.stream) != cudaSuccess ||
+      !fetch()) {
     cleanup();
     return check_cuda(cudaGetLastError());
   }
-  cudaMemcpy(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost);
   int err = h.hsc->err;
-  std::vector<int64_t> roots_h(h.G);
-  cudaMemcpy(roots_h.data(), roots, sizeof(int64_t) * h.G, cudaMemcpyDeviceToHost);
   for (int64_t r : roots_h)
     if (r != 1) err |= ERR_NOT_A_TREE;
   if (!(err & (ERR_NOT_CSR | ERR_BAD_WEIGHT | ERR_NOT_A_TREE | ERR_CROSS_GRAPH))) {
@@ -180,11 +183,10 @@ int validate_graph(Handle& h) {
       k_val_active_reset<<<1, 1, 0, h.stream>>>(h.dsc);
       k_val_jump<<<grid, kBlock, 0, h.stream>>>(jmp[cur], jmp[cur ^ 1], dep[cur], dep[cur ^ 1], n, h.dsc);
       cur ^= 1;
-      if (cudaStreamSynchronize(h.stream) != cudaSuccess) {
+      if (!fetch()) {
         cleanup();
         return check_cuda(cudaGetLastError());
       }
-      cudaMemcpy(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost);
       if (h.hsc->active == 0) {
         done = true;
         break;
