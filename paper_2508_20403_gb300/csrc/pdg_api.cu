@@ -177,7 +177,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
   int st;
   if (R > h.Rcap) {
     void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp, h.flags,
-                   h.radix_hist, h.radix_off, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
+                   h.radix_status, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
                    h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg,
                    h.pmask, h.reg_slot, h.pslot};
     for (void* p : old) device_release(h, p);
@@ -185,8 +185,9 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
     if ((st = alloc_n(h, &h.cand_idx, R)) || (st = alloc_n(h, &h.rk[0], R)) || (st = alloc_n(h, &h.rk[1], R)) ||
         (st = alloc_n(h, &h.rv[0], R)) || (st = alloc_n(h, &h.rv[1], R)) || (st = alloc_n(h, &h.rank_cand, R)) ||
         (st = alloc_n(h, &h.lsort_rank, R)) || (st = alloc_n(h, &h.scan_tmp, R + 1)) ||
-        (st = alloc_n(h, &h.flags, 2 * (R + 1))) || (st = alloc_n(h, &h.radix_hist, 256 * tiles)) ||
-        (st = alloc_n(h, &h.radix_off, 256 * tiles + 1)) || (st = alloc_n(h, &h.rec_u, R)) ||
+        (st = alloc_n(h, &h.flags, 2 * (R + 1))) ||
+        (st = alloc_n(h, &h.radix_status, (int64_t)kRadixPassesMax * 256 * tiles)) ||
+        (st = alloc_n(h, &h.rec_u, R)) ||
         (st = alloc_n(h, &h.rec_v, R)) || (st = alloc_n(h, &h.rec_anc, 2 * PDG_MAX_C * R)) ||
         (st = alloc_n(h, &h.rec_du, R)) || (st = alloc_n(h, &h.rec_dv, R)) || (st = alloc_n(h, &h.rec_rank, R)) ||
         (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
@@ -416,7 +417,8 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       (st = alloc_n(h, &h.d_cand_ptr, num_graphs + 1)) || (st = alloc_n(h, &h.d_graph_tmp, num_graphs + 1)) ||
       (st = alloc_n(h, &h.gstat, num_graphs)) || (st = alloc_n(h, &h.gcount, num_graphs)) ||
       (st = alloc_n(h, &h.d_k, num_graphs)) || (st = alloc_n(h, &h.d_out_ptr, num_graphs + 1)) ||
-      (st = alloc_n(h, &h.radix_dtot, 256)))
+      (st = alloc_n(h, &h.radix_dtot, 256)) || (st = alloc_n(h, &h.radix_hist, kRadixHistWords)) ||
+      (st = alloc_n(h, &h.radix_counters, 2 * kRadixPassesMax)))
     return fail(st);
   HostStage& s = hp->stage;
   s.G = num_graphs;
@@ -432,6 +434,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
                       h.stream) != cudaSuccess ||
       cudaMemsetAsync(h.hist, 0, sizeof(uint32_t) * (size_t)num_graphs * kSelBins, h.stream) != cudaSuccess ||
       cudaMemsetAsync(h.radix_dtot, 0, sizeof(uint32_t) * 256, h.stream) != cudaSuccess ||
+      cudaMemsetAsync(h.radix_hist, 0, sizeof(uint32_t) * kRadixHistWords, h.stream) != cudaSuccess ||
       cudaStreamSynchronize(h.stream) != cudaSuccess)
     return fail(PDG_E_CUDA);
   h.want_h.assign(num_graphs, 0);

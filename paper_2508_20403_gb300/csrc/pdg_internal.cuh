@@ -18,6 +18,8 @@ constexpr int kBlock = 256;         // threads per block for streaming kernels
 constexpr int kItems = 8;           // items per thread in blocked tiles
 constexpr int kTile = kBlock * kItems;
 constexpr int kSelBins = 4096;      // 12-bit digits of the candidate selection
+constexpr int kRadixPassesMax = 16; // 8 score digits + <= 4 graph digits + <= 4 LCA digits
+constexpr int kRadixHistWords = 16 * 256 + kRadixPassesMax;
 constexpr uint64_t kEmptyKey = ~0ull;
 
 // error bits raised by validation kernels (mapped to a status on the host)
@@ -159,9 +161,10 @@ struct Handle {
   int32_t* lsort_rank = nullptr;   // position in (lca, rank) order -> rank
   int64_t* scan_tmp = nullptr;     // Rcap + 1
   int32_t* flags = nullptr;        // Rcap + 1
-  uint32_t* radix_hist = nullptr;  // 256 * tiles
-  int64_t* radix_off = nullptr;    // 256 * tiles + 1
-  uint32_t* radix_dtot = nullptr;  // 256
+  uint32_t* radix_hist = nullptr;      // [8][256] histograms, [8][256] offsets, skip flags (fixed size)
+  uint32_t* radix_status = nullptr;    // look-back words: kRadixPassesMax * tiles * 256
+  uint32_t* radix_counters = nullptr;  // per pass: tile ticket, blocks finished
+  uint32_t* radix_dtot = nullptr;      // 256
   // records in (lca, rank) order
   int32_t* rec_u = nullptr;
   int32_t* rec_v = nullptr;

@@ -10,9 +10,16 @@
 //      segment whose members stay in rank order (Algorithm 1 step 3: the
 //      index-linked lists per LCA, here a segment CSR).
 //
-// Digits shared by every key are detected from the histogram and their
-// scatter is skipped.  Problem sizes are read on the device so the whole
-// sequence can be captured in a CUDA graph.
+// One-sweep LSD: one kernel histograms every digit position of a key set at
+// once, one kernel scans those histograms, and each pass is then a single
+// scatter kernel.  Its blocks take tiles in order from an atomic counter,
+// rank the tile's digits stably (warp match + per-warp counters), publish the
+// tile's digit counts and obtain the counts of all earlier tiles by looking
+// back through published values ("decoupled look-back").  Every wait on an
+// earlier tile is bounded (spin_limit); a timeout sets an error bit and the
+// recovery reports PDG_E_TIMEOUT instead of hanging.  A digit shared by all
+// keys is detected from the histogram and its pass moves nothing.  Sizes are
+// read on the device, so the sequence can be captured in a CUDA graph.
 #include "pdg_internal.cuh"
 
 namespace pdg {
@@ -22,107 +29,156 @@ namespace {
 constexpr int kRdxBins = 256;
 constexpr int kRdxWarps = kBlock / 32;
 constexpr int kRdxPerWarp = kTile / kRdxWarps;  // 256 items, 8 rounds of 32
+constexpr int kMaxDigits = 8;
+constexpr uint32_t kFlagA = 1u << 30;  // tile aggregate published
+constexpr uint32_t kFlagP = 2u << 30;  // inclusive prefix published
+constexpr uint32_t kCountMask = (1u << 30) - 1;
 
 __device__ __forceinline__ int64_t tiles_of(int64_t N) { return (N + kTile - 1) / kTile; }
 
-__global__ void __launch_bounds__(kBlock) k_rdx_hist(const uint64_t* __restrict__ k0, const uint64_t* __restrict__ k1,
-                                                     DevScalars* dsc, int shift, uint32_t* __restrict__ hist,
-                                                     uint32_t* __restrict__ dtot) {
-  __shared__ uint32_t cnt[kRdxBins];
+// Histograms of `ndig` digit positions (starting at bit `shift0`) of the keys
+// in the current buffer: ghist[d][bin].
+__global__ void __launch_bounds__(kBlock) k_os_hist(const uint64_t* k0, const uint64_t* k1, const DevScalars* dsc,
+                                                    int shift0, int ndig, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t sh[kMaxDigits][kRdxBins];
   const int64_t N = dsc->n_cand;
   const uint64_t* keys = dsc->radix_sel ? k1 : k0;
-  const int64_t T = tiles_of(N);
-  if (blockIdx.x == 0 && threadIdx.x == 0) dsc->radix_len = (int64_t)kRdxBins * T;
-  for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = t * kTile;
-#pragma unroll
-    for (int i = 0; i < kItems; i++) {
-      const int64_t idx = base + (int64_t)i * kBlock + threadIdx.x;
-      if (idx < N) atomicAdd(&cnt[(keys[idx] >> shift) & 0xff], 1u);
-    }
-    __syncthreads();
-    const uint32_t c = cnt[threadIdx.x];
-    hist[(int64_t)threadIdx.x * T + t] = c;
-    if (c) atomicAdd(&dtot[threadIdx.x], c);
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(kBlock) k_rdx_scatter(const uint64_t* k0, const uint64_t* k1,
-                                                        const int32_t* v0, const int32_t* v1,
-                                                        uint64_t* ko0, uint64_t* ko1,
-                                                        int32_t* vo0, int32_t* vo1,
-                                                        DevScalars* dsc, int shift, const int64_t* __restrict__ off,
-                                                        const uint32_t* __restrict__ dtot) {
-  __shared__ uint32_t wcnt[kRdxWarps][kRdxBins];
-  const int64_t N = dsc->n_cand;
-  if (N == 0) return;
-  const int sel = dsc->radix_sel;
-  const uint64_t* keys = sel ? k1 : k0;
-  const int32_t* vals = sel ? v1 : v0;
-  uint64_t* ko = sel ? ko0 : ko1;
-  int32_t* vo = sel ? vo0 : vo1;
-  if (dtot[(keys[0] >> shift) & 0xff] == (uint32_t)N) return;  // uniform digit: nothing moves
-  const int64_t T = tiles_of(N);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1;
-  for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
-    for (int d = lane; d < kRdxBins; d += 32) wcnt[w][d] = 0;
-    __syncwarp();
-    uint64_t kk[kItems];
-    int32_t vv[kItems];
-    int dig[kItems];
-    uint32_t rnk[kItems];
-    const int64_t base = t * kTile + (int64_t)w * kRdxPerWarp;
-#pragma unroll
-    for (int i = 0; i < kItems; i++) {
-      const int64_t idx = base + i * 32 + lane;
-      const bool valid = idx < N;
-      kk[i] = valid ? keys[idx] : 0;
-      vv[i] = valid ? vals[idx] : 0;
-      dig[i] = valid ? (int)((kk[i] >> shift) & 0xff) : kRdxBins;
-      const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
-      rnk[i] = valid ? wcnt[w][dig[i]] + __popc(peers & lt) : 0;
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) wcnt[w][dig[i]] += __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    {
-      uint32_t run = 0;
-      for (int ww = 0; ww < kRdxWarps; ww++) {
-        const uint32_t c = wcnt[ww][threadIdx.x];
-        wcnt[ww][threadIdx.x] = run;
-        run += c;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kItems; i++) {
-      if (dig[i] < kRdxBins) {
-        const int64_t pos = off[(int64_t)dig[i] * T + t] + wcnt[w][dig[i]] + rnk[i];
-        ko[pos] = kk[i];
-        vo[pos] = vv[i];
-      }
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void k_rdx_flip(DevScalars* dsc, int shift, const uint64_t* __restrict__ k0,
-                           const uint64_t* __restrict__ k1, uint32_t* __restrict__ dtot) {
-  // runs after the scatter: decide from the same histogram whether it moved data
-  __shared__ int moved;
-  const int64_t N = dsc->n_cand;
-  if (threadIdx.x == 0) {
-    const uint64_t* keys = dsc->radix_sel ? k1 : k0;
-    moved = (N > 0) && (dtot[(keys[0] >> shift) & 0xff] != (uint32_t)N);
+  for (int i = threadIdx.x; i < kMaxDigits * kRdxBins; i += kBlock) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i] >> shift0;
+    for (int d = 0; d < ndig; d++) atomicAdd(&sh[d][(k >> (8 * d)) & 0xff], 1u);
   }
   __syncthreads();
-  dtot[threadIdx.x] = 0;
-  if (threadIdx.x == 0 && moved) dsc->radix_sel ^= 1;
+  for (int i = threadIdx.x; i < ndig * kRdxBins; i += kBlock) {
+    const uint32_t c = (&sh[0][0])[i];
+    if (c) atomicAdd(&ghist[i], c);
+  }
+}
+
+// Exclusive scan of each digit's 256 bins (one warp per digit) and the
+// uniform-digit test; also clears the histogram for the next key set.
+__global__ void k_os_scan(uint32_t* __restrict__ ghist, int ndig, const DevScalars* dsc, uint32_t* __restrict__ goff,
+                          int32_t* __restrict__ skip) {
+  const int lane = threadIdx.x & 31, d = threadIdx.x >> 5;
+  if (d >= ndig) return;
+  const uint32_t N = (uint32_t)dsc->n_cand;
+  uint32_t v[8], s = 0;
+  for (int i = 0; i < 8; i++) {
+    v[i] = ghist[d * kRdxBins + lane * 8 + i];
+    s += v[i];
+  }
+  const uint32_t incl = warp_incl_scan(s);
+  uint32_t run = incl - s;
+  bool uniform = false;
+  for (int i = 0; i < 8; i++) {
+    goff[d * kRdxBins + lane * 8 + i] = run;
+    run += v[i];
+    if (v[i] == N) uniform = true;
+    ghist[d * kRdxBins + lane * 8 + i] = 0;
+  }
+  uniform = __any_sync(0xffffffffu, uniform) || N == 0;
+  if (lane == 0) skip[d] = uniform ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_os_scatter(const uint64_t* k0, const uint64_t* k1, const int32_t* v0,
+                                                       const int32_t* v1, uint64_t* ko0, uint64_t* ko1, int32_t* vo0,
+                                                       int32_t* vo1, DevScalars* dsc, int shift,
+                                                       const uint32_t* __restrict__ goff, const int32_t* skip,
+                                                       uint32_t* status, uint32_t* counters, int64_t spin_limit) {
+  __shared__ uint32_t wcnt[kRdxWarps][kRdxBins];
+  __shared__ uint32_t tile_base[kRdxBins];
+  __shared__ int64_t s_tile;
+  const int64_t N = dsc->n_cand;
+  const int sel = dsc->radix_sel;
+  const bool moves = !*skip;
+  if (moves) {
+    const uint64_t* keys = sel ? k1 : k0;
+    const int32_t* vals = sel ? v1 : v0;
+    uint64_t* ko = sel ? ko0 : ko1;
+    int32_t* vo = sel ? vo0 : vo1;
+    const int64_t T = tiles_of(N);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&counters[0], 1u);  // tiles in launch order
+    __syncthreads();
+    const int64_t t = s_tile;
+    if (t < T) {
+      for (int d = lane; d < kRdxBins; d += 32) wcnt[w][d] = 0;
+      __syncwarp();
+      uint64_t kk[kItems];
+      int32_t vv[kItems];
+      int dig[kItems];
+      uint32_t rnk[kItems];
+      const int64_t base = t * kTile + (int64_t)w * kRdxPerWarp;
+#pragma unroll
+      for (int i = 0; i < kItems; i++) {
+        const int64_t idx = base + i * 32 + lane;
+        const bool valid = idx < N;
+        kk[i] = valid ? keys[idx] : 0;
+        vv[i] = valid ? vals[idx] : 0;
+        dig[i] = valid ? (int)((kk[i] >> shift) & 0xff) : kRdxBins;
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
+        rnk[i] = valid ? wcnt[w][dig[i]] + __popc(peers & lt) : 0;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[w][dig[i]] += __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      // thread d: the tile's count of digit d, published, then the look-back
+      {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+        for (int ww = 0; ww < kRdxWarps; ww++) {
+          const uint32_t c = wcnt[ww][d];
+          wcnt[ww][d] = run;
+          run += c;
+        }
+        volatile uint32_t* st = status;
+        if (t == 0) {
+          st[d] = kFlagP | run;
+          tile_base[d] = goff[d];
+        } else {
+          st[t * kRdxBins + d] = kFlagA | run;
+          uint32_t excl = 0;
+          for (int64_t j = t - 1; j >= 0; j--) {
+            uint32_t v = st[j * kRdxBins + d];
+            int64_t spins = 0;
+            while ((v & ~kCountMask) == 0 && spins < spin_limit) {
+              v = st[j * kRdxBins + d];
+              spins++;
+            }
+            if ((v & ~kCountMask) == 0) {  // an earlier tile never published: give up, report
+              atomicOr(&dsc->err, ERR_TIMEOUT);
+              break;
+            }
+            excl += v & kCountMask;
+            if (v & kFlagP) break;
+          }
+          __threadfence();
+          st[t * kRdxBins + d] = kFlagP | (excl + run);
+          tile_base[d] = goff[d] + excl;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < kItems; i++) {
+        if (dig[i] < kRdxBins) {
+          const int64_t pos = (int64_t)tile_base[dig[i]] + wcnt[w][dig[i]] + rnk[i];
+          if (pos < N) {
+            ko[pos] = kk[i];
+            vo[pos] = vv[i];
+          }
+        }
+      }
+    }
+  }
+  // the last block to finish flips the ping-pong buffers (if the pass moved data)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&counters[1], 1u) == gridDim.x - 1 && moves) dsc->radix_sel = sel ^ 1;
+  }
 }
 
 // keys := graph index of the candidate held as value (keeps graphs contiguous)
@@ -161,44 +217,57 @@ __global__ void k_copy_vals(const int32_t* __restrict__ v0, const int32_t* __res
 
 }  // namespace
 
-int scan_excl_u32(Handle& h, const uint32_t* in, int64_t* out, const int64_t* n_dev, int64_t n_max);
-
-static int radix_pass_full(Handle& h, int shift) {
-  const int grid = h.num_sms * 4;
+// Sort the current key buffer by `ndig` 8-bit digits starting at bit shift0;
+// `pass0` indexes this key set's passes in the status / skip / counter arrays.
+static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
+  const int grid_hist = h.num_sms * 2;
   const int64_t tiles_max = (h.Rcap + kTile - 1) / kTile;
+  uint32_t* ghist = h.radix_hist;                // [8][256], kept zero between uses
+  uint32_t* goff = h.radix_hist + 8 * kRdxBins;  // [8][256]
+  int32_t* skip = reinterpret_cast<int32_t*>(h.radix_hist + 16 * kRdxBins) + pass0;
   ++h.launches;
-  k_rdx_hist<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.dsc, shift, h.radix_hist, h.radix_dtot);
-  PDG_CUDA(cudaGetLastError());
-  int st = scan_excl_u32(h, h.radix_hist, h.radix_off, &h.dsc->radix_len, kRdxBins * tiles_max);
-  if (st) return st;
+  k_os_hist<<<grid_hist, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.dsc, shift0, ndig, ghist);
   ++h.launches;
-  k_rdx_scatter<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1],
-                                               h.dsc, shift, h.radix_off, h.radix_dtot);
-  ++h.launches;
-  k_rdx_flip<<<1, kRdxBins, 0, h.stream>>>(h.dsc, shift, h.rk[0], h.rk[1], h.radix_dtot);
+  k_os_scan<<<1, 32 * ndig, 0, h.stream>>>(ghist, ndig, h.dsc, goff, skip);
+  for (int d = 0; d < ndig; d++) {
+    const int p = pass0 + d;
+    uint32_t* status = h.radix_status + (int64_t)p * tiles_max * kRdxBins;
+    uint32_t* counters = h.radix_counters + 2 * p;
+    ++h.launches;
+    k_os_scatter<<<(int)std::max<int64_t>(tiles_max, 1), kBlock, 0, h.stream>>>(
+        h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.dsc, shift0 + 8 * d,
+        goff + d * kRdxBins, skip + d, status, counters, h.opt.spin_limit);
+  }
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
 
 int step_sort(Handle& h) {
   const int grid = h.num_sms * 4;
+  const int64_t tiles_max = (h.Rcap + kTile - 1) / kTile;
+  // look-back status and tile counters start clean for every pass
+  PDG_CUDA(cudaMemsetAsync(h.radix_status, 0, sizeof(uint32_t) * (size_t)kRadixPassesMax * tiles_max * kRdxBins,
+                           h.stream));
+  PDG_CUDA(cudaMemsetAsync(h.radix_counters, 0, sizeof(uint32_t) * 2 * kRadixPassesMax, h.stream));
   int st;
+  int pass = 0;
   // 1. score descending (ties keep ascending id order)
-  for (int shift = 0; shift < 64; shift += 8)
-    if ((st = radix_pass_full(h, shift))) return st;
+  if ((st = onesweep(h, 0, 8, pass))) return st;
+  pass += 8;
   if (h.G > 1) {
     ++h.launches;
     k_key_graph<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.d_cand_ptr, h.G, h.dsc);
-    PDG_CUDA(cudaGetLastError());
-    for (int shift = 0; (1ll << shift) < h.G; shift += 8)
-      if ((st = radix_pass_full(h, shift))) return st;
+    int nd = 0;
+    while ((1ll << (8 * nd)) < h.G) nd++;
+    if ((st = onesweep(h, 0, nd, pass))) return st;
+    pass += nd;
   }
   // 2. group ranks by LCA
   ++h.launches;
   k_key_lca<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.cand_idx, h.lca, h.rank_cand, h.dsc);
-  PDG_CUDA(cudaGetLastError());
-  for (int shift = 0; (1ll << shift) < h.n; shift += 8)
-    if ((st = radix_pass_full(h, shift))) return st;
+  int nd = 0;
+  while ((1ll << (8 * nd)) < h.n) nd++;
+  if ((st = onesweep(h, 0, nd, pass))) return st;
   ++h.launches;
   k_copy_vals<<<grid, kBlock, 0, h.stream>>>(h.rv[0], h.rv[1], h.lsort_rank, h.dsc);
   PDG_CUDA(cudaGetLastError());

@@ -69,8 +69,9 @@ def _canonical(n: int, eu: np.ndarray, ev: np.ndarray):
     lo = np.minimum(eu, ev)
     hi = np.maximum(eu, ev)
     keep = lo != hi
-    key = lo[keep] * n + hi[keep]
-    key = np.unique(key)
+    key = np.sort(lo[keep] * n + hi[keep])
+    if key.shape[0]:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     return (key // n).astype(np.int32), (key % n).astype(np.int32)
 
 
@@ -170,31 +171,44 @@ def mesh3d_edges(s: int):
     return _canonical(s ** 3, a, b)
 
 
+def _rmat_chunk(args):
+    """One chunk of R-MAT samples from its own seeded stream (float32 draws:
+    the quadrant thresholds need far fewer than 24 bits)."""
+    seed, idx, cnt, scale, a, b, c = args
+    rng = np.random.default_rng([seed, idx])
+    ab, abc = a + b, a + b + c
+    su = np.zeros(cnt, dtype=np.int32)
+    sv = np.zeros(cnt, dtype=np.int32)
+    for lvl in range(scale):
+        r = rng.random(cnt, dtype=np.float32)
+        su |= (r >= ab).astype(np.int32) << lvl
+        sv |= (((r >= a) & (r < ab)) | (r >= abc)).astype(np.int32) << lvl
+    return su, sv
+
+
 def rmat_edges(rng: np.random.Generator, scale: int, edge_factor: int = 16,
                a: float = 0.57, b: float = 0.19, c: float = 0.19, permute: bool = True,
-               chunk: int = 1 << 23):
+               chunk: int = 1 << 22, workers: int = 0):
     """R-MAT edge samples, symmetrised and deduplicated; vertex labels are
-    randomly permuted (Graph500 practice) so ids carry no degree order."""
+    randomly permuted (Graph500 practice) so ids carry no degree order.
+    Samples come in chunks with seeds derived from `rng`, optionally drawn in a
+    spawn pool; the result does not depend on the number of workers."""
     nv = 1 << scale
     ne = edge_factor * nv
-    src = np.empty(ne, dtype=np.int64)
-    dst = np.empty(ne, dtype=np.int64)
-    ab, abc = a + b, a + b + c
-    for s0 in range(0, ne, chunk):
-        s1 = min(ne, s0 + chunk)
-        cnt = s1 - s0
-        su = np.zeros(cnt, dtype=np.int64)
-        sv = np.zeros(cnt, dtype=np.int64)
-        for lvl in range(scale):
-            r = rng.random(cnt)
-            bit_u = r >= ab
-            bit_v = ((r >= a) & (r < ab)) | (r >= abc)
-            su |= bit_u.astype(np.int64) << lvl
-            sv |= bit_v.astype(np.int64) << lvl
-        src[s0:s1] = su
-        dst[s0:s1] = sv
+    seed = int(rng.integers(0, 1 << 62))
+    jobs = [(seed, i, min(chunk, ne - s0), scale, a, b, c) for i, s0 in enumerate(range(0, ne, chunk))]
+    if workers and workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_rmat_chunk, jobs)
+    else:
+        parts = [_rmat_chunk(j) for j in jobs]
+    src = np.concatenate([p[0] for p in parts])
+    dst = np.concatenate([p[1] for p in parts])
+    del parts
     if permute:
-        perm = rng.permutation(nv)
+        perm = rng.permutation(nv).astype(np.int32)
         src = perm[src]
         dst = perm[dst]
     eu, ev = _canonical(nv, src, dst)
@@ -246,11 +260,11 @@ def mesh3d_graph(s: int = 128, seed: int = SEED_BASE + 1) -> Graph:
     return _finish(s ** 3, eu, ev, weights_loguniform, rng, f"mesh{s}^3", lcc=False)
 
 
-def rmat_graph(scale: int = 22, edge_factor: int = 16, seed: int = SEED_BASE + 2) -> Graph:
+def rmat_graph(scale: int = 22, edge_factor: int = 16, seed: int = SEED_BASE + 2, workers: int = 0) -> Graph:
     """Skewed R-MAT (a=.57, b=c=.19), symmetrised, deduplicated, largest
     connected component, weights U(0, 1]."""
     rng = np.random.default_rng(seed)
-    nv, eu, ev = rmat_edges(rng, scale, edge_factor)
+    nv, eu, ev = rmat_edges(rng, scale, edge_factor, workers=workers)
     return _finish(nv, eu, ev, weights_uniform_0_1, rng, f"rmat-s{scale}-ef{edge_factor}")
 
 
