@@ -220,6 +220,7 @@ __global__ void k_copy_vals(const int32_t* __restrict__ v0, const int32_t* __res
 // Sort the current key buffer by `ndig` 8-bit digits starting at bit shift0;
 // `pass0` indexes this key set's passes in the status / skip / counter arrays.
 static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
+  if (ndig <= 0) return PDG_OK;  // a single possible key value: already sorted
   const int grid_hist = h.num_sms * 2;
   const int64_t tiles_max = (h.Rcap + kTile - 1) / kTile;
   uint32_t* ghist = h.radix_hist;                // [8][256], kept zero between uses
