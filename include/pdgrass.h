@@ -194,7 +194,9 @@ int pdg_handle_info(pdg_handle h, int64_t* n, int64_t* m, int64_t* n_offtree, in
  * prefix of the global order that was scored into subtasks), subtasks,
  * largest subtask, candidates in the warp tier / cooperative tier, rounds of
  * the cooperative tier, prefix retries, attempts, kernels launched by the
- * recovery, and three reserved zeros.  stats must hold 12 int64.
+ * recovery, cooperative-tier candidates that showed an earlier registrant of
+ * one of their pairs ("constrained"), ancestor pairs registered by the
+ * cooperative tier, and one reserved zero.  stats must hold 12 int64.
  */
 int pdg_last_stats(pdg_handle h, int64_t* stats);
 

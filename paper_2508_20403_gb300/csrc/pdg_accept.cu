@@ -279,70 +279,6 @@ __device__ __forceinline__ int64_t slot_of(uint64_t key, uint64_t cap) {
   return (int64_t)__umul64hi(mix64(key), cap);
 }
 
-__device__ int64_t pair_insert(PairSlot* __restrict__ tab, uint64_t cap, uint64_t key, DevScalars* dsc) {
-  int64_t s = slot_of(key, cap);
-  for (uint64_t probe = 0; probe < cap; probe++) {
-    unsigned long long k = tab[s].key;
-    if (k == key) return s;
-    if (k == kEmptyKey) {
-      k = atomicCAS(&tab[s].key, (unsigned long long)kEmptyKey, (unsigned long long)key);
-      if (k == kEmptyKey || k == key) return s;
-    }
-    if (++s == (int64_t)cap) s = 0;
-  }
-  atomicOr(&dsc->err, ERR_TABLE);
-  return -1;
-}
-
-__device__ __forceinline__ int64_t pair_find(const PairSlot* __restrict__ tab, uint64_t cap, uint64_t key) {
-  int64_t s = slot_of(key, cap);
-  for (uint64_t probe = 0; probe < cap; probe++) {
-    const unsigned long long k = tab[s].key;
-    if (k == key) return s;
-    if (k == kEmptyKey) return -1;
-    if (++s == (int64_t)cap) s = 0;
-  }
-  return -1;
-}
-
-// Continue a linear-probing insert or lookup after the home slot `s0` held
-// another key (the home slots of a candidate are read together first, so
-// that a thread has all of its independent memory requests in flight).
-__device__ int64_t pair_insert_after(PairSlot* __restrict__ tab, uint64_t cap, uint64_t key, int64_t s0,
-                                     DevScalars* dsc) {
-  int64_t s = (s0 + 1 == (int64_t)cap) ? 0 : s0 + 1;
-  for (uint64_t probe = 1; probe < cap; probe++) {
-    unsigned long long k = tab[s].key;
-    if (k == key) return s;
-    if (k == kEmptyKey) {
-      k = atomicCAS(&tab[s].key, (unsigned long long)kEmptyKey, (unsigned long long)key);
-      if (k == kEmptyKey || k == key) return s;
-    }
-    if (++s == (int64_t)cap) s = 0;
-  }
-  atomicOr(&dsc->err, ERR_TABLE);
-  return -1;
-}
-
-__device__ int64_t pair_find_after(const PairSlot* __restrict__ tab, uint64_t cap, uint64_t key, int64_t s0) {
-  int64_t s = (s0 + 1 == (int64_t)cap) ? 0 : s0 + 1;
-  for (uint64_t probe = 1; probe < cap; probe++) {
-    const unsigned long long k = tab[s].key;
-    if (k == key) return s;
-    if (k == kEmptyKey) return -1;
-    if (++s == (int64_t)cap) s = 0;
-  }
-  return -1;
-}
-
-__device__ __forceinline__ PairSlot load_slot(const PairSlot* tab, int64_t s) {
-  const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(tab + s);
-  PairSlot p;
-  p.key = v.x;
-  p.minr = (uint32_t)v.y;
-  p.xidx = (uint32_t)(v.y >> 32);
-  return p;
-}
 
 __device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
 
@@ -381,9 +317,12 @@ __global__ void k_coop_clear(PairSlot* __restrict__ tab, DevScalars* dsc, int64_
     t4[i] = ones;
 }
 
-// Phase A1: register every (anc_j(u), anc_j'(v)), j, j' <= beta*, with its rank
+// Phase A1: register every (anc_j(u), anc_j'(v)), j, j' <= beta*, with its rank.
+// A candidate's keys advance through their probe sequences together: each
+// round issues one CAS per still-unplaced key, so a thread waits for about
+// as many rounds as its longest chain, not for the sum of its chains.
 template <int C>
-__global__ void __launch_bounds__(kBlock) k_pair_register(CoopArgs a, DevScalars* dsc) {
+__global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScalars* dsc) {
   const int64_t nb = dsc->n_big;
   const uint64_t cap = *a.cap;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
@@ -393,24 +332,38 @@ __global__ void __launch_bounds__(kBlock) k_pair_register(CoopArgs a, DevScalars
     if (r.b == 0) continue;  // a 0-hop neighbourhood pair only matches the edge itself
     constexpr int NP = (C + 1) * (C + 1);
     uint64_t key[NP];
-    int64_t slot[NP];
-    unsigned long long old[NP];
-    // all home-slot claims in flight at once
+    uint32_t slot[NP];  // capacities stay below 2^32 slots
+    uint32_t want = 0;
 #pragma unroll
     for (int t = 0; t < NP; t++) {
       const int j = t / (C + 1), jp = t % (C + 1);
       key[t] = pair_key(r.U[j], r.V[jp]);
       slot[t] = slot_of(key[t], cap);
-      old[t] = (j <= r.b && jp <= r.b)
-                   ? atomicCAS(&a.ptab[slot[t]].key, (unsigned long long)kEmptyKey, (unsigned long long)key[t])
-                   : (unsigned long long)key[t];
+      if (j <= r.b && jp <= r.b) want |= 1u << t;
+    }
+    uint32_t pend = want;
+    for (uint64_t step = 0; pend && step < cap; step++) {
+      unsigned long long old[NP];
+#pragma unroll
+      for (int t = 0; t < NP; t++)
+        old[t] = (pend >> t & 1u) ? atomicCAS(&a.ptab[slot[t]].key, (unsigned long long)kEmptyKey,
+                                               (unsigned long long)key[t])
+                                  : 0ull;
+#pragma unroll
+      for (int t = 0; t < NP; t++) {
+        if (!(pend >> t & 1u)) continue;
+        if (old[t] == kEmptyKey || old[t] == key[t]) pend &= ~(1u << t);
+        else if (++slot[t] == cap) slot[t] = 0;
+      }
+    }
+    if (pend) {  // the table is full: report; the host retries with a larger one
+      atomicOr(&dsc->err, ERR_TABLE);
+      return;
     }
 #pragma unroll
     for (int t = 0; t < NP; t++) {
+      if (!(want >> t & 1u)) continue;
       const int j = t / (C + 1), jp = t % (C + 1);
-      if (j > r.b || jp > r.b) continue;
-      if (old[t] != kEmptyKey && old[t] != key[t]) slot[t] = pair_insert_after(a.ptab, cap, key[t], slot[t], dsc);
-      if (slot[t] < 0) return;
       atomicMin(&a.ptab[slot[t]].minr, (uint32_t)r.rank);
       a.reg_slot[(int64_t)s * 16 + j * 4 + jp] = (int32_t)slot[t];
     }
@@ -418,7 +371,8 @@ __global__ void __launch_bounds__(kBlock) k_pair_register(CoopArgs a, DevScalars
 }
 
 // Phase A2: free candidates are recovered; probed pairs with an earlier
-// registrant are flagged and get a block of exact entries
+// registrant are flagged and get a block of exact entries.  Lookups advance
+// together, one slot per round, like the inserts of phase A1.
 template <int C>
 __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars* dsc) {
   const int64_t nb = dsc->n_big;
@@ -441,9 +395,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
       if (o == 1 && r.du > 0 && r.dv > 0) break;  // records are side-ordered: one orientation suffices
       const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
       uint64_t key[NQ];
-      int64_t slot[NQ];
-      PairSlot ps[NQ];
-      // all home slots of this orientation read at once
+      uint32_t slot[NQ];
+      uint32_t pend = 0, found = 0;
 #pragma unroll
       for (int t = 0; t < NQ; t++) {
         const int i = t / (C + 1), ip = t % (C + 1);
@@ -451,23 +404,37 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
         const int32_t z2 = o ? r.U[ip] : r.V[ip];
         key[t] = pair_key(z1, z2);
         slot[t] = slot_of(key[t], cap);
-        if (i <= dx && ip <= dy) ps[t] = load_slot(a.ptab, slot[t]);
-        else ps[t].key = kEmptyKey;
+        if (i <= dx && ip <= dy) pend |= 1u << t;
       }
+      for (uint64_t step = 0; pend && step < cap; step++) {
+        unsigned long long k[NQ];
+#pragma unroll
+        for (int t = 0; t < NQ; t++) k[t] = (pend >> t & 1u) ? a.ptab[slot[t]].key : 0ull;
+#pragma unroll
+        for (int t = 0; t < NQ; t++) {
+          if (!(pend >> t & 1u)) continue;
+          if (k[t] == key[t]) {
+            found |= 1u << t;
+            pend &= ~(1u << t);
+          } else if (k[t] == kEmptyKey) {
+            pend &= ~(1u << t);
+          } else if (++slot[t] == cap) {
+            slot[t] = 0;
+          }
+        }
+      }
+      uint64_t info[NQ];  // minr | xidx << 32 of the found slots
+#pragma unroll
+      for (int t = 0; t < NQ; t++)
+        info[t] = (found >> t & 1u) ? reinterpret_cast<const uint64_t*>(a.ptab + slot[t])[1] : 0ull;
 #pragma unroll
       for (int t = 0; t < NQ; t++) {
+        if (!(found >> t & 1u)) continue;
         const int i = t / (C + 1), ip = t % (C + 1);
-        if (i > dx || ip > dy) continue;
-        if (ps[t].key != key[t]) {
-          if (ps[t].key == kEmptyKey) continue;
-          slot[t] = pair_find_after(a.ptab, cap, key[t], slot[t]);
-          if (slot[t] < 0) continue;
-          ps[t] = load_slot(a.ptab, slot[t]);
-        }
-        if (ps[t].minr >= (uint32_t)r.rank) continue;
+        if ((uint32_t)info[t] >= (uint32_t)r.rank) continue;
         pm |= 1u << (o * 16 + i * 4 + ip);
         a.pslot[(int64_t)s * 32 + o * 16 + i * 4 + ip] = (int32_t)slot[t];
-        if (ps[t].xidx == kNone) nclaim++;
+        if ((uint32_t)(info[t] >> 32) == kNone) nclaim++;
       }
     }
     if (valid) a.pmask[s] = pm;
@@ -506,27 +473,35 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
   if ((threadIdx.x & 31) == 0 && cons) atomicAdd((unsigned long long*)&dsc->n_constrained, cons);
 }
 
-// exact registration of one candidate's flagged pairs
+// exact registration of one candidate's flagged pairs (its pair slots, their
+// exact blocks and the updates each issued as one batch)
 template <int C>
 __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, const Rec& r, bool accepted,
                                                uint64_t und_val) {
   if (r.b == 0) return;  // never registered (matches only itself)
+  constexpr int NP = (C + 1) * (C + 1);
+  int32_t sl[NP];
+  uint32_t xi[NP];
 #pragma unroll
-  for (int j = 0; j <= C; j++)
+  for (int t = 0; t < NP; t++) {
+    const int j = t / (C + 1), jp = t % (C + 1);
+    sl[t] = (j <= r.b && jp <= r.b) ? a.reg_slot[(int64_t)s * 16 + j * 4 + jp] : -1;
+  }
 #pragma unroll
-    for (int jp = 0; jp <= C; jp++) {
-      if (j > r.b || jp > r.b) continue;
-      const int32_t slot = a.reg_slot[(int64_t)s * 16 + j * 4 + jp];
-      const uint32_t xi = a.ptab[slot].xidx;
-      if (xi == kNone) continue;
-      ExactEnt* e = a.xtab + (int64_t)xi * 16 + j * 4 + jp;
-      if (accepted) atomicMin(&e->acc, (uint32_t)r.rank);
-      else atomicMin(&e->und, (unsigned long long)und_val);
-    }
+  for (int t = 0; t < NP; t++) xi[t] = sl[t] >= 0 ? a.ptab[sl[t]].xidx : kNone;
+#pragma unroll
+  for (int t = 0; t < NP; t++) {
+    if (xi[t] == kNone) continue;
+    const int j = t / (C + 1), jp = t % (C + 1);
+    ExactEnt* e = a.xtab + (int64_t)xi[t] * 16 + j * 4 + jp;
+    if (accepted) atomicMin(&e->acc, (uint32_t)r.rank);
+    else atomicMin(&e->und, (unsigned long long)und_val);
+  }
 }
 
 // exact probes: 2 = rejected, 1 = must wait, 0 = free of earlier markers.
-// The pair slots of the flagged probes were saved by phase A2 (pslot).
+// The pair slots of the flagged probes were saved by phase A2 (pslot); the
+// entries one flagged probe may read are loaded together.
 template <int C, bool WITH_UND>
 __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const Rec& r, uint32_t pm, uint64_t tag) {
   int res = 0;
@@ -550,15 +525,24 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
         const uint32_t xi = xis[o][i][ip];
         if (xi == kNone) continue;
         const int h1 = dx - i, h2 = dy - ip;
+        ulonglong2 ent[C + 1][C + 1];
 #pragma unroll
         for (int j = 0; j + i <= C; j++)
 #pragma unroll
           for (int jp = 0; jp + ip <= C; jp++) {
             const int bb = min(min(j + h1, jp + h2), C);
-            if (i + j > bb || ip + jp > bb) continue;
-            const ExactEnt e = a.xtab[(int64_t)xi * 16 + j * 4 + jp];
-            if (e.acc < (uint32_t)r.rank) return 2;
-            if (WITH_UND && (e.und & 0xffffffff00000000ull) == tag && (uint32_t)e.und < (uint32_t)r.rank) res = 1;
+            ent[j][jp] = (i + j <= bb && ip + jp <= bb)
+                             ? __ldcg(reinterpret_cast<const ulonglong2*>(a.xtab + (int64_t)xi * 16 + j * 4 + jp))
+                             : make_ulonglong2(~0ull, ~0ull);
+          }
+#pragma unroll
+        for (int j = 0; j + i <= C; j++)
+#pragma unroll
+          for (int jp = 0; jp + ip <= C; jp++) {
+            const uint32_t acc = (uint32_t)ent[j][jp].x;
+            const uint64_t und = ent[j][jp].y;
+            if (acc < (uint32_t)r.rank) return 2;
+            if (WITH_UND && (und & 0xffffffff00000000ull) == tag && (uint32_t)und < (uint32_t)r.rank) res = 1;
           }
       }
   }
@@ -591,7 +575,6 @@ __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* 
   if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
   const int64_t nb = dsc->n_big;
-  const uint64_t cap = *a.cap;
   const uint64_t tag = und_tag(round);
   unsigned long long waiting = 0;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
@@ -615,7 +598,6 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
                                const int32_t* __restrict__ seg_begin, int last_round) {
   if (dsc->n_constrained == 0 || a.und_count[last_round] == 0) return;
   const int64_t ns = dsc->n_big_seg;
-  const uint64_t cap = *a.cap;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ns; x += (int64_t)gridDim.x * blockDim.x) {
     const int32_t q = big_seg[x];
     for (int32_t s = seg_begin[q]; s < seg_begin[q + 1]; s++) {

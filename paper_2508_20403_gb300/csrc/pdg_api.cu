@@ -171,6 +171,25 @@ __global__ void k_endpoints(const int64_t* __restrict__ up_ptr, const int64_t* _
 
 }  // namespace
 
+// status words of the single-pass scan for inputs of up to n_max elements
+int ensure_scan_status(Handle& h, int64_t n_max) {
+  const int64_t tiles = (std::max<int64_t>(n_max, 1) + kTile - 1) / kTile;
+  if (h.scan_ctr == nullptr) {
+    int st = alloc_n(h, &h.scan_ctr, 2);
+    if (st) return st;
+    PDG_CUDA(cudaMemsetAsync(h.scan_ctr, 0, 2 * sizeof(uint32_t), h.stream));
+  }
+  if (tiles <= h.scan_tiles_cap) return PDG_OK;
+  device_release(h, h.scan_status);
+  h.scan_status = nullptr;
+  h.scan_tiles_cap = 0;
+  int st = alloc_n(h, &h.scan_status, tiles);
+  if (st) return st;
+  PDG_CUDA(cudaMemsetAsync(h.scan_status, 0, sizeof(uint64_t) * tiles, h.stream));
+  h.scan_tiles_cap = tiles;
+  return PDG_OK;
+}
+
 int ensure_candidates(Handle& h, int64_t R, int c) {
   const int64_t Rmax = std::max<int64_t>(h.E_off, 1);
   R = std::min<int64_t>(std::max<int64_t>(R, 1), Rmax);
@@ -200,12 +219,14 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
     }
     h.Rcap = R;
   }
+  if ((st = ensure_scan_status(h, h.Rcap + 1))) return st;
   return grow_tables(h, std::max<int64_t>(1024, 2 * (int64_t)(c + 1) * (c + 1) * h.Rcap), 0);
 }
 
 // pair table of `slots` slots; exact entries for slots / 16 flagged pairs (or `xblocks`)
 int grow_tables(Handle& h, int64_t slots, int64_t xblocks) {
   int st;
+  slots = std::min<int64_t>(slots, (1ll << 32) - 1);  // slot indices are 32-bit on the device
   if (slots > h.table_cap) {
     device_release(h, h.ptab);
     h.ptab = nullptr;
@@ -347,6 +368,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
     sparsifier_free(hp);
     return code;
   };
+  if ((st = sort_setup())) return fail(st);
   const cudaMemcpyKind kind = (mem_kind == PDG_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   // nnz
   int64_t ends[2];
@@ -418,7 +440,8 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       (st = alloc_n(h, &h.gstat, num_graphs)) || (st = alloc_n(h, &h.gcount, num_graphs)) ||
       (st = alloc_n(h, &h.d_k, num_graphs)) || (st = alloc_n(h, &h.d_out_ptr, num_graphs + 1)) ||
       (st = alloc_n(h, &h.radix_dtot, 256)) || (st = alloc_n(h, &h.radix_hist, kRadixHistWords)) ||
-      (st = alloc_n(h, &h.radix_counters, 2 * kRadixPassesMax)))
+      (st = alloc_n(h, &h.radix_counters, 2 * kRadixPassesMax)) ||
+      (st = ensure_scan_status(h, std::max<int64_t>(n, num_graphs) + 1)))
     return fail(st);
   HostStage& s = hp->stage;
   s.G = num_graphs;
@@ -672,6 +695,8 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
   h.stats[6] = retries;
   h.stats[7] = attempts;
   h.stats[8] = h.launches;
+  h.stats[9] = h.hsc->n_constrained;
+  h.stats[10] = h.hsc->big_regs;
   int result = PDG_OK;
   for (int32_t g = 0; g < G; g++) {
     out_count[g] = s.gcount[g];

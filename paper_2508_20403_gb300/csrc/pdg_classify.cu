@@ -8,11 +8,12 @@
 // non-root vertex u, r(u) = fl(1/w(u, parent u)) (the resistive weight
 // W_re = 1/w of Eq. RT).
 //
-// Layout: each block owns a contiguous chunk of CSR entries; each thread
-// reads kItems consecutive entries (vector loads) and follows the row index
-// incrementally from one binary search, so skewed rows cost the same as
-// short ones.  Two passes: the count pass streams only the column indices,
-// the write pass also the weights.
+// Layout: each block owns a contiguous chunk of CSR entries, taken in tiles
+// of kTile; each thread reads kItems consecutive entries (vector loads).  The
+// row starts a tile spans are staged in shared memory, so a thread finds its
+// row by a short search there and then follows it incrementally; skewed rows
+// cost the same as short ones.  Two passes: the count pass streams only the
+// column indices, the write pass also the weights.
 #include "pdg_internal.cuh"
 
 namespace pdg {
@@ -54,6 +55,24 @@ __device__ __forceinline__ void load_weights(const double* __restrict__ w, int64
   }
 }
 
+// Row of CSR entry p (largest u with row_ptr[u] <= p), found by one warp with
+// 32-way splits: about log32(n) dependent loads instead of log2(n).
+__device__ __forceinline__ int64_t warp_row_of(const int64_t* __restrict__ row_ptr, int64_t n, int64_t p) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;  // row_ptr[lo] <= p < row_ptr[hi]
+  while (hi - lo > 1) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t q = lo + lane * step;
+    const bool ok = q < hi && __ldg(row_ptr + q) <= p;
+    const int last = 31 - __clz(__ballot_sync(0xffffffffu, ok));  // lane 0 is always ok
+    lo += last * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
+constexpr int kSpanMax = kTile;  // rows staged per tile (enough when no row is empty)
+
 template <bool WRITE>
 __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__ row_ptr,
                                                      const int32_t* __restrict__ col,
@@ -67,36 +86,77 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
                                                      int32_t* __restrict__ ov, int32_t* __restrict__ oid,
                                                      double* __restrict__ ow) {
   __shared__ int64_t sm[kBlock / 32 + 1];
+  // row starts of the tile, relative to its first entry and clipped to
+  // [-1, kTile + 1]: s_rp[j] = row_ptr[r0 + j] - t0
+  __shared__ int16_t s_rp[kSpanMax + 1];
+  __shared__ int64_t s_r0;
+  // write pass: per-warp queue of (row, weight) for the reciprocals, then the
+  // tile's off-tree records (a tile holds at most kTile entries of each)
+  __shared__ double st_w[WRITE ? kTile : 1];
+  __shared__ int32_t st_u[WRITE ? kTile : 1], st_v[WRITE ? kTile : 1], st_id[WRITE ? kTile : 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t chunk = cls_chunk(nnz, gridDim.x);
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(nnz, b0 + chunk);
   int64_t run_up = WRITE ? off_up[blockIdx.x] : 0;
   int64_t run_off = WRITE ? off_off[blockIdx.x] : 0;
   int64_t tot_up = 0, tot_off = 0;
+  if (b0 < b1 && wid == 0) {
+    const int64_t r = warp_row_of(row_ptr, n, b0);
+    if (lane == 0) s_r0 = r;
+  }
   for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
-    const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
+    const int tlen = (int)min((int64_t)kTile, b1 - t0);
+    __syncthreads();  // s_r0 is set; the previous tile's shared reads are done
+    const int64_t r0 = s_r0;
+    // stage row starts kBlock at a time until they cover the tile
+    if (threadIdx.x == 0) s_rp[0] = (int16_t)max(__ldg(row_ptr + r0) - t0, (int64_t)-1);
+    int span = 0;
+    for (;;) {
+      const int j = span + 1 + threadIdx.x;
+      const int64_t r = r0 + j;
+      const int64_t rel = (r <= n) ? __ldg(row_ptr + r) - t0 : (int64_t)kTile + 1;
+      s_rp[j] = (int16_t)min(max(rel, (int64_t)-1), (int64_t)kTile + 1);
+      __syncthreads();
+      span += kBlock;
+      if (s_rp[span] >= tlen || span >= kSpanMax) break;  // uniform
+    }
+    const bool covered = s_rp[span] >= tlen;  // else (many empty rows): global row_ptr
+    const int rel0 = threadIdx.x * kItems;
     int32_t c[kItems];
     double x[kItems];
-    uint32_t is_up = 0, is_off = 0;
     int32_t rows[kItems];
-    if (base < b1) {
-      load_cols(col, base, b1, c);
-      if (WRITE) load_weights(w, base, b1, x);
-      int64_t u = row_of(row_ptr, n, base);
-      int64_t next = __ldg(row_ptr + u + 1);
+    uint32_t is_up = 0, is_off = 0, is_par = 0;
+    if (rel0 < tlen) {
+      const int64_t base = t0 + rel0;
+      load_cols(col, base, t0 + tlen, c);
+      if (WRITE) load_weights(w, base, t0 + tlen, x);
+      int64_t u, next;
+      if (covered) {
+        int lo = 0, hi = span;  // s_rp[lo] <= rel0 < s_rp[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_rp[mid] <= rel0) lo = mid; else hi = mid;
+        }
+        u = r0 + lo;
+        next = t0 + s_rp[lo + 1];
+      } else {
+        u = row_of(row_ptr, n, base);
+        next = __ldg(row_ptr + u + 1);
+      }
       int32_t pu = __ldg(parent + u);
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
         const int64_t p = base + i;
-        if (p < b1) {
+        if (i < tlen - rel0) {
           while (p >= next) {
             u++;
-            next = __ldg(row_ptr + u + 1);
+            next = covered ? t0 + s_rp[u - r0 + 1] : __ldg(row_ptr + u + 1);
             pu = __ldg(parent + u);
           }
           rows[i] = (int32_t)u;
           const int32_t v = c[i];
-          if (WRITE && pu == v) rtree[u] = 1.0 / x[i];
+          if (WRITE && pu == v) is_par |= 1u << i;
           if (u < v) {
             is_up |= 1u << i;
             const bool tree = (__ldg(parent + v) == (int32_t)u) || (pu == v);
@@ -104,6 +164,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
           }
         }
       }
+      if (rel0 + kItems >= tlen) s_r0 = u;  // row of the tile's last entry: the next tile starts there
     }
     const int64_t n_up = __popc(is_up), n_off = __popc(is_off);
     if (!WRITE) {
@@ -111,22 +172,54 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
       tot_off += n_off;
       continue;
     }
+    // r(u) = fl(1/w(u, parent u)): the warp's parent entries are queued and
+    // divided densely (a division per lane per item would keep the slow
+    // double-precision pipe busy for every CSR entry)
+    {
+      const int npar = __popc(is_par);
+      const int incl = warp_incl_scan(npar);
+      int slot = wid * (kTile / (kBlock / 32)) + incl - npar;
+#pragma unroll
+      for (int i = 0; i < kItems; i++) {
+        if (is_par & (1u << i)) {
+          st_u[slot] = rows[i];
+          st_w[slot] = x[i];
+          slot++;
+        }
+      }
+      __syncwarp();
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      for (int j = lane; j < tot; j += 32) {
+        const int q = wid * (kTile / (kBlock / 32)) + j;
+        rtree[st_u[q]] = 1.0 / st_w[q];
+      }
+    }
     int64_t tile_tot;
-    int64_t ex = block_excl_scan((n_up << 32) | n_off, sm, &tile_tot);
+    int64_t ex = block_excl_scan((n_up << 32) | n_off, sm, &tile_tot);  // also orders the queue reads
     int64_t id = run_up + (ex >> 32);
-    int64_t pos = run_off + (ex & 0xffffffffll);
+    int lpos = (int)(ex & 0xffffffffll);  // position inside the tile's output run
+    // stage the tile's off-tree records in shared memory ...
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
       if (is_up & (1u << i)) {
         if (is_off & (1u << i)) {
-          ou[pos] = rows[i];
-          ov[pos] = c[i];
-          oid[pos] = (int32_t)id;
-          ow[pos] = x[i];
-          pos++;
+          st_u[lpos] = rows[i];
+          st_v[lpos] = c[i];
+          st_id[lpos] = (int32_t)id;
+          st_w[lpos] = x[i];
+          lpos++;
         }
         id++;
       }
+    }
+    __syncthreads();
+    // ... and write them out as one contiguous, coalesced run
+    const int cnt = (int)(tile_tot & 0xffffffffll);
+    for (int j = threadIdx.x; j < cnt; j += kBlock) {
+      ou[run_off + j] = st_u[j];
+      ov[run_off + j] = st_v[j];
+      oid[run_off + j] = st_id[j];
+      ow[run_off + j] = st_w[j];
     }
     run_up += tile_tot >> 32;
     run_off += tile_tot & 0xffffffffll;

@@ -164,6 +164,9 @@ struct Handle {
   uint32_t* radix_hist = nullptr;      // [8][256] histograms, [8][256] offsets, skip flags (fixed size)
   uint32_t* radix_status = nullptr;    // look-back words: kRadixPassesMax * tiles * 256
   uint32_t* radix_counters = nullptr;  // per pass: tile ticket, blocks finished
+  uint64_t* scan_status = nullptr;     // single-pass scan: flag | value per tile, zero between scans
+  uint32_t* scan_ctr = nullptr;        // single-pass scan: tile ticket, blocks finished
+  int64_t scan_tiles_cap = 0;
   uint32_t* radix_dtot = nullptr;      // 256
   // records in (lca, rank) order
   int32_t* rec_u = nullptr;
@@ -306,6 +309,7 @@ int grid_for(const Handle& h, int64_t work, int per_block = kBlock);
 
 // device-wide exclusive scan: out[i] = sum in[0..i), out[N] = total.
 // N may live on the device (n_dev != nullptr) or be given on the host.
+int ensure_scan_status(Handle& h, int64_t n_max);  // scans of up to n_max elements can run
 int scan_excl_i64(Handle& h, const int64_t* in, int64_t* out, int64_t n_host, const int64_t* n_dev, int64_t n_max);
 int scan_excl_i32(Handle& h, const int32_t* in, int64_t* out, int64_t n_host, const int64_t* n_dev, int64_t n_max);
 int scan_excl_u32(Handle& h, const uint32_t* in, int64_t* out, const int64_t* n_dev, int64_t n_max);
@@ -317,6 +321,7 @@ int step_classify(Handle& h);                   // A1
 int step_tree(Handle& h);                       // A2
 int step_score(Handle& h, int score_mode);      // A3
 int step_select(Handle& h);                     // A4a: candidate prefix per graph
+int sort_setup();                               // per-device kernel attributes of the sort
 int step_sort(Handle& h);                       // A4b: (graph, score desc, id asc) then (lca, rank)
 int step_accept(Handle& h, int c);              // A5 + A6
 int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7

@@ -1,98 +1,156 @@
-// Device-wide exclusive prefix sums (reduce -> scan of block sums -> scan),
-// used by every compaction of the pipeline.  The length may be a device
-// value so that launches do not depend on data read back to the host.
+// Device-wide exclusive prefix sums, used by every compaction of the
+// pipeline: out[i] = sum of in[0..i), out[N] = the total.  The length may be
+// a device value so that launches do not depend on data read back to the
+// host (the whole recovery is captured in a CUDA graph).
+//
+// One launch per scan.  Short inputs (capacity up to kScanSmall) are walked
+// by a single block, tile after tile.  Longer ones use a single pass with
+// decoupled look-back: blocks take tiles in order from a ticket counter, scan
+// their tile, publish its sum, and add the sums of the earlier tiles read
+// back through the published words -- one warp reads 32 of them per memory
+// round trip.  Every wait is bounded (spin_limit): a timeout sets an error
+// bit instead of hanging.  The last block to finish clears the status words
+// and counters, so the next scan starts clean without a memset.
 #include "pdg_internal.cuh"
 
 namespace pdg {
 
 namespace {
 
-constexpr int kScanBlocksMax = 1024;
+constexpr int64_t kScanSmall = 8 * kTile;
+constexpr uint64_t kStA = 1ull << 62;          // tile sum published
+constexpr uint64_t kStP = 2ull << 62;          // inclusive prefix published
+constexpr uint64_t kStVal = (1ull << 62) - 1;  // value bits
 
 __device__ __forceinline__ int64_t load_n(int64_t n_host, const int64_t* n_dev) {
   return n_dev ? *n_dev : n_host;
 }
 
-__device__ __forceinline__ int64_t chunk_of(int64_t N, int nb) {
-  int64_t c = (N + nb - 1) / nb;
-  return (c + kTile - 1) / kTile * kTile;
+// Loads the kItems values of this thread in tile t0 (zero past N); returns their sum.
+template <typename T>
+__device__ __forceinline__ int64_t load_items(const T* __restrict__ in, int64_t base, int64_t N,
+                                              int64_t (&v)[kItems]) {
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; i++) {
+    v[i] = (base + i < N) ? (int64_t)in[base + i] : 0;
+    s += v[i];
+  }
+  return s;
+}
+
+__device__ __forceinline__ void store_items(int64_t* __restrict__ out, int64_t base, int64_t N, int64_t ex,
+                                            const int64_t (&v)[kItems]) {
+#pragma unroll
+  for (int i = 0; i < kItems; i++) {
+    if (base + i < N) out[base + i] = ex;
+    ex += v[i];
+  }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_scan_reduce(const T* __restrict__ in, int64_t n_host,
-                                                        const int64_t* n_dev, int64_t* __restrict__ bsum) {
+__global__ void __launch_bounds__(kBlock) k_scan_small(const T* __restrict__ in, int64_t* __restrict__ out,
+                                                       int64_t n_host, const int64_t* n_dev) {
   __shared__ int64_t sm[kBlock / 32 + 1];
   const int64_t N = load_n(n_host, n_dev);
-  const int64_t chunk = chunk_of(N, gridDim.x);
-  const int64_t b0 = (int64_t)blockIdx.x * chunk;
-  const int64_t b1 = min(N, b0 + chunk);
-  int64_t s = 0;
-  for (int64_t i = b0 + threadIdx.x; i < b1; i += kBlock) s += (int64_t)in[i];
-  s = block_sum(s, sm);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = s;
+  int64_t run = 0;
+  for (int64_t t0 = 0; t0 < N; t0 += kTile) {
+    const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
+    int64_t v[kItems];
+    const int64_t s = load_items(in, base, N, v);
+    int64_t tot;
+    const int64_t ex = block_excl_scan(s, sm, &tot) + run;
+    store_items(out, base, N, ex, v);
+    run += tot;
+  }
+  if (threadIdx.x == 0) out[N] = run;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_top(int64_t* __restrict__ bsum, int nb, int64_t n_host,
-                                                   const int64_t* n_dev, int64_t* __restrict__ out) {
-  __shared__ int64_t sm[33];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int64_t x = (threadIdx.x < nb) ? bsum[threadIdx.x] : 0;
-  int64_t inc = warp_incl_scan(x);
-  if (lane == 31) sm[wid] = inc;
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_scan_onepass(const T* __restrict__ in, int64_t* __restrict__ out,
+                                                         int64_t n_host, const int64_t* n_dev, uint64_t* status,
+                                                         uint32_t* ctr, int64_t spin_limit, DevScalars* dsc) {
+  __shared__ int64_t sm[kBlock / 32 + 1];
+  __shared__ int64_t s_tile, s_excl;
+  __shared__ int s_last;
+  const int64_t N = load_n(n_host, n_dev);
+  const int64_t nt = (N + kTile - 1) / kTile;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&ctr[0], 1u);  // tiles in launch order
   __syncthreads();
-  if (wid == 0) {
-    int64_t s = sm[lane];
-    int64_t si = warp_incl_scan(s);
-    sm[lane] = si - s;
-    if (lane == 31) sm[32] = si;
+  const int64_t t = s_tile;
+  if (t < nt) {
+    const int64_t base = t * kTile + (int64_t)threadIdx.x * kItems;
+    int64_t v[kItems];
+    const int64_t s = load_items(in, base, N, v);
+    int64_t tot;
+    const int64_t ex = block_excl_scan(s, sm, &tot);
+    if (threadIdx.x < 32) {
+      volatile uint64_t* st = status;
+      if (lane == 0) st[t] = (t == 0 ? kStP : kStA) | (uint64_t)tot;
+      int64_t excl = 0;
+      bool timed_out = false;
+      for (int64_t j0 = t - 1; j0 >= 0;) {
+        // lane l reads tile j0 - l; tiles before the first count as a zero prefix
+        const int64_t j = j0 - lane;
+        uint64_t w = (j >= 0) ? (uint64_t)st[j] : (uint64_t)kStP;
+        int64_t spins = 0;
+        while ((w >> 62) == 0 && spins < spin_limit) {
+          w = st[j];
+          spins++;
+        }
+        if (__any_sync(0xffffffffu, (w >> 62) == 0)) {  // an earlier tile never published
+          timed_out = true;
+          break;
+        }
+        const unsigned pmask = __ballot_sync(0xffffffffu, (w & kStP) != 0);
+        const int first = pmask ? __ffs(pmask) - 1 : 32;  // nearest inclusive prefix
+        int64_t val = (lane <= first) ? (int64_t)(w & kStVal) : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+        excl += val;
+        if (first < 32) break;
+        j0 -= 32;
+      }
+      if (lane == 0) {
+        if (timed_out) atomicOr(&dsc->err, ERR_TIMEOUT);
+        if (t > 0) st[t] = kStP | (uint64_t)(excl + tot);
+        s_excl = excl;
+        if (t == nt - 1) out[N] = excl + tot;
+      }
+    }
+    __syncthreads();
+    store_items(out, base, N, s_excl + ex, v);
+  }
+  // the last block to finish clears the status words and the counters
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) ? 1 : 0;
   }
   __syncthreads();
-  int64_t ex = sm[wid] + inc - x;
-  if (threadIdx.x < nb) bsum[threadIdx.x] = ex;
-  if (threadIdx.x == 0) out[load_n(n_host, n_dev)] = sm[32];
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_scan_down(const T* __restrict__ in, int64_t* __restrict__ out,
-                                                      int64_t n_host, const int64_t* n_dev,
-                                                      const int64_t* __restrict__ bsum) {
-  __shared__ int64_t sm[kBlock / 32 + 1];
-  const int64_t N = load_n(n_host, n_dev);
-  const int64_t chunk = chunk_of(N, gridDim.x);
-  const int64_t b0 = (int64_t)blockIdx.x * chunk;
-  const int64_t b1 = min(N, b0 + chunk);
-  int64_t run = bsum[blockIdx.x];
-  for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
-    int64_t base = t0 + (int64_t)threadIdx.x * kItems;
-    int64_t v[kItems];
-    int64_t s = 0;
-#pragma unroll
-    for (int i = 0; i < kItems; i++) {
-      v[i] = (base + i < b1) ? (int64_t)in[base + i] : 0;
-      s += v[i];
+  if (s_last) {
+    for (int64_t i = threadIdx.x; i < nt; i += kBlock) status[i] = 0;
+    if (threadIdx.x == 0) {
+      ctr[0] = 0;
+      ctr[1] = 0;
+      if (nt == 0) out[N] = 0;
     }
-    int64_t tot;
-    int64_t ex = block_excl_scan(s, sm, &tot) + run;
-#pragma unroll
-    for (int i = 0; i < kItems; i++) {
-      if (base + i < b1) out[base + i] = ex;
-      ex += v[i];
-    }
-    run += tot;
   }
 }
 
 template <typename T>
 int scan_impl(Handle& h, const T* in, int64_t* out, int64_t n_host, const int64_t* n_dev, int64_t n_max) {
   if (n_max <= 0) n_max = 1;
-  int nb = (int)std::min<int64_t>(kScanBlocksMax, (n_max + kTile - 1) / kTile);
-  if (nb < 1) nb = 1;
   ++h.launches;
-  k_scan_reduce<T><<<nb, kBlock, 0, h.stream>>>(in, n_host, n_dev, h.blk_b);
-  ++h.launches;
-  k_scan_top<<<1, 1024, 0, h.stream>>>(h.blk_b, nb, n_host, n_dev, out);
-  ++h.launches;
-  k_scan_down<T><<<nb, kBlock, 0, h.stream>>>(in, out, n_host, n_dev, h.blk_b);
+  if (n_max <= kScanSmall) {
+    k_scan_small<T><<<1, kBlock, 0, h.stream>>>(in, out, n_host, n_dev);
+  } else {
+    const int64_t tiles = (n_max + kTile - 1) / kTile;
+    if (tiles > h.scan_tiles_cap || tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized at init / growth
+    k_scan_onepass<T><<<(int)tiles, kBlock, 0, h.stream>>>(in, out, n_host, n_dev, h.scan_status, h.scan_ctr,
+                                                           h.opt.spin_limit, h.dsc);
+  }
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

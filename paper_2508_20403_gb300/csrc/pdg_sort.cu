@@ -13,9 +13,10 @@
 // One-sweep LSD: one kernel histograms every digit position of a key set at
 // once, one kernel scans those histograms, and each pass is then a single
 // scatter kernel.  Its blocks take tiles in order from an atomic counter,
-// rank the tile's digits stably (warp match + per-warp counters), publish the
+// rank the tile's digits stably (ballot peer masks + per-warp counters), publish the
 // tile's digit counts and obtain the counts of all earlier tiles by looking
-// back through published values ("decoupled look-back").  Every wait on an
+// back through published values ("decoupled look-back"), a window of tiles
+// per memory round trip.  Every wait on an
 // earlier tile is bounded (spin_limit); a timeout sets an error bit and the
 // recovery reports PDG_E_TIMEOUT instead of hanging.  A digit shared by all
 // keys is detected from the histogram and its pass moves nothing.  Sizes are
@@ -27,14 +28,21 @@ namespace pdg {
 namespace {
 
 constexpr int kRdxBins = 256;
-constexpr int kRdxWarps = kBlock / 32;
-constexpr int kRdxPerWarp = kTile / kRdxWarps;  // 256 items, 8 rounds of 32
+// Scatter tiles are 512 threads x 8 keys = 4096 keys: tiles this large keep
+// the look-back short at the candidate counts of a recovery (10^5 .. 10^7
+// keys) while a pass still spreads over many SMs.
+constexpr int kOsThreads = 512;
+constexpr int kOsItems = 8;
+constexpr int kOsTile = kOsThreads * kOsItems;
+constexpr int kRdxWarps = kOsThreads / 32;
+constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // 256 items, 8 rounds of 32
 constexpr int kMaxDigits = 8;
+constexpr int kLookWin = 16;  // look-back words fetched per round trip
 constexpr uint32_t kFlagA = 1u << 30;  // tile aggregate published
 constexpr uint32_t kFlagP = 2u << 30;  // inclusive prefix published
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 
-__device__ __forceinline__ int64_t tiles_of(int64_t N) { return (N + kTile - 1) / kTile; }
+__device__ __forceinline__ int64_t tiles_of(int64_t N) { return (N + kOsTile - 1) / kOsTile; }
 
 // Histograms of `ndig` digit positions (starting at bit `shift0`) of the keys
 // in the current buffer: ghist[d][bin].
@@ -81,13 +89,23 @@ __global__ void k_os_scan(uint32_t* __restrict__ ghist, int ndig, const DevScala
   if (lane == 0) skip[d] = uniform ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(kBlock) k_os_scatter(const uint64_t* k0, const uint64_t* k1, const int32_t* v0,
+// Dynamic shared memory of one scatter block: the tile's keys and values
+// bucketed by digit, the per-warp digit counters and the per-digit offsets.
+constexpr size_t kOsSmem = (size_t)kOsTile * (sizeof(uint64_t) + sizeof(int32_t)) +
+                           sizeof(uint32_t) * ((size_t)kRdxWarps * kRdxBins + 2 * kRdxBins + 32);
+
+__global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0, const uint64_t* k1, const int32_t* v0,
                                                        const int32_t* v1, uint64_t* ko0, uint64_t* ko1, int32_t* vo0,
                                                        int32_t* vo1, DevScalars* dsc, int shift,
                                                        const uint32_t* __restrict__ goff, const int32_t* skip,
                                                        uint32_t* status, uint32_t* counters, int64_t spin_limit) {
-  __shared__ uint32_t wcnt[kRdxWarps][kRdxBins];
-  __shared__ uint32_t tile_base[kRdxBins];
+  extern __shared__ __align__(16) unsigned char os_smem[];
+  uint64_t* skey = reinterpret_cast<uint64_t*>(os_smem);                        // [kOsTile]
+  int32_t* sval = reinterpret_cast<int32_t*>(skey + kOsTile);                   // [kOsTile]
+  uint32_t(*wcnt)[kRdxBins] = reinterpret_cast<uint32_t(*)[kRdxBins]>(sval + kOsTile);  // [warps][256]
+  uint32_t* s_loff = &wcnt[kRdxWarps][0];  // tile-local start of each digit's bucket
+  uint32_t* s_base = s_loff + kRdxBins;    // output position of bucket slot 0, per digit
+  uint32_t* s_wsum = s_base + kRdxBins;    // per-warp totals of the digit scan
   __shared__ int64_t s_tile;
   const int64_t N = dsc->n_cand;
   const int sel = dsc->radix_sel;
@@ -103,72 +121,115 @@ __global__ void __launch_bounds__(kBlock) k_os_scatter(const uint64_t* k0, const
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&counters[0], 1u);  // tiles in launch order
     __syncthreads();
     const int64_t t = s_tile;
-    if (t < T) {
+    if (t < T) {  // uniform over the block
+      const int64_t t0 = t * kOsTile;
+      const int tile_n = (int)(N - t0 < kOsTile ? N - t0 : kOsTile);
       for (int d = lane; d < kRdxBins; d += 32) wcnt[w][d] = 0;
       __syncwarp();
-      uint64_t kk[kItems];
-      int32_t vv[kItems];
-      int dig[kItems];
-      uint32_t rnk[kItems];
-      const int64_t base = t * kTile + (int64_t)w * kRdxPerWarp;
+      uint64_t kk[kOsItems];
+      int32_t vv[kOsItems];
+      uint32_t rnk[kOsItems];
+      const int64_t base = t0 + (int64_t)w * kRdxPerWarp;
+      // all loads first (independent, in flight together), then the ranking
 #pragma unroll
-      for (int i = 0; i < kItems; i++) {
+      for (int i = 0; i < kOsItems; i++) {
         const int64_t idx = base + i * 32 + lane;
-        const bool valid = idx < N;
-        kk[i] = valid ? keys[idx] : 0;
-        vv[i] = valid ? vals[idx] : 0;
-        dig[i] = valid ? (int)((kk[i] >> shift) & 0xff) : kRdxBins;
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
-        rnk[i] = valid ? wcnt[w][dig[i]] + __popc(peers & lt) : 0;
+        kk[i] = idx < N ? keys[idx] : 0;
+        vv[i] = idx < N ? vals[idx] : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < kOsItems; i++) {
+        const bool valid = base + i * 32 + lane < N;
+        const int dig = (int)((kk[i] >> shift) & 0xff);
+        // lanes holding the same digit: one ballot per digit bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+          const bool bit = (dig >> b) & 1;
+          const unsigned bb = __ballot_sync(0xffffffffu, bit);
+          peers &= bit ? bb : ~bb;
+        }
+        rnk[i] = valid ? wcnt[w][dig] + __popc(peers & lt) : 0;
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wcnt[w][dig[i]] += __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) wcnt[w][dig] += __popc(peers);
         __syncwarp();
       }
       __syncthreads();
-      // thread d: the tile's count of digit d, published, then the look-back
-      {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
+      // thread d < 256: the tile's count of digit d (published at once), the
+      // per-warp offsets inside the digit, and the scan over digits
+      const int d = threadIdx.x;
+      uint32_t run = 0, incl = 0;
+      volatile uint32_t* st = status;
+      if (d < kRdxBins) {
         for (int ww = 0; ww < kRdxWarps; ww++) {
           const uint32_t c = wcnt[ww][d];
           wcnt[ww][d] = run;
           run += c;
         }
-        volatile uint32_t* st = status;
-        if (t == 0) {
-          st[d] = kFlagP | run;
-          tile_base[d] = goff[d];
-        } else {
-          st[t * kRdxBins + d] = kFlagA | run;
-          uint32_t excl = 0;
-          for (int64_t j = t - 1; j >= 0; j--) {
-            uint32_t v = st[j * kRdxBins + d];
-            int64_t spins = 0;
-            while ((v & ~kCountMask) == 0 && spins < spin_limit) {
-              v = st[j * kRdxBins + d];
-              spins++;
+        st[t * kRdxBins + d] = (t == 0 ? kFlagP : kFlagA) | run;
+        incl = warp_incl_scan(run);
+        if (lane == 31) s_wsum[w] = incl;
+      }
+      __syncthreads();
+      if (d < kRdxBins) {
+        uint32_t before = 0;
+        for (int ww = 0; ww < w; ww++) before += s_wsum[ww];
+        s_loff[d] = before + incl - run;
+      }
+      __syncthreads();
+      // bucket the tile by digit in shared memory (stable: warp order, then rank)
+#pragma unroll
+      for (int i = 0; i < kOsItems; i++) {
+        if (base + i * 32 + lane < N) {
+          const int dig = (int)((kk[i] >> shift) & 0xff);
+          const uint32_t lp = s_loff[dig] + wcnt[w][dig] + rnk[i];
+          skey[lp] = kk[i];
+          sval[lp] = vv[i];
+        }
+      }
+      // look back kLookWin tiles per round trip: the window's words are
+      // loaded together, then consumed newest first until a prefix
+      if (d < kRdxBins) {
+        uint32_t excl = 0;
+        if (t > 0) {
+          bool done = false;
+          for (int64_t j0 = t - 1; j0 >= 0 && !done; j0 -= kLookWin) {
+            uint32_t win[kLookWin];
+#pragma unroll
+            for (int q = 0; q < kLookWin; q++) win[q] = (j0 - q >= 0) ? st[(j0 - q) * kRdxBins + d] : 0u;
+#pragma unroll
+            for (int q = 0; q < kLookWin; q++) {
+              const int64_t j = j0 - q;
+              if (!done && j >= 0) {
+                uint32_t v = win[q];
+                int64_t spins = 0;
+                while ((v & ~kCountMask) == 0 && spins < spin_limit) {
+                  v = st[j * kRdxBins + d];
+                  spins++;
+                }
+                if ((v & ~kCountMask) == 0) {  // an earlier tile never published: give up, report
+                  atomicOr(&dsc->err, ERR_TIMEOUT);
+                  done = true;
+                } else {
+                  excl += v & kCountMask;
+                  if (v & kFlagP) done = true;
+                }
+              }
             }
-            if ((v & ~kCountMask) == 0) {  // an earlier tile never published: give up, report
-              atomicOr(&dsc->err, ERR_TIMEOUT);
-              break;
-            }
-            excl += v & kCountMask;
-            if (v & kFlagP) break;
           }
           __threadfence();
           st[t * kRdxBins + d] = kFlagP | (excl + run);
-          tile_base[d] = goff[d] + excl;
         }
+        s_base[d] = goff[d] + excl - s_loff[d];  // modulo 2^32; the sums below are < N
       }
       __syncthreads();
-#pragma unroll
-      for (int i = 0; i < kItems; i++) {
-        if (dig[i] < kRdxBins) {
-          const int64_t pos = (int64_t)tile_base[dig[i]] + wcnt[w][dig[i]] + rnk[i];
-          if (pos < N) {
-            ko[pos] = kk[i];
-            vo[pos] = vv[i];
-          }
+      // consecutive threads write consecutive slots of each digit's run
+      for (int j = threadIdx.x; j < tile_n; j += kOsThreads) {
+        const uint64_t k = skey[j];
+        const uint32_t pos = s_base[(k >> shift) & 0xff] + (uint32_t)j;
+        if (pos < (uint64_t)N) {
+          ko[pos] = k;
+          vo[pos] = sval[j];
         }
       }
     }
@@ -180,6 +241,15 @@ __global__ void __launch_bounds__(kBlock) k_os_scatter(const uint64_t* k0, const
     if (atomicAdd(&counters[1], 1u) == gridDim.x - 1 && moves) dsc->radix_sel = sel ^ 1;
   }
 }
+
+}  // namespace
+
+int sort_setup() {
+  PDG_CUDA(cudaFuncSetAttribute(k_os_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsSmem));
+  return PDG_OK;
+}
+
+namespace {
 
 // keys := graph index of the candidate held as value (keeps graphs contiguous)
 __global__ void k_key_graph(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1, const int32_t* __restrict__ v0,
@@ -222,7 +292,7 @@ __global__ void k_copy_vals(const int32_t* __restrict__ v0, const int32_t* __res
 static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
   if (ndig <= 0) return PDG_OK;  // a single possible key value: already sorted
   const int grid_hist = h.num_sms * 2;
-  const int64_t tiles_max = (h.Rcap + kTile - 1) / kTile;
+  const int64_t tiles_max = (h.Rcap + kOsTile - 1) / kOsTile;
   uint32_t* ghist = h.radix_hist;                // [8][256], kept zero between uses
   uint32_t* goff = h.radix_hist + 8 * kRdxBins;  // [8][256]
   int32_t* skip = reinterpret_cast<int32_t*>(h.radix_hist + 16 * kRdxBins) + pass0;
@@ -235,7 +305,7 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
     uint32_t* status = h.radix_status + (int64_t)p * tiles_max * kRdxBins;
     uint32_t* counters = h.radix_counters + 2 * p;
     ++h.launches;
-    k_os_scatter<<<(int)std::max<int64_t>(tiles_max, 1), kBlock, 0, h.stream>>>(
+    k_os_scatter<<<(int)std::max<int64_t>(tiles_max, 1), kOsThreads, kOsSmem, h.stream>>>(
         h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.dsc, shift0 + 8 * d,
         goff + d * kRdxBins, skip + d, status, counters, h.opt.spin_limit);
   }
@@ -245,7 +315,7 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
 
 int step_sort(Handle& h) {
   const int grid = h.num_sms * 4;
-  const int64_t tiles_max = (h.Rcap + kTile - 1) / kTile;
+  const int64_t tiles_max = (h.Rcap + kOsTile - 1) / kOsTile;
   // look-back status and tile counters start clean for every pass
   PDG_CUDA(cudaMemsetAsync(h.radix_status, 0, sizeof(uint32_t) * (size_t)kRadixPassesMax * tiles_max * kRdxBins,
                            h.stream));
