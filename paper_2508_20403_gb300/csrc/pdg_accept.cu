@@ -163,68 +163,136 @@ __global__ void __launch_bounds__(kBlock) k_build_records(
   }
 }
 
-__global__ void k_seg_flags(const int32_t* __restrict__ rec_lca, const DevScalars* __restrict__ dsc,
-                            int32_t* __restrict__ flags) {
+// Subtask boundaries: the positions whose LCA differs from the previous
+// position's, in order (single pass: tiles in ticket order, block scan plus
+// decoupled look-back); seg_begin[n_seg] = N closes the last segment.
+__global__ void __launch_bounds__(kLbThreads) k_seg_starts(const int32_t* __restrict__ rec_lca, DevScalars* dsc,
+                                                          int32_t* __restrict__ seg_begin, uint64_t* status,
+                                                          uint32_t* ctr, int64_t spin_limit) {
+  __shared__ int64_t sm[kLbThreads / 32 + 1];
+  __shared__ int64_t s_tile, s_excl;
+  __shared__ int s_last;
   const int64_t N = dsc->n_cand;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
-    flags[s] = (s == 0 || rec_lca[s] != rec_lca[s - 1]) ? 1 : 0;
-}
-
-// out[scan[i]] = i for flagged i; *count_out = number flagged
-__global__ void k_scatter_idx(const int32_t* __restrict__ flags, const int64_t* __restrict__ scan,
-                              const int64_t* __restrict__ n_dev, int32_t* __restrict__ out,
-                              int64_t* __restrict__ count_out, int64_t tail_value_at_count) {
-  const int64_t N = *n_dev;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    if (flags[i]) out[scan[i]] = (int32_t)i;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int64_t cnt = scan[N];
-    if (count_out) *count_out = cnt;
-    if (tail_value_at_count >= 0) out[cnt] = (int32_t)N;  // sentinel end of the last segment
+  const int64_t nt = (N + kLbTile - 1) / kLbTile;
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&ctr[0], 1u);
+  __syncthreads();
+  const int64_t t = s_tile;
+  if (t < nt) {
+    const int64_t base = t * kLbTile + (int64_t)threadIdx.x * kItems;
+    uint32_t head = 0;
+    int32_t prev = (base > 0 && base < N) ? rec_lca[base - 1] : -1;
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+      const int64_t p = base + i;
+      if (p < N) {
+        const int32_t l = rec_lca[p];
+        if (p == 0 || l != prev) head |= 1u << i;
+        prev = l;
+      }
+    }
+    int64_t tile_tot;
+    const int64_t local = block_excl_scan_n<kLbThreads>((int64_t)__popc(head), sm, &tile_tot);
+    if (threadIdx.x < 32) {
+      bool timed_out;
+      const int64_t excl = warp_lookback(status, t, tile_tot, spin_limit, &timed_out);
+      if (threadIdx.x == 0) {
+        if (timed_out) atomicOr(&dsc->err, ERR_TIMEOUT);
+        s_excl = excl;
+        if (t == nt - 1) {
+          dsc->n_seg = excl + tile_tot;
+          seg_begin[excl + tile_tot] = (int32_t)N;
+        }
+      }
+    }
+    __syncthreads();
+    int64_t pos = s_excl + local;
+#pragma unroll
+    for (int i = 0; i < kItems; i++)
+      if (head & (1u << i)) seg_begin[pos++] = (int32_t)(base + i);
+  }
+  // the last block to finish clears the look-back words and the counters
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int64_t i = threadIdx.x; i < nt; i += kLbThreads) status[i] = 0;
+    if (threadIdx.x == 0) {
+      ctr[0] = 0;
+      ctr[1] = 0;
+      if (nt == 0) {
+        dsc->n_seg = 0;
+        seg_begin[0] = 0;
+      }
+    }
   }
 }
 
-// per segment: tier flags (warp tier / cooperative tier) and statistics
+// Appends the lanes with `pred` to list[*count ...] (one atomic per warp; the
+// list keeps the lanes' order within a warp, not across warps).
+__device__ __forceinline__ void warp_append(bool pred, int32_t value, int32_t* __restrict__ list, int64_t* count) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(0xffffffffu, pred);
+  if (!b) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd((unsigned long long*)count, (unsigned long long)__popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) list[base + __popc(b & ((1u << lane) - 1))] = value;
+}
+
+// Per subtask: the warp tier (2..warp_max candidates) and the cooperative
+// tier (larger) lists, and the largest subtask.
 __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
-                           int32_t* __restrict__ fw, int32_t* __restrict__ fb) {
+                           int32_t* __restrict__ warp_seg, int32_t* __restrict__ big_seg) {
   const int64_t S = dsc->n_seg;
+  const int lane = threadIdx.x & 31;
   int64_t mx = 0;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < S; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sz = seg_begin[q + 1] - seg_begin[q];
-    fw[q] = (sz >= 2 && sz <= warp_max) ? 1 : 0;
-    fb[q] = (sz > warp_max) ? 1 : 0;
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); q0 < S;
+       q0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = q0 + lane;
+    const int64_t sz = (q < S) ? seg_begin[q + 1] - seg_begin[q] : 0;
+    warp_append(sz >= 2 && sz <= warp_max, (int32_t)q, warp_seg, &dsc->n_warp_seg);
+    warp_append(sz > warp_max, (int32_t)q, big_seg, &dsc->n_big_seg);
     mx = max(mx, sz);
   }
   mx = __reduce_max_sync(0xffffffffu, (unsigned)min(mx, (int64_t)0x7fffffff));
-  if ((threadIdx.x & 31) == 0 && mx) atomicMax((unsigned long long*)&dsc->max_seg, (unsigned long long)mx);
+  if (lane == 0 && mx) atomicMax((unsigned long long*)&dsc->max_seg, (unsigned long long)mx);
 }
 
-// per position: singletons are recovered; cooperative-tier positions flagged
+// Per position: singletons are recovered; cooperative-tier positions are
+// listed (big_pos) and marked undecided.
 __global__ void k_pos_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
                            const int32_t* __restrict__ rec_rank, const uint8_t* __restrict__ rec_b,
-                           uint8_t* __restrict__ acc_flag, int32_t* __restrict__ fbig, uint8_t* __restrict__ state) {
+                           uint8_t* __restrict__ acc_flag, int32_t* __restrict__ big_pos, uint8_t* __restrict__ state) {
   const int64_t N = dsc->n_cand;
   const int32_t S = (int32_t)dsc->n_seg;
+  const int lane = threadIdx.x & 31;
   unsigned long long regs = 0;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-    int32_t lo = 0, hi = S;  // segment q with seg_begin[q] <= s < seg_begin[q+1]
-    while (hi - lo > 1) {
-      int32_t mid = (lo + hi) >> 1;
-      if (seg_begin[mid] <= s) lo = mid; else hi = mid;
+  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); s0 < N;
+       s0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = s0 + lane;
+    bool big = false;
+    if (s < N) {
+      int32_t lo = 0, hi = S;  // segment q with seg_begin[q] <= s < seg_begin[q+1]
+      while (hi - lo > 1) {
+        int32_t mid = (lo + hi) >> 1;
+        if (seg_begin[mid] <= s) lo = mid; else hi = mid;
+      }
+      const int64_t sz = seg_begin[lo + 1] - seg_begin[lo];
+      if (sz == 1) acc_flag[rec_rank[s]] = 1;
+      else if (sz > warp_max) {
+        big = true;
+        state[s] = ST_UNDECIDED;
+        const unsigned b = rec_b[s];
+        if (b > 0) regs += (unsigned long long)(b + 1) * (b + 1);
+      }
     }
-    const int64_t sz = seg_begin[lo + 1] - seg_begin[lo];
-    int32_t big = 0;
-    if (sz == 1) acc_flag[rec_rank[s]] = 1;
-    else if (sz > warp_max) {
-      big = 1;
-      state[s] = ST_UNDECIDED;
-      const unsigned b = rec_b[s];
-      if (b > 0) regs += (unsigned long long)(b + 1) * (b + 1);
-    }
-    fbig[s] = big;
+    warp_append(big, (int32_t)s, big_pos, &dsc->n_big);
   }
   for (int o = 16; o; o >>= 1) regs += __shfl_down_sync(0xffffffffu, regs, o);
-  if ((threadIdx.x & 31) == 0 && regs) atomicAdd((unsigned long long*)&dsc->big_regs, regs);
+  if (lane == 0 && regs) atomicAdd((unsigned long long*)&dsc->big_regs, regs);
 }
 
 // ------------------------------------------------------------------ warp tier
@@ -295,10 +363,18 @@ struct CoopArgs {
   int64_t* n_flag;     // flagged pairs (exact blocks handed out)
   int64_t xcap;        // exact blocks available
   int64_t* und_count;  // per round: candidates still waiting
+  uint32_t* flagbits;  // one bit per pair slot: the pair has an exact block
+  int32_t* und_list;   // positions left undecided by phase A (any order)
+  int64_t* n_und;      // their number
 };
 
-__global__ void k_coop_clear(PairSlot* __restrict__ tab, DevScalars* dsc, int64_t table_cap,
-                             uint64_t* __restrict__ cap_out, int64_t* __restrict__ n_flag) {
+__device__ __forceinline__ bool slot_flagged(const uint32_t* __restrict__ bits, int32_t slot) {
+  return (bits[slot >> 5] >> (slot & 31)) & 1u;
+}
+
+__global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ flagbits, DevScalars* dsc,
+                             int64_t table_cap, uint64_t* __restrict__ cap_out, int64_t* __restrict__ n_flag,
+                             int64_t* __restrict__ n_und) {
   // effective capacity: twice the registrations (load <= 0.5), at least 1024
   int64_t want = 2 * dsc->big_regs;
   if (want < 1024) want = 1024;
@@ -309,12 +385,16 @@ __global__ void k_coop_clear(PairSlot* __restrict__ tab, DevScalars* dsc, int64_
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *cap_out = (uint64_t)want;
     *n_flag = 0;
+    *n_und = 0;
   }
   if (dsc->n_big == 0) return;
   uint4* t4 = reinterpret_cast<uint4*>(tab);
   const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < want; i += (int64_t)gridDim.x * blockDim.x)
     t4[i] = ones;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= want / 32;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flagbits[i] = 0;
 }
 
 // Phase A1: register every (anc_j(u), anc_j'(v)), j, j' <= beta*, with its rank.
@@ -461,12 +541,21 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
           e[w].acc = kNone;
           e[w].und = ~0ull;
         }
+        atomicOr(&a.flagbits[slt >> 5], 1u << (slt & 31));
       }
       xi++;
     }
     if (valid) {
       a.state[s] = pm ? ST_UNDECIDED : ST_ACCEPTED_NEW;
       cons += pm ? 1 : 0;
+    }
+    // undecided positions join the list that the rounds of phase B walk
+    const unsigned ub = __ballot_sync(0xffffffffu, valid && pm);
+    if (ub) {
+      int ubase = 0;
+      if (lane == 0) ubase = (int)atomicAdd((unsigned long long*)a.n_und, (unsigned long long)__popc(ub));
+      ubase = __shfl_sync(0xffffffffu, ubase, 0);
+      if (valid && pm) a.und_list[ubase + __popc(ub & ((1u << lane) - 1))] = s;
     }
   }
   for (int o = 16; o; o >>= 1) cons += __shfl_down_sync(0xffffffffu, cons, o);
@@ -475,34 +564,52 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
 
 // exact registration of one candidate's flagged pairs (its pair slots, their
 // exact blocks and the updates each issued as one batch)
-template <int C>
-__device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, const Rec& r, bool accepted,
+//
+// FIRST: reg_slot holds pair slots (round 1); an undecided candidate then
+// overwrites them with the exact-block indices (all-ones: none), which later
+// rounds and the finisher read directly.
+template <int C, bool FIRST>
+__device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int b, int32_t rank, bool accepted,
                                                uint64_t und_val) {
-  if (r.b == 0) return;  // never registered (matches only itself)
+  if (b == 0) return;  // never registered (matches only itself)
   constexpr int NP = (C + 1) * (C + 1);
   int32_t sl[NP];
   uint32_t xi[NP];
 #pragma unroll
   for (int t = 0; t < NP; t++) {
     const int j = t / (C + 1), jp = t % (C + 1);
-    sl[t] = (j <= r.b && jp <= r.b) ? a.reg_slot[(int64_t)s * 16 + j * 4 + jp] : -1;
+    sl[t] = (j <= b && jp <= b) ? a.reg_slot[(int64_t)s * 16 + j * 4 + jp] : -1;
   }
+  if (FIRST) {
 #pragma unroll
-  for (int t = 0; t < NP; t++) xi[t] = sl[t] >= 0 ? a.ptab[sl[t]].xidx : kNone;
+    for (int t = 0; t < NP; t++)
+      xi[t] = (sl[t] >= 0 && slot_flagged(a.flagbits, sl[t])) ? a.ptab[sl[t]].xidx : kNone;
+    if (!accepted) {
+#pragma unroll
+      for (int t = 0; t < NP; t++) {
+        const int j = t / (C + 1), jp = t % (C + 1);
+        if (j <= b && jp <= b) a.reg_slot[(int64_t)s * 16 + j * 4 + jp] = (int32_t)xi[t];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < NP; t++) xi[t] = (uint32_t)sl[t];
+  }
 #pragma unroll
   for (int t = 0; t < NP; t++) {
     if (xi[t] == kNone) continue;
     const int j = t / (C + 1), jp = t % (C + 1);
     ExactEnt* e = a.xtab + (int64_t)xi[t] * 16 + j * 4 + jp;
-    if (accepted) atomicMin(&e->acc, (uint32_t)r.rank);
+    if (accepted) atomicMin(&e->acc, (uint32_t)rank);
     else atomicMin(&e->und, (unsigned long long)und_val);
   }
 }
 
 // exact probes: 2 = rejected, 1 = must wait, 0 = free of earlier markers.
 // The pair slots of the flagged probes were saved by phase A2 (pslot); the
-// entries one flagged probe may read are loaded together.
-template <int C, bool WITH_UND>
+// first round replaces them by the exact-block indices.  The entries one
+// flagged probe may read are loaded together.
+template <int C, bool WITH_UND, bool FIRST>
 __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const Rec& r, uint32_t pm, uint64_t tag) {
   int res = 0;
   uint32_t xis[2][C + 1][C + 1];
@@ -513,8 +620,20 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
 #pragma unroll
       for (int ip = 0; ip <= C; ip++) {
         const int bit = o * 16 + i * 4 + ip;
-        xis[o][i][ip] = (pm & (1u << bit)) ? a.ptab[a.pslot[(int64_t)s * 32 + bit]].xidx : kNone;
+        const int32_t v = (pm & (1u << bit)) ? a.pslot[(int64_t)s * 32 + bit] : -1;
+        xis[o][i][ip] = (FIRST && v >= 0) ? a.ptab[v].xidx : (uint32_t)v;
       }
+  if (FIRST) {
+#pragma unroll
+    for (int o = 0; o < 2; o++)
+#pragma unroll
+      for (int i = 0; i <= C; i++)
+#pragma unroll
+        for (int ip = 0; ip <= C; ip++) {
+          const int bit = o * 16 + i * 4 + ip;
+          if (pm & (1u << bit)) a.pslot[(int64_t)s * 32 + bit] = (int32_t)xis[o][i][ip];
+        }
+  }
 #pragma unroll
   for (int o = 0; o < 2; o++) {
     const int dx = o ? r.dv : r.du, dy = o ? r.du : r.dv;
@@ -553,19 +672,31 @@ template <int C>
 __global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalars* dsc, int round) {
   if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
-  const int64_t nb = dsc->n_big;
+  // round 1 also registers the candidates phase A accepted; later rounds only
+  // touch the positions phase A left undecided
+  const int64_t nb = (round == 1) ? dsc->n_big : *a.n_und;
+  const int32_t* pos = (round == 1) ? a.big_pos : a.und_list;
   const uint64_t tag = und_tag(round);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t s = a.big_pos[q];
+    const int32_t s = pos[q];
     const uint8_t st = a.state[s];
     if (st != ST_UNDECIDED && st != ST_ACCEPTED_NEW) continue;
-    Rec r;
-    load_rec(a.ra, s, C, r);
-    if (st == ST_UNDECIDED) {
-      exact_register<C>(a, s, r, false, tag | (uint64_t)(uint32_t)r.rank);
+    const int b = a.ra.b[s];
+    const int32_t rank = a.ra.rank[s];
+    if (round == 1) {
+      if (st == ST_UNDECIDED) {
+        exact_register<C, true>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank);
+      } else {
+        exact_register<C, true>(a, s, b, rank, true, 0);
+        a.state[s] = ST_ACCEPTED;
+      }
     } else {
-      exact_register<C>(a, s, r, true, 0);
-      a.state[s] = ST_ACCEPTED;
+      if (st == ST_UNDECIDED) {
+        exact_register<C, false>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank);
+      } else {
+        exact_register<C, false>(a, s, b, rank, true, 0);
+        a.state[s] = ST_ACCEPTED;
+      }
     }
   }
 }
@@ -574,15 +705,16 @@ template <int C>
 __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* dsc, int round) {
   if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
-  const int64_t nb = dsc->n_big;
+  const int64_t nb = *a.n_und;
   const uint64_t tag = und_tag(round);
   unsigned long long waiting = 0;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t s = a.big_pos[q];
+    const int32_t s = a.und_list[q];
     if (a.state[s] != ST_UNDECIDED) continue;
     Rec r;
     load_rec(a.ra, s, C, r);
-    const int res = exact_probe<C, true>(a, s, r, a.pmask[s], tag);
+    const int res = (round == 1) ? exact_probe<C, true, true>(a, s, r, a.pmask[s], tag)
+                                 : exact_probe<C, true, false>(a, s, r, a.pmask[s], tag);
     if (res == 2) a.state[s] = ST_REJECTED;
     else if (res == 0) a.state[s] = ST_ACCEPTED_NEW;
     else waiting++;
@@ -605,11 +737,11 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
       if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
       Rec r;
       load_rec(a.ra, s, C, r);
-      if (st == ST_UNDECIDED && exact_probe<C, false>(a, s, r, a.pmask[s], 0) == 2) {
+      if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0) == 2) {
         a.state[s] = ST_REJECTED;
         continue;
       }
-      exact_register<C>(a, s, r, true, 0);
+      exact_register<C, false>(a, s, r.b, r.rank, true, 0);
       a.state[s] = ST_ACCEPTED;
     }
   }
@@ -632,11 +764,14 @@ int run_coop(Handle& h, const CoopArgs& a, int grid, int rounds) {
   k_pair_register<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
   ++h.launches;
   k_pair_probe<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
+  // round 1 registers every cooperative candidate; the rest of the rounds only
+  // walk the (shorter) list of candidates phase A left undecided
+  const int grid_und = std::max(1, h.num_sms * 2);
   for (int r = 1; r <= rounds; r++) {
     ++h.launches;
-    k_exact_register<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+    k_exact_register<C><<<r == 1 ? grid : grid_und, kBlock, 0, h.stream>>>(a, h.dsc, r);
     ++h.launches;
-    k_exact_probe<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, r);
+    k_exact_probe<C><<<grid_und, kBlock, 0, h.stream>>>(a, h.dsc, r);
   }
   ++h.launches;
   k_exact_finish<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.big_seg, h.seg_begin, rounds);
@@ -656,34 +791,18 @@ int step_accept(Handle& h, int c) {
                                                   h.P[h.p_final], h.parent, up1, h.n, c, h.dsc, cap, h.rec_u,
                                                   h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank,
                                                   h.rec_lca);
+  // subtask boundaries, tier lists, per-position tiers
+  const int64_t lb_tiles = (cap + kLbTile - 1) / kLbTile;
+  if (lb_tiles > h.scan_tiles_cap || lb_tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized with the buffers
   ++h.launches;
-  k_seg_flags<<<grid, kBlock, 0, h.stream>>>(h.rec_lca, h.dsc, h.flags);
-  PDG_CUDA(cudaGetLastError());
-  // segment starts -> seg_begin[0..n_seg], seg_begin[n_seg] = N
-  if ((st = scan_excl_i32(h, h.flags, h.scan_tmp, 0, &h.dsc->n_cand, cap))) return st;
+  k_seg_starts<<<(int)std::max<int64_t>(lb_tiles, 1), kLbThreads, 0, h.stream>>>(
+      h.rec_lca, h.dsc, h.seg_begin, h.scan_status, h.scan_ctr, h.opt.spin_limit);
   ++h.launches;
-  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(h.flags, h.scan_tmp, &h.dsc->n_cand, h.seg_begin, &h.dsc->n_seg, 1);
-  // tiers per segment
-  int32_t* fw = h.flags;              // reuse: n_seg <= N
-  int32_t* fb = h.flags + cap + 1;    // second half of the flag buffer
-  ++h.launches;
-  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, fw, fb);
-  PDG_CUDA(cudaGetLastError());
-  if ((st = scan_excl_i32(h, fw, h.scan_tmp, 0, &h.dsc->n_seg, cap))) return st;
-  ++h.launches;
-  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fw, h.scan_tmp, &h.dsc->n_seg, h.warp_seg, &h.dsc->n_warp_seg, -1);
-  if ((st = scan_excl_i32(h, fb, h.scan_tmp, 0, &h.dsc->n_seg, cap))) return st;
-  ++h.launches;
-  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fb, h.scan_tmp, &h.dsc->n_seg, h.big_seg, &h.dsc->n_big_seg, -1);
-  // per position: singletons, cooperative-tier membership
-  int32_t* fpos = h.flags;
+  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.warp_seg, h.big_seg);
   ++h.launches;
   k_pos_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.rec_rank, h.rec_b, h.acc_flag,
-                                            fpos, h.state);
+                                            h.big_pos, h.state);
   PDG_CUDA(cudaGetLastError());
-  if ((st = scan_excl_i32(h, fpos, h.scan_tmp, 0, &h.dsc->n_cand, cap))) return st;
-  ++h.launches;
-  k_scatter_idx<<<grid, kBlock, 0, h.stream>>>(fpos, h.scan_tmp, &h.dsc->n_cand, h.big_pos, &h.dsc->n_big, -1);
   const RecArrays ra{h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, cap};
   // warp tier
   ++h.launches;
@@ -693,12 +812,13 @@ int step_accept(Handle& h, int c) {
   uint64_t* d_cap = reinterpret_cast<uint64_t*>(h.blk_a + 9800);
   int64_t* n_flag = h.blk_a + 9801;
   int64_t* und_count = h.blk_a + 9850;  // [0 .. max_rounds], max_rounds <= 64
+  int64_t* n_und = h.blk_a + 9802;
   const int R = std::max(1, std::min(h.opt.max_rounds, 64));
   PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
   ++h.launches;
-  k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.dsc, h.table_cap, d_cap, n_flag);
-  const CoopArgs a{ra,     h.big_pos, h.state, h.pmask, h.reg_slot, h.pslot, h.ptab,
-                   h.xtab, d_cap,     n_flag,  h.xcap,  und_count};
+  k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.flagbits, h.dsc, h.table_cap, d_cap, n_flag, n_und);
+  const CoopArgs a{ra,        h.big_pos, h.state, h.pmask,    h.reg_slot, h.pslot, h.ptab, h.xtab,
+                   d_cap,     n_flag,    h.xcap,  und_count,  h.flagbits, h.und_list, n_und};
   switch (c) {
     case 0: st = run_coop<0>(h, a, grid, R); break;
     case 1: st = run_coop<1>(h, a, grid, R); break;

@@ -195,16 +195,15 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
   R = std::min<int64_t>(std::max<int64_t>(R, 1), Rmax);
   int st;
   if (R > h.Rcap) {
-    void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp, h.flags,
+    void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp,
                    h.radix_status, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
                    h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg,
-                   h.pmask, h.reg_slot, h.pslot};
+                   h.pmask, h.reg_slot, h.pslot, h.und_list};
     for (void* p : old) device_release(h, p);
     const int64_t tiles = (R + kTile - 1) / kTile;
     if ((st = alloc_n(h, &h.cand_idx, R)) || (st = alloc_n(h, &h.rk[0], R)) || (st = alloc_n(h, &h.rk[1], R)) ||
         (st = alloc_n(h, &h.rv[0], R)) || (st = alloc_n(h, &h.rv[1], R)) || (st = alloc_n(h, &h.rank_cand, R)) ||
         (st = alloc_n(h, &h.lsort_rank, R)) || (st = alloc_n(h, &h.scan_tmp, R + 1)) ||
-        (st = alloc_n(h, &h.flags, 2 * (R + 1))) ||
         (st = alloc_n(h, &h.radix_status, (int64_t)kRadixPassesMax * 256 * tiles)) ||
         (st = alloc_n(h, &h.rec_u, R)) ||
         (st = alloc_n(h, &h.rec_v, R)) || (st = alloc_n(h, &h.rec_anc, 2 * PDG_MAX_C * R)) ||
@@ -212,7 +211,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
         (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
         (st = alloc_n(h, &h.acc_flag, R)) || (st = alloc_n(h, &h.seg_begin, R + 1)) ||
         (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) ||
-        (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R)) ||
+        (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R)) || (st = alloc_n(h, &h.und_list, R)) ||
         (st = alloc_n(h, &h.pslot, 32 * R))) {
       h.Rcap = 0;
       return st;
@@ -229,8 +228,10 @@ int grow_tables(Handle& h, int64_t slots, int64_t xblocks) {
   slots = std::min<int64_t>(slots, (1ll << 32) - 1);  // slot indices are 32-bit on the device
   if (slots > h.table_cap) {
     device_release(h, h.ptab);
+    device_release(h, h.flagbits);
     h.ptab = nullptr;
-    if ((st = alloc_n(h, &h.ptab, slots))) {
+    h.flagbits = nullptr;
+    if ((st = alloc_n(h, &h.ptab, slots)) || (st = alloc_n(h, &h.flagbits, slots / 32 + 1))) {
       h.table_cap = 0;
       return st;
     }
@@ -441,7 +442,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       (st = alloc_n(h, &h.d_k, num_graphs)) || (st = alloc_n(h, &h.d_out_ptr, num_graphs + 1)) ||
       (st = alloc_n(h, &h.radix_dtot, 256)) || (st = alloc_n(h, &h.radix_hist, kRadixHistWords)) ||
       (st = alloc_n(h, &h.radix_counters, 2 * kRadixPassesMax)) ||
-      (st = ensure_scan_status(h, std::max<int64_t>(n, num_graphs) + 1)))
+      (st = ensure_scan_status(h, std::max<int64_t>(std::max<int64_t>(n, num_graphs), E) + 1)))
     return fail(st);
   HostStage& s = hp->stage;
   s.G = num_graphs;

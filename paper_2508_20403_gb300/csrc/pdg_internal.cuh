@@ -160,7 +160,6 @@ struct Handle {
   int32_t* rank_cand = nullptr;    // rank -> candidate index
   int32_t* lsort_rank = nullptr;   // position in (lca, rank) order -> rank
   int64_t* scan_tmp = nullptr;     // Rcap + 1
-  int32_t* flags = nullptr;        // Rcap + 1
   uint32_t* radix_hist = nullptr;      // [8][256] histograms, [8][256] offsets, skip flags (fixed size)
   uint32_t* radix_status = nullptr;    // look-back words: kRadixPassesMax * tiles * 256
   uint32_t* radix_counters = nullptr;  // per pass: tile ticket, blocks finished
@@ -191,6 +190,8 @@ struct Handle {
   uint32_t* pmask = nullptr;
   int32_t* reg_slot = nullptr;
   int32_t* pslot = nullptr;
+  uint32_t* flagbits = nullptr;  // one bit per pair slot: the pair was flagged (has an exact block)
+  int32_t* und_list = nullptr;    // positions left undecided by phase A
 
   // budget
   int32_t* gstat = nullptr;      // G
@@ -289,11 +290,81 @@ __device__ __forceinline__ T block_excl_scan(T x, T* smem, T* total) {
   return res;
 }
 
+// The same for blocks of NT threads (NT a multiple of 32, at most 1024);
+// smem must hold NT/32 + 1 values.
+template <int NT, typename T>
+__device__ __forceinline__ T block_excl_scan_n(T x, T* smem, T* total) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T inc = warp_incl_scan(x);
+  if (lane == 31) smem[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T s = (lane < NW) ? smem[lane] : T(0);
+    T si = warp_incl_scan(s);
+    if (lane < NW) smem[lane] = si - s;
+    if (lane == NW - 1) smem[NW] = si;
+  }
+  __syncthreads();
+  T res = smem[wid] + inc - x;
+  *total = smem[NW];
+  __syncthreads();
+  return res;
+}
+
+// Tiles of the single-pass (look-back) kernels: 1024 threads x kItems.
+constexpr int kLbThreads = 1024;
+constexpr int kLbTile = kLbThreads * kItems;
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T x, T* smem) {
   T tot;
   block_excl_scan(x, smem, &tot);
   return tot;
+}
+
+// Decoupled look-back of a single-pass tile scan (executed by one full warp).
+// status[t] holds kStA | tile sum once tile t is scanned and kStP | inclusive
+// prefix once its prefix is known (0 before).  Publishes tile t's sum,
+// collects the exclusive prefix of tile t -- lane l reads tile j0 - l, so 32
+// earlier tiles per memory round trip -- and publishes the inclusive prefix.
+// Every wait is bounded by spin_limit; *timed_out reports a wait that ran out.
+constexpr uint64_t kStA = 1ull << 62;          // tile sum published
+constexpr uint64_t kStP = 2ull << 62;          // inclusive prefix published
+constexpr uint64_t kStVal = (1ull << 62) - 1;  // value bits
+
+__device__ __forceinline__ int64_t warp_lookback(uint64_t* status, int64_t t, int64_t tot, int64_t spin_limit,
+                                                 bool* timed_out) {
+  const int lane = threadIdx.x & 31;
+  volatile uint64_t* st = status;
+  if (lane == 0) st[t] = (t == 0 ? kStP : kStA) | (uint64_t)tot;
+  int64_t excl = 0;
+  bool out = false;
+  for (int64_t j0 = t - 1; j0 >= 0;) {
+    // tiles before the first count as a zero prefix
+    const int64_t j = j0 - lane;
+    uint64_t w = (j >= 0) ? (uint64_t)st[j] : (uint64_t)kStP;
+    int64_t spins = 0;
+    while ((w >> 62) == 0 && spins < spin_limit) {
+      w = st[j];
+      spins++;
+    }
+    if (__any_sync(0xffffffffu, (w >> 62) == 0)) {  // an earlier tile never published
+      out = true;
+      break;
+    }
+    const unsigned pmask = __ballot_sync(0xffffffffu, (w & kStP) != 0);
+    const int first = pmask ? __ffs(pmask) - 1 : 32;  // nearest inclusive prefix
+    int64_t val = (lane <= first) ? (int64_t)(w & kStVal) : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+    excl += val;
+    if (first < 32) break;
+    j0 -= 32;
+  }
+  if (lane == 0 && t > 0) st[t] = kStP | (uint64_t)(excl + tot);
+  *timed_out = out;
+  return excl;
 }
 
 // ---------------------------------------------------------------- host side

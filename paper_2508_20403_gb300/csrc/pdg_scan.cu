@@ -18,9 +18,6 @@ namespace pdg {
 namespace {
 
 constexpr int64_t kScanSmall = 8 * kTile;
-constexpr uint64_t kStA = 1ull << 62;          // tile sum published
-constexpr uint64_t kStP = 2ull << 62;          // inclusive prefix published
-constexpr uint64_t kStVal = (1ull << 62) - 1;  // value bits
 
 __device__ __forceinline__ int64_t load_n(int64_t n_host, const int64_t* n_dev) {
   return n_dev ? *n_dev : n_host;
@@ -67,54 +64,29 @@ __global__ void __launch_bounds__(kBlock) k_scan_small(const T* __restrict__ in,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_scan_onepass(const T* __restrict__ in, int64_t* __restrict__ out,
-                                                         int64_t n_host, const int64_t* n_dev, uint64_t* status,
-                                                         uint32_t* ctr, int64_t spin_limit, DevScalars* dsc) {
-  __shared__ int64_t sm[kBlock / 32 + 1];
+__global__ void __launch_bounds__(kLbThreads) k_scan_onepass(const T* __restrict__ in, int64_t* __restrict__ out,
+                                                             int64_t n_host, const int64_t* n_dev, uint64_t* status,
+                                                             uint32_t* ctr, int64_t spin_limit, DevScalars* dsc) {
+  __shared__ int64_t sm[kLbThreads / 32 + 1];
   __shared__ int64_t s_tile, s_excl;
   __shared__ int s_last;
   const int64_t N = load_n(n_host, n_dev);
-  const int64_t nt = (N + kTile - 1) / kTile;
+  const int64_t nt = (N + kLbTile - 1) / kLbTile;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&ctr[0], 1u);  // tiles in launch order
   __syncthreads();
   const int64_t t = s_tile;
   if (t < nt) {
-    const int64_t base = t * kTile + (int64_t)threadIdx.x * kItems;
+    const int64_t base = t * kLbTile + (int64_t)threadIdx.x * kItems;
     int64_t v[kItems];
     const int64_t s = load_items(in, base, N, v);
     int64_t tot;
-    const int64_t ex = block_excl_scan(s, sm, &tot);
+    const int64_t ex = block_excl_scan_n<kLbThreads>(s, sm, &tot);
     if (threadIdx.x < 32) {
-      volatile uint64_t* st = status;
-      if (lane == 0) st[t] = (t == 0 ? kStP : kStA) | (uint64_t)tot;
-      int64_t excl = 0;
-      bool timed_out = false;
-      for (int64_t j0 = t - 1; j0 >= 0;) {
-        // lane l reads tile j0 - l; tiles before the first count as a zero prefix
-        const int64_t j = j0 - lane;
-        uint64_t w = (j >= 0) ? (uint64_t)st[j] : (uint64_t)kStP;
-        int64_t spins = 0;
-        while ((w >> 62) == 0 && spins < spin_limit) {
-          w = st[j];
-          spins++;
-        }
-        if (__any_sync(0xffffffffu, (w >> 62) == 0)) {  // an earlier tile never published
-          timed_out = true;
-          break;
-        }
-        const unsigned pmask = __ballot_sync(0xffffffffu, (w & kStP) != 0);
-        const int first = pmask ? __ffs(pmask) - 1 : 32;  // nearest inclusive prefix
-        int64_t val = (lane <= first) ? (int64_t)(w & kStVal) : 0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-        excl += val;
-        if (first < 32) break;
-        j0 -= 32;
-      }
+      bool timed_out;
+      const int64_t excl = warp_lookback(status, t, tot, spin_limit, &timed_out);
       if (lane == 0) {
         if (timed_out) atomicOr(&dsc->err, ERR_TIMEOUT);
-        if (t > 0) st[t] = kStP | (uint64_t)(excl + tot);
         s_excl = excl;
         if (t == nt - 1) out[N] = excl + tot;
       }
@@ -130,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) k_scan_onepass(const T* __restrict__ i
   }
   __syncthreads();
   if (s_last) {
-    for (int64_t i = threadIdx.x; i < nt; i += kBlock) status[i] = 0;
+    for (int64_t i = threadIdx.x; i < nt; i += kLbThreads) status[i] = 0;
     if (threadIdx.x == 0) {
       ctr[0] = 0;
       ctr[1] = 0;
@@ -146,10 +118,10 @@ int scan_impl(Handle& h, const T* in, int64_t* out, int64_t n_host, const int64_
   if (n_max <= kScanSmall) {
     k_scan_small<T><<<1, kBlock, 0, h.stream>>>(in, out, n_host, n_dev);
   } else {
-    const int64_t tiles = (n_max + kTile - 1) / kTile;
+    const int64_t tiles = (n_max + kLbTile - 1) / kLbTile;
     if (tiles > h.scan_tiles_cap || tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized at init / growth
-    k_scan_onepass<T><<<(int)tiles, kBlock, 0, h.stream>>>(in, out, n_host, n_dev, h.scan_status, h.scan_ctr,
-                                                           h.opt.spin_limit, h.dsc);
+    k_scan_onepass<T><<<(int)tiles, kLbThreads, 0, h.stream>>>(in, out, n_host, n_dev, h.scan_status, h.scan_ctr,
+                                                               h.opt.spin_limit, h.dsc);
   }
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;

@@ -19,10 +19,16 @@ namespace pdg {
 namespace {
 
 constexpr int kSelChunkBlocks = 1024;
+constexpr int kHistUnroll = 8;  // keys in flight per thread in the histogram passes
 
 __device__ __forceinline__ int64_t sel_chunk(int64_t E, int nb) {
   int64_t c = (E + nb - 1) / nb;
   return (c + kTile - 1) / kTile * kTile;
+}
+
+__device__ __forceinline__ void sel_count(uint32_t* h, uint64_t k, int lvl, int32_t b1) {
+  if (lvl == 0) atomicAdd(&h[k >> 52], 1u);
+  else if ((int32_t)(k >> 52) == b1) atomicAdd(&h[(k >> 40) & 0xfff], 1u);
 }
 
 // level 1 (lvl == 0): bins of key >> 52; level 2: bins of (key >> 40) & 0xfff
@@ -47,19 +53,21 @@ __global__ void __launch_bounds__(kBlock) k_sel_hist(const uint64_t* __restrict_
     if (s.take_all || r0 >= r1) continue;
     uint32_t* hg = hist + (int64_t)g * kSelBins;
     if (r1 - r0 < 256) {  // too short to amortise clearing and flushing 4096 shared bins
-      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const uint64_t k = key[i];
-        if (lvl == 0) atomicAdd(&hg[k >> 52], 1u);
-        else if ((int32_t)(k >> 52) == s.b1) atomicAdd(&hg[(k >> 40) & 0xfff], 1u);
-      }
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) sel_count(hg, key[i], lvl, s.b1);
       continue;
     }
     for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      const uint64_t k = key[i];
-      if (lvl == 0) atomicAdd(&sh[k >> 52], 1u);
-      else if ((int32_t)(k >> 52) == s.b1) atomicAdd(&sh[(k >> 40) & 0xfff], 1u);
+    for (int64_t i0 = r0; i0 < r1; i0 += (int64_t)kBlock * kHistUnroll) {
+      uint64_t k[kHistUnroll];
+#pragma unroll
+      for (int u = 0; u < kHistUnroll; u++) {
+        const int64_t i = i0 + u * kBlock + threadIdx.x;
+        k[u] = i < r1 ? key[i] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kHistUnroll; u++)
+        if (i0 + u * kBlock + threadIdx.x < r1) sel_count(sh, k[u], lvl, s.b1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kSelBins; i += blockDim.x)
@@ -68,17 +76,22 @@ __global__ void __launch_bounds__(kBlock) k_sel_hist(const uint64_t* __restrict_
   }
 }
 
-// One warp per graph: walk the bins from the top until `need` edges are
-// covered; clears the histogram for the next level.
-__global__ void k_sel_pick(uint32_t* __restrict__ hist, GraphSel* __restrict__ sel, const int64_t* __restrict__ off_ptr,
-                           int32_t G, int lvl, int64_t* __restrict__ count_out) {
-  const int lane = threadIdx.x & 31;
-  const int32_t g = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (g >= G) return;
+// One block per graph: walk the bins from the top until `need` edges are
+// covered; clears the histogram for the next level.  Thread t owns the 16
+// bins just below the 16 t highest ones.
+constexpr int kPickPer = kSelBins / kBlock;
+static_assert(kPickPer == 16, "pick layout");
+
+__global__ void __launch_bounds__(kBlock) k_sel_pick(uint32_t* __restrict__ hist, GraphSel* __restrict__ sel,
+                                                     const int64_t* __restrict__ off_ptr, int32_t G, int lvl,
+                                                     int64_t* __restrict__ count_out) {
+  __shared__ int64_t sm[kBlock / 32 + 1];
+  __shared__ int s_owner;
+  const int32_t g = blockIdx.x;
   GraphSel s = sel[g];
   uint32_t* hg = hist + (int64_t)g * kSelBins;
   if (s.take_all) {
-    if (lvl == 1 && lane == 0) {
+    if (lvl == 1 && threadIdx.x == 0) {
       s.count = off_ptr[g + 1] - off_ptr[g];
       s.thresh = 0;
       sel[g] = s;
@@ -87,93 +100,125 @@ __global__ void k_sel_pick(uint32_t* __restrict__ hist, GraphSel* __restrict__ s
     return;
   }
   const int64_t need = (lvl == 0) ? s.want : s.want - s.above1;
-  // lane 0 owns the top 128 bins, lane 31 the lowest
-  constexpr int per = kSelBins / 32;
-  const int top = kSelBins - 1 - lane * per;
-  int64_t mine = 0;
-  for (int i = 0; i < per; i++) mine += hg[top - i];
-  const int64_t incl = warp_incl_scan(mine);
-  const int64_t excl = incl - mine;
-  // first lane whose inclusive sum reaches need (or the last lane)
-  const unsigned hit = __ballot_sync(0xffffffffu, incl >= need);
-  const int owner = hit ? (__ffs(hit) - 1) : 31;
-  int bin = 0;
-  int64_t above = 0;
-  if (lane == owner) {
-    int64_t run = excl;
-    bin = top - per + 1;  // lowest bin of the lane if need is never reached
-    for (int i = 0; i < per; i++) {
-      const uint32_t c = hg[top - i];
-      if (run + c >= need) {
-        bin = top - i;
-        break;
-      }
-      run += c;
-    }
-    above = run;
+  const int lo = kSelBins - kPickPer * (threadIdx.x + 1);  // lowest bin of this thread
+  uint32_t c[kPickPer];
+  const uint4* h4 = reinterpret_cast<const uint4*>(hg + lo);
+#pragma unroll
+  for (int q = 0; q < kPickPer / 4; q++) {
+    const uint4 x = h4[q];
+    c[4 * q] = x.x;
+    c[4 * q + 1] = x.y;
+    c[4 * q + 2] = x.z;
+    c[4 * q + 3] = x.w;
   }
-  bin = __shfl_sync(0xffffffffu, bin, owner);
-  above = __shfl_sync(0xffffffffu, above, owner);
-  const uint32_t bin_count = hg[bin];
-  __syncwarp();
-  for (int i = lane; i < kSelBins; i += 32) hg[i] = 0;
-  if (lane == 0) {
+  int64_t mine = 0;
+#pragma unroll
+  for (int i = 0; i < kPickPer; i++) mine += c[i];
+  int64_t tot;
+  const int64_t excl = block_excl_scan(mine, sm, &tot);  // counts of the higher bins
+  // owner: the first thread whose inclusive sum reaches need, else the last
+  if (threadIdx.x == 0) s_owner = kBlock - 1;
+  __syncthreads();
+  if (excl < need && excl + mine >= need) s_owner = threadIdx.x;  // at most one thread
+  if (threadIdx.x == 0 && need <= 0) s_owner = 0;
+  __syncthreads();
+  if (threadIdx.x == s_owner) {
+    int64_t run = excl;  // edges in the bins above `bin`
+    int bin = lo;        // lowest bin of the thread if need is never reached
+    uint32_t bin_count = c[0];
+    bool found = false;
+#pragma unroll
+    for (int i = kPickPer - 1; i >= 0; i--) {
+      if (found) continue;
+      if (run + c[i] >= need) {
+        bin = lo + i;
+        bin_count = c[i];
+        found = true;
+      } else {
+        run += c[i];
+      }
+    }
     if (lvl == 0) {
       s.b1 = bin;
-      s.above1 = above;
+      s.above1 = run;
     } else {
       s.b2 = bin;
-      s.above2 = above;
-      s.count = s.above1 + above + bin_count;
+      s.above2 = run;
+      s.count = s.above1 + run + bin_count;
       s.thresh = ((uint64_t)s.b1 << 52) | ((uint64_t)bin << 40);
       count_out[g] = s.count;
     }
     sel[g] = s;
   }
+  uint4* w4 = reinterpret_cast<uint4*>(hg + lo);
+#pragma unroll
+  for (int q = 0; q < kPickPer / 4; q++) w4[q] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-template <bool WRITE>
-__global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restrict__ key, int64_t E,
+// Single-pass ordered compaction of the selected edges (key >= the graph's
+// threshold), in canonical id order: tiles in ticket order, positions from a
+// block scan plus the decoupled look-back over earlier tiles.
+__global__ void __launch_bounds__(kLbThreads) k_sel_compact(const uint64_t* __restrict__ key, int64_t E,
                                                         const int64_t* __restrict__ off_ptr, int32_t G,
-                                                        const GraphSel* __restrict__ sel,
-                                                        int64_t* __restrict__ bcount, const int64_t* __restrict__ boff,
-                                                        int64_t cap, int32_t* __restrict__ cand_idx,
-                                                        uint64_t* __restrict__ rkey, int32_t* __restrict__ rval) {
-  __shared__ int64_t sm[kBlock / 32 + 1];
-  const int64_t chunk = sel_chunk(E, gridDim.x);
-  const int64_t b0 = (int64_t)blockIdx.x * chunk;
-  const int64_t b1 = min(E, b0 + chunk);
-  int64_t run = WRITE ? boff[blockIdx.x] : 0;
-  int64_t tot = 0;
-  for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
-    const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
+                                                        const GraphSel* __restrict__ sel, int64_t cap,
+                                                        int32_t* __restrict__ cand_idx, uint64_t* __restrict__ rkey,
+                                                        int32_t* __restrict__ rval, int64_t* __restrict__ total,
+                                                        uint64_t* status, uint32_t* ctr, int64_t spin_limit,
+                                                        DevScalars* dsc) {
+  __shared__ int64_t sm[kLbThreads / 32 + 1];
+  __shared__ int64_t s_tile, s_excl;
+  __shared__ int s_last;
+  const int64_t nt = (E + kLbTile - 1) / kLbTile;
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&ctr[0], 1u);
+  __syncthreads();
+  const int64_t t = s_tile;
+  if (t < nt) {
+    const int64_t base = t * kLbTile + (int64_t)threadIdx.x * kItems;
     uint32_t pick = 0;
     uint64_t k[kItems];
-    // graph of the first item, then advanced item by item
-    int32_t g = (G == 1 || base >= b1) ? 0 : part_of(off_ptr, G, base);
-    int64_t g_end = (G == 1) ? INT64_MAX : off_ptr[g + 1];
-    uint64_t th = sel[g].thresh;
+    if (base < E) {
+      // graph of the first item, then advanced item by item
+      int32_t g = (G == 1) ? 0 : part_of(off_ptr, G, base);
+      int64_t g_end = (G == 1) ? INT64_MAX : off_ptr[g + 1];
+      uint64_t th = sel[g].thresh;
+      if (base + kItems <= E) {
+        const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(key + base);
 #pragma unroll
-    for (int i = 0; i < kItems; i++) {
-      const int64_t p = base + i;
-      k[i] = 0;
-      if (p < b1) {
-        while (p >= g_end) {
-          g++;
-          g_end = off_ptr[g + 1];
-          th = sel[g].thresh;
+        for (int q = 0; q < kItems / 2; q++) {
+          const ulonglong2 x = k2[q];
+          k[2 * q] = x.x;
+          k[2 * q + 1] = x.y;
         }
-        k[i] = key[p];
-        if (k[i] >= th) pick |= 1u << i;
+      } else {
+#pragma unroll
+        for (int i = 0; i < kItems; i++) k[i] = (base + i < E) ? key[base + i] : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < kItems; i++) {
+        const int64_t p = base + i;
+        if (p < E) {
+          while (p >= g_end) {
+            g++;
+            g_end = off_ptr[g + 1];
+            th = sel[g].thresh;
+          }
+          if (k[i] >= th) pick |= 1u << i;
+        }
       }
     }
-    const int64_t cnt = __popc(pick);
-    if (!WRITE) {
-      tot += cnt;
-      continue;
-    }
     int64_t tile_tot;
-    int64_t pos = run + block_excl_scan(cnt, sm, &tile_tot);
+    const int64_t local = block_excl_scan_n<kLbThreads>((int64_t)__popc(pick), sm, &tile_tot);
+    if (threadIdx.x < 32) {
+      bool timed_out;
+      const int64_t excl = warp_lookback(status, t, tile_tot, spin_limit, &timed_out);
+      if (threadIdx.x == 0) {
+        if (timed_out) atomicOr(&dsc->err, ERR_TIMEOUT);
+        s_excl = excl;
+        if (t == nt - 1) *total = excl + tile_tot;
+      }
+    }
+    __syncthreads();
+    int64_t pos = s_excl + local;
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
       if (pick & (1u << i)) {
@@ -185,17 +230,27 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
         pos++;
       }
     }
-    run += tile_tot;
   }
-  if (!WRITE) {
-    tot = block_sum(tot, sm);
-    if (threadIdx.x == 0) bcount[blockIdx.x] = tot;
+  // the last block to finish clears the look-back words and the counters
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int64_t i = threadIdx.x; i < nt; i += kLbThreads) status[i] = 0;
+    if (threadIdx.x == 0) {
+      ctr[0] = 0;
+      ctr[1] = 0;
+      if (nt == 0) *total = 0;
+    }
   }
 }
 
-__global__ void k_sel_total(const int64_t* __restrict__ boff, int nb, const int64_t* __restrict__ cand_ptr,
-                            int32_t G, int64_t cap, DevScalars* dsc) {
-  const int64_t total = boff[nb];
+__global__ void k_sel_total(const int64_t* __restrict__ total_p, const int64_t* __restrict__ cand_ptr, int32_t G,
+                            int64_t cap, DevScalars* dsc) {
+  const int64_t total = *total_p;
   dsc->n_cand_wanted = total;
   if (total > cap || total != cand_ptr[G]) {
     // nothing downstream may touch more than `cap` candidates: run it empty
@@ -211,8 +266,6 @@ __global__ void k_sel_total(const int64_t* __restrict__ boff, int nb, const int6
 int step_select(Handle& h) {
   const int64_t E = h.E_off;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kSelChunkBlocks, (E + kTile - 1) / kTile));
-  const int warps_per_block = 8;
-  const int pick_grid = (h.G + warps_per_block - 1) / warps_per_block;
   bool any_select = false;
   for (int32_t g = 0; g < h.G; g++)
     if (h.want_h[g] < h.off_ptr_h[g + 1] - h.off_ptr_h[g]) any_select = true;
@@ -222,23 +275,20 @@ int step_select(Handle& h) {
       k_sel_hist<<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, lvl, h.hist);
     }
     ++h.launches;
-    k_sel_pick<<<pick_grid, warps_per_block * 32, 0, h.stream>>>(h.hist, h.sel, h.d_off_ptr, h.G, lvl, h.d_graph_tmp);
+    k_sel_pick<<<h.G, kBlock, 0, h.stream>>>(h.hist, h.sel, h.d_off_ptr, h.G, lvl, h.d_graph_tmp);
   }
   PDG_CUDA(cudaGetLastError());
   int st = scan_excl_i64(h, h.d_graph_tmp, h.d_cand_ptr, h.G, nullptr, h.G);
   if (st) return st;
-  int64_t* bcount = h.blk_a;
-  int64_t* boff = h.blk_a + 2560;
+  int64_t* total = h.blk_a + 2560;
+  const int64_t tiles = (E + kLbTile - 1) / kLbTile;
+  if (tiles > h.scan_tiles_cap || tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized at init
   ++h.launches;
-  k_sel_compact<false><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, nullptr, 0, nullptr,
-                                                    nullptr, nullptr);
-  st = scan_excl_i64(h, bcount, boff, nb, nullptr, nb);
-  if (st) return st;
+  k_sel_compact<<<(int)std::max<int64_t>(tiles, 1), kLbThreads, 0, h.stream>>>(
+      h.key, E, h.d_off_ptr, h.G, h.sel, h.Rcap, h.cand_idx, h.rk[0], h.rv[0], total, h.scan_status, h.scan_ctr,
+      h.opt.spin_limit, h.dsc);
   ++h.launches;
-  k_sel_compact<true><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, nullptr, boff, h.Rcap,
-                                                   h.cand_idx, h.rk[0], h.rv[0]);
-  ++h.launches;
-  k_sel_total<<<1, 1, 0, h.stream>>>(boff, nb, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
+  k_sel_total<<<1, 1, 0, h.stream>>>(total, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
