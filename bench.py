@@ -43,8 +43,73 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+class _NvmlSampler:
+    """SM clock and clock-event reasons read through NVML every ~1 ms on a
+    background thread (read-only queries; nothing is set)."""
+
+    # nvmlClocksEventReasons bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, torch_index: int):
+        import ctypes
+        import threading
+
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+
+            prop = torch.cuda.get_device_properties(torch_index)
+            bus = getattr(prop, "pci_bus_id", None)
+            dom = getattr(prop, "pci_domain_id", 0)
+            pdev = getattr(prop, "pci_device_id", 0)
+            if bus is not None:
+                pci = f"{dom:08x}:{bus:02x}:{pdev:02x}.0".encode()
+                ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci, ctypes.byref(self.dev)) == 0
+        except Exception:
+            ok = False
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(torch_index), ctypes.byref(self.dev)) != 0:
+            raise RuntimeError("no NVML handle")
+        mx = ctypes.c_uint(0)
+        self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples = []
+        self.stop = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        ct = self.ct
+        clk = ct.c_uint(0)
+        rs = ct.c_ulonglong(0)
+        while not self.stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(clk)) == 0 and \
+                    self.reasons_fn(self.dev, ct.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            time.sleep(0.001)
+
+    def start(self):
+        self.thread.start()
+
+    def finish(self):
+        self.stop.set()
+        self.thread.join(timeout=5)
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+
+
 class ClockSampler:
-    """nvidia-smi samples during the timed region (read-only queries)."""
+    """Clocks during the timed region: NVML every ~1 ms, else nvidia-smi
+    every 100 ms (read-only queries)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -53,9 +118,16 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.nvml = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
 
     def __enter__(self):
+        try:
+            self.nvml = _NvmlSampler(self.index)
+            self.nvml.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -67,6 +139,8 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self.nvml.finish()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -76,6 +150,13 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        if self.nvml is not None:
+            sm = [c for c, _ in self.nvml.samples]
+            if not sm:
+                return {"sm_mhz": None, "sm_max_mhz": self.nvml.max_mhz, "reasons": ["no samples"], "source": "nvml"}
+            reasons = sorted({nm for _, r in self.nvml.samples for nm, bit in _NvmlSampler.BITS.items() if r & bit})
+            return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": self.nvml.max_mhz, "reasons": reasons,
+                    "samples": len(sm), "source": "nvml"}
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm, smax, reasons = [], [], set()
@@ -96,14 +177,14 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi"}
 
 
 # ---------------------------------------------------------------- algorithmic bytes
 
 def step_bytes(n, nnz, E, J, R, k):
-    """Compulsory DRAM bytes of each step (each stream once, gathers at
-    element size), per recovery."""
+    """Compulsory DRAM bytes of each step of the GPU pipeline (each stream
+    once, gathers at element size), per recovery."""
     return {
         # read row_ptr, col, w, parent; write r(v) and the off-tree SoA (u, v, id: 4 B, w: 8 B)
         "classify": 8 * (n + 1) + 12 * nnz + 4 * n + 8 * n + 20 * E,
@@ -111,14 +192,49 @@ def step_bytes(n, nnz, E, J, R, k):
         "tree": 12 * n + 16 * n + J * 60 * n,
         # read (u, v, w) 16 B, gather P(u), P(v), P(LCA) 48 B, write key + lca 12 B
         "score": 76 * E,
-        # two histogram passes + count/write passes over the keys, write candidates (idx, key, val)
-        "select": 32 * E + 16 * R,
+        # two histogram passes + one compaction pass over the keys, write candidates (idx, key, val)
+        "select": 24 * E + 16 * R,
         # 8 score digits + 3 LCA digits, each: read key+val 12 B, write 12 B
         "sort": 11 * 24 * R,
-        # records (~44 B written + read), tier flags and scans
+        # records (~44 B written + read), tier lists
         "accept": 100 * R,
         "budget": 8 * R + 12 * k,
     }
+
+
+# the longest single launch of a recovery: step A3 is one kernel, k_score
+DOMINANT_KERNEL = "k_score"
+SCORE_BYTES_PER_EDGE = 76  # read u, v (8 B), w (8 B); gather P(u), P(v), P(lca) (48 B); write key, lca (12 B)
+
+
+def path_bytes(n, m, E, k):
+    """Algorithmic bytes of one recovery (compulsory traffic of the method:
+    read the CSR and parent, write and read depth and D, one write and one
+    read of a 24-byte sort record per off-tree edge, the output)."""
+    return 8 * (n + 1) + 24 * m + 4 * n + 40 * n + 48 * E + 4 * k
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, if
+    the summary was taken on the kernel source as it is now (else None)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    src = os.path.join(ROOT, "paper_2508_20403_gb300", "csrc", "pdg_score.cu")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("- ") and ": " in line:
+                    key, val = line[2:].split(": ", 1)
+                    fields[key.strip()] = val.strip().strip("`")
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+        if fields.get("kernel source sha256") != digest:
+            return None
+        return float(fields["dram bytes per launch"])
+    except Exception:
+        return None
 
 
 def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None):
@@ -186,7 +302,7 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_max = float(tt.item())
     value = world * info["n_offtree"] / (t_max / 1e3)
-    # per-step roofline of the dominant step
+    # per-step breakdown and the roofline of the dominant kernel
     names = ["classify", "tree", "score", "select", "sort", "accept", "budget"]
     avg = {nm: float(np.mean([s[nm] for s in step_ms])) for nm in names}
     J = 0
@@ -194,10 +310,12 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
         J += 1
     nnz = 2 * info["m"]
     bytes_ = step_bytes(info["n"], nnz, info["n_offtree"], J, stats["candidates"], k)
-    dom = max(names, key=lambda nm: avg[nm])
     peak, peak_kind = measured_peaks()
-    achieved = bytes_[dom] / (avg[dom] / 1e3) / 1e9
-    total_bytes = sum(bytes_.values())
+    dom_bytes = SCORE_BYTES_PER_EDGE * info["n_offtree"]
+    dom_ms = avg["score"]  # the events around step A3 bracket exactly one launch of k_score
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = ncu_traffic(DOMINANT_KERNEL, "mesh128_a010")
+    b_alg = path_bytes(info["n"], info["m"], info["n_offtree"], k)
     result = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
@@ -209,11 +327,13 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
         "min_ms": float(np.min(times)), "median_ms": float(np.median(times)),
         "step_ms": {nm: round(avg[nm], 4) for nm in names},
         "recovery_stats": stats,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                     "algorithmic_bytes": bytes_[dom], "duration_ms": avg[dom]},
-        "path_roofline": {"algorithmic_bytes": total_bytes, "achieved_gbs": total_bytes / (t_max / 1e3) / 1e9,
-                          "frac": total_bytes / (t_max / 1e3) / 1e9 / peak},
+        "roofline": {"bound": "hbm", "kernel": DOMINANT_KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "algorithmic_bytes": dom_bytes, "duration_ms": dom_ms},
+        "path_roofline": {"algorithmic_bytes": b_alg, "achieved_gbs": b_alg / (t_max / 1e3) / 1e9,
+                          "frac": b_alg / (t_max / 1e3) / 1e9 / peak,
+                          "step_bytes": bytes_, "step_gbs": {nm: round(bytes_[nm] / (avg[nm] / 1e3) / 1e9, 1)
+                                                             for nm in names}},
         "gpu_launches": int(np.sum(launches)),
         "gpu_launches_per_step": int(np.mean(launches)),
     }
@@ -411,7 +531,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--alpha", type=float, default=0.10)

@@ -28,14 +28,14 @@ namespace pdg {
 namespace {
 
 constexpr int kRdxBins = 256;
-// Scatter tiles are 512 threads x 8 keys = 4096 keys: tiles this large keep
-// the look-back short at the candidate counts of a recovery (10^5 .. 10^7
-// keys) while a pass still spreads over many SMs.
+// Scatter tiles are 512 threads x 4 keys = 2048 keys: at the candidate counts
+// of a recovery (10^5 .. 10^7 keys) a pass then spreads over all SMs, and a
+// warp ranks its keys in 4 rounds; the look-back reads 16 tiles per round trip.
 constexpr int kOsThreads = 512;
-constexpr int kOsItems = 8;
+constexpr int kOsItems = 4;
 constexpr int kOsTile = kOsThreads * kOsItems;
 constexpr int kRdxWarps = kOsThreads / 32;
-constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // 256 items, 8 rounds of 32
+constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // 128 items, 4 rounds of 32
 constexpr int kMaxDigits = 8;
 constexpr int kLookWin = 16;  // look-back words fetched per round trip
 constexpr uint32_t kFlagA = 1u << 30;  // tile aggregate published
