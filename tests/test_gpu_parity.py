@@ -254,11 +254,49 @@ def mesh128():
     return W.mesh3d_graph(128)
 
 
+def _compare_bench_path(B, g, alpha, c=2):
+    """The benchmark's launch path: inputs resident in device memory, outputs
+    written to device buffers, the recovery captured into a CUDA graph on the
+    first call and replayed on the second; both calls must equal the oracle."""
+    import torch
+
+    k = int(np.floor(alpha * g.n))
+    ost, oids, osc, _ = O.recover(g, alpha, c=c)
+    opt = B.default_options(use_graph=1)
+    out_ids = torch.zeros(max(k, 1), dtype=torch.int32, device="cuda")
+    out_sc = torch.zeros(max(k, 1), dtype=torch.float64, device="cuda")
+    with B.Sparsifier.from_graph(g, device=True, options=opt) as sp:
+        for _ in range(2):
+            out_ids.fill_(-1)
+            out_sc.fill_(0.0)
+            st, ids, sc, cnt = sp.recover(alpha, c, out_ids=out_ids, out_scores=out_sc)
+            assert (st == B.PDG_UNDER_BUDGET) == (ost == O.UNDER_BUDGET)
+            assert ids.cpu().numpy().tolist() == oids.tolist(), (g.name, alpha, c, sp.last_stats())
+            got = sc.cpu().numpy()
+            assert np.array_equal(got, osc)
+            np.testing.assert_allclose(got, osc, rtol=SCORE_RTOL, atol=0)
+        return sp.last_stats()
+
+
 @pytest.mark.parametrize("alpha", [0.02, 0.10])
 def test_mesh128_full_size(B, mesh128, alpha):
     """The benchmark's workload in the benchmark's launch configuration."""
-    stats = _compare(B, mesh128, alpha)
+    stats = _compare_bench_path(B, mesh128, alpha)
     assert stats["coop_candidates"] > 0 and stats["max_subtask"] > 1000
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    import os
+
+    return W.rmat_graph(22, workers=min(16, os.cpu_count() or 1))
+
+
+def test_rmat22_full_size(B, rmat22):
+    """R-MAT scale 22 (about 2.4M vertices, 64M edges after deduplication, one
+    giant subtask at the hub root) at full size, bench launch path."""
+    stats = _compare_bench_path(B, rmat22, 0.02)
+    assert stats["max_subtask"] > 10000
 
 
 def test_mesh48_cooperative_tier_only(B):
