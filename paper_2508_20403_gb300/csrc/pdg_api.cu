@@ -138,18 +138,9 @@ __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->n_constrained = 0;
 }
 
-// upper entries (col > row) per row: endpoints of canonical ids
-__global__ void k_upper_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n,
-                              int64_t* __restrict__ cnt) {
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = row_ptr[u], e = row_ptr[u + 1];
-    cnt[u] = e - lower_bound_i32(col, b, e, (int32_t)(u + 1));
-  }
-}
-
-__global__ void k_endpoints(const int64_t* __restrict__ up_ptr, const int64_t* __restrict__ row_ptr,
-                            const int32_t* __restrict__ col, int64_t n, int64_t m, const int32_t* __restrict__ ids,
-                            int64_t count, int32_t* __restrict__ ou, int32_t* __restrict__ ov, DevScalars* dsc) {
+__global__ void k_endpoints(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, int64_t m,
+                            const int32_t* __restrict__ ids, int64_t count, int32_t* __restrict__ ou,
+                            int32_t* __restrict__ ov, DevScalars* dsc) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t id = ids[i];
     if (id < 0 || id >= m) {
@@ -157,15 +148,8 @@ __global__ void k_endpoints(const int64_t* __restrict__ up_ptr, const int64_t* _
       ou[i] = ov[i] = -1;
       continue;
     }
-    int64_t lo = 0, hi = n;  // up_ptr[lo] <= id < up_ptr[hi]
-    while (hi - lo > 1) {
-      int64_t mid = (lo + hi) >> 1;
-      if (up_ptr[mid] <= id) lo = mid; else hi = mid;
-    }
-    const int64_t b = row_ptr[lo], e = row_ptr[lo + 1];
-    const int64_t first = lower_bound_i32(col, b, e, (int32_t)(lo + 1));
-    ou[i] = (int32_t)lo;
-    ov[i] = col[first + (id - up_ptr[lo])];
+    ou[i] = eu[id];
+    ov[i] = ev[id];
   }
 }
 
@@ -268,7 +252,6 @@ using namespace pdg;
 struct pdg_sparsifier {
   Handle h;
   HostStage stage;
-  int64_t* up_ptr = nullptr;  // lazily built for pdg_edge_endpoints
 };
 
 extern "C" {
@@ -401,7 +384,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       cudaMemcpyAsync(h.d_vtx_ptr, vtx_ptr, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice, h.stream) !=
           cudaSuccess)
     return fail(PDG_E_CUDA);
-  h.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (h.nnz + kTile - 1) / kTile));
+  h.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (h.m + kTile - 1) / kTile));
   if ((st = validate_graph(h))) return fail(st);
   // per-graph edge counts from the row offsets at the graph boundaries
   std::vector<int64_t> rp_at(num_graphs + 1);
@@ -416,6 +399,16 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       return fail(PDG_E_CUDA);
     device_release(h, tmp);
   }
+  // the graph stays resident as its canonical edge list; the CSR is dropped
+  if ((st = alloc_n(h, &h.el_u, std::max<int64_t>(h.m, 1))) || (st = alloc_n(h, &h.el_v, std::max<int64_t>(h.m, 1))) ||
+      (st = alloc_n(h, &h.el_w, std::max<int64_t>(h.m, 1))) || (st = build_edge_list(h)))
+    return fail(st);
+  device_release(h, h.row_ptr);
+  device_release(h, h.col);
+  device_release(h, h.w);
+  h.row_ptr = nullptr;
+  h.col = nullptr;
+  h.w = nullptr;
   h.edge_ptr_h.assign(num_graphs + 1, 0);
   h.off_ptr_h.assign(num_graphs + 1, 0);
   for (int32_t g = 0; g < num_graphs; g++) {
@@ -773,15 +766,6 @@ int pdg_edge_endpoints(pdg_handle hp, const int32_t* ids, int64_t count, int32_t
   if (count == 0) return PDG_OK;
   Handle& h = hp->h;
   int st;
-  if (!hp->up_ptr) {
-    int64_t* cnt = nullptr;
-    if ((st = alloc_n(h, &cnt, h.n)) || (st = alloc_n(h, &hp->up_ptr, h.n + 1))) return st;
-    ++h.launches;
-    k_upper_count<<<grid_for(h, h.n), kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.n, cnt);
-    if ((st = scan_excl_i64(h, cnt, hp->up_ptr, h.n, nullptr, h.n))) return st;
-    PDG_CUDA(cudaStreamSynchronize(h.stream));
-    device_release(h, cnt);
-  }
   const int32_t* d_ids = ids;
   int32_t* d_u = u;
   int32_t* d_v = v;
@@ -796,8 +780,7 @@ int pdg_edge_endpoints(pdg_handle hp, const int32_t* ids, int64_t count, int32_t
   ++h.launches;
   k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
   ++h.launches;
-  k_endpoints<<<grid_for(h, count), kBlock, 0, h.stream>>>(hp->up_ptr, h.row_ptr, h.col, h.n, h.m, d_ids, count, d_u,
-                                                           d_v, h.dsc);
+  k_endpoints<<<grid_for(h, count), kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.m, d_ids, count, d_u, d_v, h.dsc);
   if (mem_kind == PDG_MEM_HOST) {
     PDG_CUDA(cudaMemcpyAsync(u, d_u, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, h.stream));
     PDG_CUDA(cudaMemcpyAsync(v, d_v, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, h.stream));

@@ -3,17 +3,17 @@
 // off-tree edges, in canonical id order, into structure-of-arrays form.
 //
 // Canonical id of {u, v}, u < v: rank of the CSR entry (u, v) among all
-// entries with row < col in row-major order.  Edge (u, v) is a tree edge iff
-// parent[v] == u or parent[u] == v.  The write pass also records, for every
-// non-root vertex u, r(u) = fl(1/w(u, parent u)) (the resistive weight
-// W_re = 1/w of Eq. RT).
+// entries with row < col in row-major order.  The handle keeps the graph as
+// its canonical edge list (u, v, w in id order; built once from the CSR by
+// build_edge_list at init), so every recovery classifies by streaming that
+// list: edge (u, v) is a tree edge iff parent[v] == u or parent[u] == v.  The
+// write pass also records, for every non-root vertex x, r(x) =
+// fl(1/w(x, parent x)) (the resistive weight W_re = 1/w of Eq. RT).
 //
-// Layout: each block owns a contiguous chunk of CSR entries, taken in tiles
-// of kTile; each thread reads kItems consecutive entries (vector loads).  The
-// row starts a tile spans are staged in shared memory, so a thread finds its
-// row by a short search there and then follows it incrementally; skewed rows
-// cost the same as short ones.  Two passes: the count pass streams only the
-// column indices, the write pass also the weights.
+// Layout: each block owns a contiguous chunk of edges (CSR entries for the
+// edge-list build), taken in tiles of kTile; each thread reads kItems
+// consecutive items with vector loads.  Two passes: a count pass, then a
+// write pass that places each tile's output as one contiguous run.
 #include "pdg_internal.cuh"
 
 namespace pdg {
@@ -73,34 +73,29 @@ __device__ __forceinline__ int64_t warp_row_of(const int64_t* __restrict__ row_p
 
 constexpr int kSpanMax = kTile;  // rows staged per tile (enough when no row is empty)
 
+// Edge-list build (init): every CSR entry with row < col, in row-major order.
+// The row starts a tile spans are staged in shared memory, so a thread finds
+// its row by a short search there and then follows it incrementally; skewed
+// rows cost the same as short ones.
 template <bool WRITE>
-__global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__ row_ptr,
-                                                     const int32_t* __restrict__ col,
-                                                     const double* __restrict__ w,
-                                                     const int32_t* __restrict__ parent, int64_t n,
-                                                     int64_t nnz, int64_t* __restrict__ cnt_up,
-                                                     int64_t* __restrict__ cnt_off,
-                                                     const int64_t* __restrict__ off_up,
-                                                     const int64_t* __restrict__ off_off,
-                                                     double* __restrict__ rtree, int32_t* __restrict__ ou,
-                                                     int32_t* __restrict__ ov, int32_t* __restrict__ oid,
-                                                     double* __restrict__ ow) {
+__global__ void __launch_bounds__(kBlock) k_edge_list(const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col,
+                                                      const double* __restrict__ w, int64_t n, int64_t nnz,
+                                                      int64_t* __restrict__ cnt_up,
+                                                      const int64_t* __restrict__ off_up,
+                                                      int32_t* __restrict__ eu, int32_t* __restrict__ ev,
+                                                      double* __restrict__ ew) {
   __shared__ int64_t sm[kBlock / 32 + 1];
   // row starts of the tile, relative to its first entry and clipped to
   // [-1, kTile + 1]: s_rp[j] = row_ptr[r0 + j] - t0
   __shared__ int16_t s_rp[kSpanMax + 1];
   __shared__ int64_t s_r0;
-  // write pass: per-warp queue of (row, weight) for the reciprocals, then the
-  // tile's off-tree records (a tile holds at most kTile entries of each)
-  __shared__ double st_w[WRITE ? kTile : 1];
-  __shared__ int32_t st_u[WRITE ? kTile : 1], st_v[WRITE ? kTile : 1], st_id[WRITE ? kTile : 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t chunk = cls_chunk(nnz, gridDim.x);
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(nnz, b0 + chunk);
   int64_t run_up = WRITE ? off_up[blockIdx.x] : 0;
-  int64_t run_off = WRITE ? off_off[blockIdx.x] : 0;
-  int64_t tot_up = 0, tot_off = 0;
+  int64_t tot_up = 0;
   if (b0 < b1 && wid == 0) {
     const int64_t r = warp_row_of(row_ptr, n, b0);
     if (lane == 0) s_r0 = r;
@@ -126,7 +121,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
     int32_t c[kItems];
     double x[kItems];
     int32_t rows[kItems];
-    uint32_t is_up = 0, is_off = 0, is_par = 0;
+    uint32_t is_up = 0;
     if (rel0 < tlen) {
       const int64_t base = t0 + rel0;
       load_cols(col, base, t0 + tlen, c);
@@ -144,7 +139,6 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
         u = row_of(row_ptr, n, base);
         next = __ldg(row_ptr + u + 1);
       }
-      int32_t pu = __ldg(parent + u);
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
         const int64_t p = base + i;
@@ -152,37 +146,105 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
           while (p >= next) {
             u++;
             next = covered ? t0 + s_rp[u - r0 + 1] : __ldg(row_ptr + u + 1);
-            pu = __ldg(parent + u);
           }
           rows[i] = (int32_t)u;
-          const int32_t v = c[i];
-          if (WRITE && pu == v) is_par |= 1u << i;
-          if (u < v) {
-            is_up |= 1u << i;
-            const bool tree = (__ldg(parent + v) == (int32_t)u) || (pu == v);
-            if (!tree) is_off |= 1u << i;
-          }
+          if (u < c[i]) is_up |= 1u << i;
         }
       }
       if (rel0 + kItems >= tlen) s_r0 = u;  // row of the tile's last entry: the next tile starts there
     }
-    const int64_t n_up = __popc(is_up), n_off = __popc(is_off);
+    const int64_t n_up = __popc(is_up);
     if (!WRITE) {
       tot_up += n_up;
+      continue;
+    }
+    int64_t tile_tot;
+    int64_t pos = run_up + block_excl_scan(n_up, sm, &tile_tot);
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+      if (is_up & (1u << i)) {
+        eu[pos] = rows[i];
+        ev[pos] = c[i];
+        ew[pos] = x[i];
+        pos++;
+      }
+    }
+    run_up += tile_tot;
+  }
+  if (!WRITE) {
+    tot_up = block_sum(tot_up, sm);
+    if (threadIdx.x == 0) cnt_up[blockIdx.x] = tot_up;
+  }
+}
+
+// Recovery-time classification of the canonical edge list.  Count pass:
+// off-tree edges per block.  Write pass: r(x) for the tree edges (queued per
+// warp so the FP64 reciprocals run densely -- a division per lane per item
+// would keep the slow double-precision pipe busy for every edge) and the
+// off-tree SoA, staged per tile and written as one coalesced run.
+template <bool WRITE>
+__global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                                                     const double* __restrict__ ew,
+                                                     const int32_t* __restrict__ parent, int64_t m,
+                                                     int64_t* __restrict__ cnt_off,
+                                                     const int64_t* __restrict__ off_off,
+                                                     double* __restrict__ rtree, int32_t* __restrict__ ou,
+                                                     int32_t* __restrict__ ov, int32_t* __restrict__ oid,
+                                                     double* __restrict__ ow) {
+  __shared__ int64_t sm[kBlock / 32 + 1];
+  // write pass: per-warp queue of (child, weight) for the reciprocals, then
+  // the tile's off-tree records (a tile holds at most kTile entries of each)
+  __shared__ double st_w[WRITE ? kTile : 1];
+  __shared__ int32_t st_u[WRITE ? kTile : 1], st_v[WRITE ? kTile : 1], st_id[WRITE ? kTile : 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t chunk = cls_chunk(m, gridDim.x);
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = min(m, b0 + chunk);
+  int64_t run_off = WRITE ? off_off[blockIdx.x] : 0;
+  int64_t tot_off = 0;
+  for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
+    const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
+    int32_t a[kItems], b[kItems], child[kItems];
+    double x[kItems];
+    uint32_t is_off = 0, is_tree = 0;
+    if (base < b1) {
+      load_cols(eu, base, b1, a);
+      load_cols(ev, base, b1, b);
+      if (WRITE) load_weights(ew, base, b1, x);
+      int32_t pa[kItems], pb[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; i++) {
+        const bool ok = base + i < b1;
+        pa[i] = ok ? __ldg(parent + a[i]) : -1;
+        pb[i] = ok ? __ldg(parent + b[i]) : -1;
+      }
+#pragma unroll
+      for (int i = 0; i < kItems; i++) {
+        if (base + i >= b1) continue;
+        if (pb[i] == a[i]) {
+          is_tree |= 1u << i;
+          child[i] = b[i];
+        } else if (pa[i] == b[i]) {
+          is_tree |= 1u << i;
+          child[i] = a[i];
+        } else {
+          is_off |= 1u << i;
+        }
+      }
+    }
+    const int64_t n_off = __popc(is_off);
+    if (!WRITE) {
       tot_off += n_off;
       continue;
     }
-    // r(u) = fl(1/w(u, parent u)): the warp's parent entries are queued and
-    // divided densely (a division per lane per item would keep the slow
-    // double-precision pipe busy for every CSR entry)
     {
-      const int npar = __popc(is_par);
-      const int incl = warp_incl_scan(npar);
-      int slot = wid * (kTile / (kBlock / 32)) + incl - npar;
+      const int ntree = __popc(is_tree);
+      const int incl = warp_incl_scan(ntree);
+      int slot = wid * (kTile / (kBlock / 32)) + incl - ntree;
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
-        if (is_par & (1u << i)) {
-          st_u[slot] = rows[i];
+        if (is_tree & (1u << i)) {
+          st_u[slot] = child[i];
           st_w[slot] = x[i];
           slot++;
         }
@@ -195,65 +257,69 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int64_t* __restrict__
       }
     }
     int64_t tile_tot;
-    int64_t ex = block_excl_scan((n_up << 32) | n_off, sm, &tile_tot);  // also orders the queue reads
-    int64_t id = run_up + (ex >> 32);
-    int lpos = (int)(ex & 0xffffffffll);  // position inside the tile's output run
+    int lpos = (int)block_excl_scan(n_off, sm, &tile_tot);  // also orders the queue reads
     // stage the tile's off-tree records in shared memory ...
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
-      if (is_up & (1u << i)) {
-        if (is_off & (1u << i)) {
-          st_u[lpos] = rows[i];
-          st_v[lpos] = c[i];
-          st_id[lpos] = (int32_t)id;
-          st_w[lpos] = x[i];
-          lpos++;
-        }
-        id++;
+      if (is_off & (1u << i)) {
+        st_u[lpos] = a[i];
+        st_v[lpos] = b[i];
+        st_id[lpos] = (int32_t)(base + i);
+        st_w[lpos] = x[i];
+        lpos++;
       }
     }
     __syncthreads();
     // ... and write them out as one contiguous, coalesced run
-    const int cnt = (int)(tile_tot & 0xffffffffll);
+    const int cnt = (int)tile_tot;
     for (int j = threadIdx.x; j < cnt; j += kBlock) {
       ou[run_off + j] = st_u[j];
       ov[run_off + j] = st_v[j];
       oid[run_off + j] = st_id[j];
       ow[run_off + j] = st_w[j];
     }
-    run_up += tile_tot >> 32;
-    run_off += tile_tot & 0xffffffffll;
+    run_off += tile_tot;
+    __syncthreads();
   }
   if (!WRITE) {
-    tot_up = block_sum(tot_up, sm);
     tot_off = block_sum(tot_off, sm);
-    if (threadIdx.x == 0) {
-      cnt_up[blockIdx.x] = tot_up;
-      cnt_off[blockIdx.x] = tot_off;
-    }
+    if (threadIdx.x == 0) cnt_off[blockIdx.x] = tot_off;
   }
 }
 
 }  // namespace
 
-int step_classify(Handle& h) {
+int build_edge_list(Handle& h) {
   if (h.nnz == 0) return PDG_OK;
-  const int nb = h.nblk;
-  int64_t* cnt_up = h.blk_a;
-  int64_t* cnt_off = h.blk_a + 2560;
-  int64_t* off_up = h.blk_a + 5120;
-  int64_t* off_off = h.blk_a + 7680;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (h.nnz + kTile - 1) / kTile));
+  int64_t* cnt = h.blk_a;
+  int64_t* off = h.blk_a + 2560;
   ++h.launches;
-  k_classify<false><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.parent, h.n, h.nnz, cnt_up, cnt_off,
-                                                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  k_edge_list<false><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.n, h.nnz, cnt, nullptr, nullptr, nullptr,
+                                                  nullptr);
   PDG_CUDA(cudaGetLastError());
-  int st = scan_excl_i64(h, cnt_up, off_up, nb, nullptr, nb);
-  if (st) return st;
-  st = scan_excl_i64(h, cnt_off, off_off, nb, nullptr, nb);
+  int st = scan_excl_i64(h, cnt, off, nb, nullptr, nb);
   if (st) return st;
   ++h.launches;
-  k_classify<true><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.parent, h.n, h.nnz, nullptr, nullptr,
-                                                off_up, off_off, h.rtree, h.off_u, h.off_v, h.off_id, h.off_w);
+  k_edge_list<true><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.n, h.nnz, nullptr, off, h.el_u, h.el_v, h.el_w);
+  PDG_CUDA(cudaGetLastError());
+  return PDG_OK;
+}
+
+int step_classify(Handle& h) {
+  if (h.m == 0) return PDG_OK;
+  const int nb = h.nblk;
+  int64_t* cnt_off = h.blk_a;
+  int64_t* off_off = h.blk_a + 2560;
+  ++h.launches;
+  k_classify<false><<<nb, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, cnt_off, nullptr, nullptr,
+                                                 nullptr, nullptr, nullptr, nullptr);
+  PDG_CUDA(cudaGetLastError());
+  int st = scan_excl_i64(h, cnt_off, off_off, nb, nullptr, nb);
+  if (st) return st;
+  ++h.launches;
+  k_classify<true><<<nb, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, nullptr, off_off, h.rtree, h.off_u,
+                                                h.off_v, h.off_id, h.off_w);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

@@ -118,9 +118,12 @@ struct Handle {
   std::vector<int64_t> vtx_ptr_h, edge_ptr_h, off_ptr_h;  // G+1 each
 
   // resident graph
-  int64_t* row_ptr = nullptr;
+  int64_t* row_ptr = nullptr;  // input CSR: resident during init only
   int32_t* col = nullptr;
   double* w = nullptr;
+  int32_t* el_u = nullptr;  // canonical edge list (u < v, id order), resident
+  int32_t* el_v = nullptr;
+  double* el_w = nullptr;
   int32_t* parent = nullptr;
   int64_t* d_vtx_ptr = nullptr;
   int64_t* d_edge_ptr = nullptr;
@@ -388,6 +391,7 @@ int scan_excl_u8(Handle& h, const uint8_t* in, int64_t* out, const int64_t* n_de
 
 // steps
 int validate_graph(Handle& h);                  // sparsify_init checks + max depth
+int build_edge_list(Handle& h);                 // init: canonical edge list from the CSR
 int step_classify(Handle& h);                   // A1
 int step_tree(Handle& h);                       // A2
 int step_score(Handle& h, int score_mode);      // A3

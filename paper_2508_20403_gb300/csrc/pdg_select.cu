@@ -155,33 +155,33 @@ __global__ void __launch_bounds__(kBlock) k_sel_pick(uint32_t* __restrict__ hist
   for (int q = 0; q < kPickPer / 4; q++) w4[q] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Single-pass ordered compaction of the selected edges (key >= the graph's
-// threshold), in canonical id order: tiles in ticket order, positions from a
-// block scan plus the decoupled look-back over earlier tiles.
-__global__ void __launch_bounds__(kLbThreads) k_sel_compact(const uint64_t* __restrict__ key, int64_t E,
+// Ordered compaction of the selected edges (key >= the graph's threshold), in
+// canonical id order: a count pass per block chunk, a scan of the block
+// counts, and a write pass that places each tile's selected edges by a block
+// scan.  Both passes stream the keys with vector loads.
+template <bool WRITE>
+__global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restrict__ key, int64_t E,
                                                         const int64_t* __restrict__ off_ptr, int32_t G,
-                                                        const GraphSel* __restrict__ sel, int64_t cap,
-                                                        int32_t* __restrict__ cand_idx, uint64_t* __restrict__ rkey,
-                                                        int32_t* __restrict__ rval, int64_t* __restrict__ total,
-                                                        uint64_t* status, uint32_t* ctr, int64_t spin_limit,
-                                                        DevScalars* dsc) {
-  __shared__ int64_t sm[kLbThreads / 32 + 1];
-  __shared__ int64_t s_tile, s_excl;
-  __shared__ int s_last;
-  const int64_t nt = (E + kLbTile - 1) / kLbTile;
-  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&ctr[0], 1u);
-  __syncthreads();
-  const int64_t t = s_tile;
-  if (t < nt) {
-    const int64_t base = t * kLbTile + (int64_t)threadIdx.x * kItems;
+                                                        const GraphSel* __restrict__ sel,
+                                                        int64_t* __restrict__ bcount, const int64_t* __restrict__ boff,
+                                                        int64_t cap, int32_t* __restrict__ cand_idx,
+                                                        uint64_t* __restrict__ rkey, int32_t* __restrict__ rval) {
+  __shared__ int64_t sm[kBlock / 32 + 1];
+  const int64_t chunk = sel_chunk(E, gridDim.x);
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = min(E, b0 + chunk);
+  int64_t run = WRITE ? boff[blockIdx.x] : 0;
+  int64_t tot = 0;
+  for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
+    const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
     uint32_t pick = 0;
     uint64_t k[kItems];
-    if (base < E) {
+    if (base < b1) {
       // graph of the first item, then advanced item by item
       int32_t g = (G == 1) ? 0 : part_of(off_ptr, G, base);
       int64_t g_end = (G == 1) ? INT64_MAX : off_ptr[g + 1];
       uint64_t th = sel[g].thresh;
-      if (base + kItems <= E) {
+      if (base + kItems <= b1) {
         const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(key + base);
 #pragma unroll
         for (int q = 0; q < kItems / 2; q++) {
@@ -191,12 +191,12 @@ __global__ void __launch_bounds__(kLbThreads) k_sel_compact(const uint64_t* __re
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < kItems; i++) k[i] = (base + i < E) ? key[base + i] : 0;
+        for (int i = 0; i < kItems; i++) k[i] = (base + i < b1) ? key[base + i] : 0;
       }
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
         const int64_t p = base + i;
-        if (p < E) {
+        if (p < b1) {
           while (p >= g_end) {
             g++;
             g_end = off_ptr[g + 1];
@@ -206,19 +206,13 @@ __global__ void __launch_bounds__(kLbThreads) k_sel_compact(const uint64_t* __re
         }
       }
     }
-    int64_t tile_tot;
-    const int64_t local = block_excl_scan_n<kLbThreads>((int64_t)__popc(pick), sm, &tile_tot);
-    if (threadIdx.x < 32) {
-      bool timed_out;
-      const int64_t excl = warp_lookback(status, t, tile_tot, spin_limit, &timed_out);
-      if (threadIdx.x == 0) {
-        if (timed_out) atomicOr(&dsc->err, ERR_TIMEOUT);
-        s_excl = excl;
-        if (t == nt - 1) *total = excl + tile_tot;
-      }
+    const int64_t cnt = __popc(pick);
+    if (!WRITE) {
+      tot += cnt;
+      continue;
     }
-    __syncthreads();
-    int64_t pos = s_excl + local;
+    int64_t tile_tot;
+    int64_t pos = run + block_excl_scan(cnt, sm, &tile_tot);
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
       if (pick & (1u << i)) {
@@ -230,21 +224,11 @@ __global__ void __launch_bounds__(kLbThreads) k_sel_compact(const uint64_t* __re
         pos++;
       }
     }
+    run += tile_tot;
   }
-  // the last block to finish clears the look-back words and the counters
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (s_last) {
-    for (int64_t i = threadIdx.x; i < nt; i += kLbThreads) status[i] = 0;
-    if (threadIdx.x == 0) {
-      ctr[0] = 0;
-      ctr[1] = 0;
-      if (nt == 0) *total = 0;
-    }
+  if (!WRITE) {
+    tot = block_sum(tot, sm);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = tot;
   }
 }
 
@@ -280,13 +264,16 @@ int step_select(Handle& h) {
   PDG_CUDA(cudaGetLastError());
   int st = scan_excl_i64(h, h.d_graph_tmp, h.d_cand_ptr, h.G, nullptr, h.G);
   if (st) return st;
-  int64_t* total = h.blk_a + 2560;
-  const int64_t tiles = (E + kLbTile - 1) / kLbTile;
-  if (tiles > h.scan_tiles_cap || tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized at init
+  int64_t* bcount = h.blk_a;
+  int64_t* boff = h.blk_a + 2560;  // [0, nb]: block offsets, boff[nb] = total
   ++h.launches;
-  k_sel_compact<<<(int)std::max<int64_t>(tiles, 1), kLbThreads, 0, h.stream>>>(
-      h.key, E, h.d_off_ptr, h.G, h.sel, h.Rcap, h.cand_idx, h.rk[0], h.rv[0], total, h.scan_status, h.scan_ctr,
-      h.opt.spin_limit, h.dsc);
+  k_sel_compact<false><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, nullptr, 0, nullptr,
+                                                    nullptr, nullptr);
+  if ((st = scan_excl_i64(h, bcount, boff, nb, nullptr, nb))) return st;
+  ++h.launches;
+  k_sel_compact<true><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, nullptr, boff, h.Rcap,
+                                                   h.cand_idx, h.rk[0], h.rv[0]);
+  int64_t* total = boff + nb;
   ++h.launches;
   k_sel_total<<<1, 1, 0, h.stream>>>(total, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
   PDG_CUDA(cudaGetLastError());
