@@ -16,8 +16,9 @@ namespace pdg {
 namespace {
 
 __device__ __forceinline__ int32_t up_level(const int32_t* __restrict__ parent, const int32_t* __restrict__ up,
-                                            int64_t n, int j, int32_t x) {
-  return j == 0 ? __ldg(parent + x) : __ldg(up + (int64_t)(j - 1) * n + x);
+                                            uint32_t n, int j, int32_t x) {
+  // level j >= 1 starts at up + (j - 1) n (a 32 x 32 -> 64-bit product)
+  return j == 0 ? __ldg(parent + x) : __ldg(up + (uint64_t)(uint32_t)(j - 1) * n + x);
 }
 
 // x * 2^-S rounded to nearest, ties to even; x > 0 and the result is normal.
@@ -44,6 +45,14 @@ __device__ __forceinline__ double fixed_to_double(u128 x, int S) {
   return __longlong_as_double((long long)bits);
 }
 
+// The same when x < 2^64: the integer -> FP64 conversion rounds to nearest
+// even, and the scaling by 2^-S (scale) is exact because the result is normal.
+__device__ __forceinline__ double fixed_to_double_fast(u128 x, int S, double scale) {
+  const uint64_t hi = (uint64_t)(x >> 64);
+  if (hi == 0) return __dmul_rn(__ull2double_rn((unsigned long long)x), scale);
+  return fixed_to_double(x, S);
+}
+
 __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou, const int32_t* __restrict__ ov,
                                                   const double* __restrict__ ow, const u128* __restrict__ P,
                                                   const int32_t* __restrict__ parent,
@@ -51,6 +60,9 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
                                                   const DevScalars* __restrict__ dsc, int score_mode,
                                                   uint64_t* __restrict__ key, int32_t* __restrict__ lca) {
   const int S = 52 - dsc->e_min;
+  // 2^-S as a double: S lies in [-848, 952] for weights in [2^-900, 2^900]
+  const double scale = __longlong_as_double((long long)((uint64_t)(1023 - S) << 52));
+  const uint32_t nn = (uint32_t)n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = ou[i], v = ov[i];
     const u128 Pu = P[u], Pv = P[v];
@@ -60,14 +72,13 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
       int32_t t = a; a = b; b = t;
       uint32_t s = da; da = db; db = s;
     }
-    uint32_t diff = da - db;
-    for (int j = 0; diff; j++, diff >>= 1)
-      if (diff & 1u) a = up_level(parent, up, n, j, a);
+    // lift the deeper endpoint by the depth difference, one level per set bit
+    for (uint32_t diff = da - db; diff; diff &= diff - 1) a = up_level(parent, up, nn, __ffs(diff) - 1, a);
     int32_t l = a;
     if (a != b) {
       for (int j = 31 - __clz((int)max(db, 1u)); j >= 0; j--) {
-        const int32_t ua = up_level(parent, up, n, j, a);
-        const int32_t ub = up_level(parent, up, n, j, b);
+        const int32_t ua = up_level(parent, up, nn, j, a);
+        const int32_t ub = up_level(parent, up, nn, j, b);
         if (ua != ub) {
           a = ua;
           b = ub;
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
     }
     const u128 Pl = P[l];
     const u128 r_fixed = (Pu >> 32) + (Pv >> 32) - ((Pl >> 32) << 1);
-    const double R = fixed_to_double(r_fixed, S);
+    const double R = fixed_to_double_fast(r_fixed, S, scale);
     const double s = (score_mode == PDG_SCORE_RESISTANCE) ? R : __dmul_rn(ow[i], R);
     key[i] = (uint64_t)__double_as_longlong(s);
     lca[i] = l;
