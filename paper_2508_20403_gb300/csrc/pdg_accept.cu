@@ -113,14 +113,6 @@ __device__ __forceinline__ int32_t anc_step(const int32_t* __restrict__ parent, 
   return y < 0 ? -1 : parent[y];
 }
 
-// k-th ancestor by binary lifting (level 0 = parent, level j >= 1 in up)
-__device__ __forceinline__ int32_t anc_k(const int32_t* __restrict__ parent, const int32_t* __restrict__ up, int64_t n,
-                                         int32_t x, int k) {
-  for (int j = 0; k && x >= 0; j++, k >>= 1)
-    if (k & 1) x = (j == 0) ? parent[x] : up[(int64_t)(j - 1) * n + x];
-  return x;
-}
-
 // Records in (LCA, rank) order.  Each record is oriented so that the child
 // of the LCA above the first endpoint has the smaller id ("side" order; an
 // endpoint equal to the LCA is its own side).  A marker with beta* >= 1 has
@@ -130,7 +122,8 @@ __device__ __forceinline__ int32_t anc_k(const int32_t* __restrict__ parent, con
 __global__ void __launch_bounds__(kBlock) k_build_records(
     const int32_t* __restrict__ lsort_rank, const int32_t* __restrict__ rank_cand, const int32_t* __restrict__ cand_idx,
     const int32_t* __restrict__ ou, const int32_t* __restrict__ ov, const int32_t* __restrict__ lca,
-    const u128* __restrict__ P, const int32_t* __restrict__ parent, const int32_t* __restrict__ up, int64_t n,
+    const uint8_t* __restrict__ side, const u128* __restrict__ P, const int32_t* __restrict__ parent,
+    const int32_t* __restrict__ up,
     int c, const DevScalars* __restrict__ dsc, int64_t cap, int32_t* __restrict__ rec_u, int32_t* __restrict__ rec_v,
     int32_t* __restrict__ rec_anc, int32_t* __restrict__ rec_du, int32_t* __restrict__ rec_dv,
     uint8_t* __restrict__ rec_b, int32_t* __restrict__ rec_rank, int32_t* __restrict__ rec_lca) {
@@ -143,9 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_build_records(
     const int32_t l = lca[i];
     const int32_t dl = (int32_t)(uint32_t)P[l];
     int32_t du = (int32_t)(uint32_t)P[u] - dl, dv = (int32_t)(uint32_t)P[v] - dl;
-    const int32_t su = du > 0 ? anc_k(parent, up, n, u, du - 1) : l;
-    const int32_t sv = dv > 0 ? anc_k(parent, up, n, v, dv - 1) : l;
-    if (sv < su) {
+    if (side[i]) {  // oriented by the step that found the LCA
       int32_t t = u; u = v; v = t;
       t = du; du = dv; dv = t;
     }
@@ -242,54 +233,67 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t value, int32_t* _
   if (pred) list[base + __popc(b & ((1u << lane) - 1))] = value;
 }
 
-// Per subtask: the warp tier (2..warp_max candidates) and the cooperative
-// tier (larger) lists, and the largest subtask.
+// Per subtask: singletons are recovered outright; the warp tier (2..warp_max
+// candidates) and the cooperative tier (larger) are listed; the largest
+// subtask is recorded.
+constexpr int kBigChunk = 1024;  // positions per warp when listing the cooperative tier
+
 __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
-                           int32_t* __restrict__ warp_seg, int32_t* __restrict__ big_seg) {
+                           const int32_t* __restrict__ rec_rank, uint8_t* __restrict__ acc_flag,
+                           int32_t* __restrict__ warp_seg, int32_t* __restrict__ big_seg,
+                           int64_t* __restrict__ big_chunk) {
   const int64_t S = dsc->n_seg;
   const int lane = threadIdx.x & 31;
   int64_t mx = 0;
   for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); q0 < S;
        q0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = q0 + lane;
-    const int64_t sz = (q < S) ? seg_begin[q + 1] - seg_begin[q] : 0;
+    const int32_t b = (q < S) ? seg_begin[q] : 0;
+    const int64_t sz = (q < S) ? seg_begin[q + 1] - b : 0;
+    if (sz == 1) acc_flag[rec_rank[b]] = 1;
     warp_append(sz >= 2 && sz <= warp_max, (int32_t)q, warp_seg, &dsc->n_warp_seg);
     warp_append(sz > warp_max, (int32_t)q, big_seg, &dsc->n_big_seg);
+    // cooperative subtasks are also cut into chunks, one warp each below
+    const int nch = (sz > warp_max) ? (int)((sz + kBigChunk - 1) / kBigChunk) : 0;
+    const int incl = warp_incl_scan(nch);
+    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+    if (wtot) {
+      unsigned long long base = 0;
+      if (lane == 31) base = atomicAdd((unsigned long long*)&dsc->n_big_chunk, (unsigned long long)wtot);
+      base = __shfl_sync(0xffffffffu, base, 31);
+      for (int k = 0; k < nch; k++)
+        big_chunk[base + incl - nch + k] = ((int64_t)q << 32) | (int64_t)k * kBigChunk;
+    }
     mx = max(mx, sz);
   }
   mx = __reduce_max_sync(0xffffffffu, (unsigned)min(mx, (int64_t)0x7fffffff));
   if (lane == 0 && mx) atomicMax((unsigned long long*)&dsc->max_seg, (unsigned long long)mx);
 }
 
-// Per position: singletons are recovered; cooperative-tier positions are
-// listed (big_pos) and marked undecided.
-__global__ void k_pos_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
-                           const int32_t* __restrict__ rec_rank, const uint8_t* __restrict__ rec_b,
-                           uint8_t* __restrict__ acc_flag, int32_t* __restrict__ big_pos, uint8_t* __restrict__ state) {
-  const int64_t N = dsc->n_cand;
-  const int32_t S = (int32_t)dsc->n_seg;
+// One warp per chunk of a cooperative subtask: its positions join big_pos
+// (contiguous, in order) and start undecided; pair registrations are counted.
+__global__ void k_big_positions(const int64_t* __restrict__ big_chunk, const int32_t* __restrict__ seg_begin,
+                                DevScalars* dsc, const uint8_t* __restrict__ rec_b, int32_t* __restrict__ big_pos,
+                                uint8_t* __restrict__ state) {
+  const int64_t nch = dsc->n_big_chunk;
   const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long regs = 0;
-  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); s0 < N;
-       s0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = s0 + lane;
-    bool big = false;
-    if (s < N) {
-      int32_t lo = 0, hi = S;  // segment q with seg_begin[q] <= s < seg_begin[q+1]
-      while (hi - lo > 1) {
-        int32_t mid = (lo + hi) >> 1;
-        if (seg_begin[mid] <= s) lo = mid; else hi = mid;
-      }
-      const int64_t sz = seg_begin[lo + 1] - seg_begin[lo];
-      if (sz == 1) acc_flag[rec_rank[s]] = 1;
-      else if (sz > warp_max) {
-        big = true;
-        state[s] = ST_UNDECIDED;
-        const unsigned b = rec_b[s];
-        if (b > 0) regs += (unsigned long long)(b + 1) * (b + 1);
-      }
+  for (int64_t x = warp; x < nch; x += nwarps) {
+    const int64_t c = big_chunk[x];
+    const int32_t q = (int32_t)(c >> 32);
+    const int32_t b = seg_begin[q] + (int32_t)(c & 0xffffffff);
+    const int32_t e = min(seg_begin[q + 1], b + kBigChunk);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd((unsigned long long*)&dsc->n_big, (unsigned long long)(e - b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int32_t s = b + lane; s < e; s += 32) {
+      big_pos[base + (s - b)] = s;
+      state[s] = ST_UNDECIDED;
+      const unsigned bb = rec_b[s];
+      if (bb > 0) regs += (unsigned long long)(bb + 1) * (bb + 1);
     }
-    warp_append(big, (int32_t)s, big_pos, &dsc->n_big);
   }
   for (int o = 16; o; o >>= 1) regs += __shfl_down_sync(0xffffffffu, regs, o);
   if (lane == 0 && regs) atomicAdd((unsigned long long*)&dsc->big_regs, regs);
@@ -788,7 +792,7 @@ int step_accept(Handle& h, int c) {
   int st;
   ++h.launches;
   k_build_records<<<grid, kBlock, 0, h.stream>>>(h.lsort_rank, h.rank_cand, h.cand_idx, h.off_u, h.off_v, h.lca,
-                                                  h.P[h.p_final], h.parent, up1, h.n, c, h.dsc, cap, h.rec_u,
+                                                  h.side, h.P[h.p_final], h.parent, up1, c, h.dsc, cap, h.rec_u,
                                                   h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank,
                                                   h.rec_lca);
   // subtask boundaries, tier lists, per-position tiers
@@ -798,10 +802,10 @@ int step_accept(Handle& h, int c) {
   k_seg_starts<<<(int)std::max<int64_t>(lb_tiles, 1), kLbThreads, 0, h.stream>>>(
       h.rec_lca, h.dsc, h.seg_begin, h.scan_status, h.scan_ctr, h.opt.spin_limit);
   ++h.launches;
-  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.warp_seg, h.big_seg);
+  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.rec_rank, h.acc_flag,
+                                            h.warp_seg, h.big_seg, h.big_chunk);
   ++h.launches;
-  k_pos_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.rec_rank, h.rec_b, h.acc_flag,
-                                            h.big_pos, h.state);
+  k_big_positions<<<grid, kBlock, 0, h.stream>>>(h.big_chunk, h.seg_begin, h.dsc, h.rec_b, h.big_pos, h.state);
   PDG_CUDA(cudaGetLastError());
   const RecArrays ra{h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, cap};
   // warp tier

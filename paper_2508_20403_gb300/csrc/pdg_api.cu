@@ -136,6 +136,7 @@ __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->radix_len = 0;
   dsc->n_warp_cand = 0;
   dsc->n_constrained = 0;
+  dsc->n_big_chunk = 0;
 }
 
 __global__ void k_endpoints(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, int64_t m,
@@ -181,7 +182,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
   if (R > h.Rcap) {
     void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp,
                    h.radix_status, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
-                   h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg,
+                   h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg, h.big_chunk,
                    h.pmask, h.reg_slot, h.pslot, h.und_list};
     for (void* p : old) device_release(h, p);
     const int64_t tiles = (R + kTile - 1) / kTile;
@@ -194,7 +195,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
         (st = alloc_n(h, &h.rec_du, R)) || (st = alloc_n(h, &h.rec_dv, R)) || (st = alloc_n(h, &h.rec_rank, R)) ||
         (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
         (st = alloc_n(h, &h.acc_flag, R)) || (st = alloc_n(h, &h.seg_begin, R + 1)) ||
-        (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) ||
+        (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) || (st = alloc_n(h, &h.big_chunk, R)) ||
         (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R)) || (st = alloc_n(h, &h.und_list, R)) ||
         (st = alloc_n(h, &h.pslot, 32 * R))) {
       h.Rcap = 0;
@@ -428,7 +429,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       (st = alloc_n(h, &h.off_u, E)) || (st = alloc_n(h, &h.off_v, E)) || (st = alloc_n(h, &h.off_id, E)) ||
       (st = alloc_n(h, &h.off_w, E)) || (st = alloc_n(h, &h.rtree, n)) || (st = alloc_n(h, &h.P[0], n)) ||
       (st = alloc_n(h, &h.P[1], n)) || (st = alloc_n(h, &h.up, (int64_t)std::max(h.J - 1, 1) * n)) ||
-      (st = alloc_n(h, &h.key, E)) || (st = alloc_n(h, &h.lca, E)) ||
+      (st = alloc_n(h, &h.key, E)) || (st = alloc_n(h, &h.lca, E)) || (st = alloc_n(h, &h.side, E)) ||
       (st = alloc_n(h, &h.hist, (int64_t)num_graphs * kSelBins)) || (st = alloc_n(h, &h.sel, num_graphs)) ||
       (st = alloc_n(h, &h.d_cand_ptr, num_graphs + 1)) || (st = alloc_n(h, &h.d_graph_tmp, num_graphs + 1)) ||
       (st = alloc_n(h, &h.gstat, num_graphs)) || (st = alloc_n(h, &h.gcount, num_graphs)) ||

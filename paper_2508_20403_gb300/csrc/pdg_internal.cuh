@@ -63,6 +63,7 @@ struct DevScalars {
   int64_t n_warp_cand;  // candidates in the warp tier
   int64_t n_cand_wanted;  // candidates the selection produced (may exceed capacity)
   int64_t n_constrained;  // cooperative tier: candidates with a possible earlier marker
+  int64_t n_big_chunk;    // cooperative tier: chunks of at most kBigChunk positions
 };
 
 // Cooperative tier: pair table slot (16 bytes; all-ones = empty) and exact
@@ -147,6 +148,7 @@ struct Handle {
   // scores
   uint64_t* key = nullptr;  // FP64 score bits (positive -> order preserving)
   int32_t* lca = nullptr;
+  uint8_t* side = nullptr;  // per off-tree edge: 1 iff the v-side child of the LCA has the smaller id
 
   // selection
   uint32_t* hist = nullptr;  // G * kSelBins
@@ -185,6 +187,7 @@ struct Handle {
   int32_t* warp_seg = nullptr;   // subtasks of the warp tier
   int32_t* big_pos = nullptr;    // positions of the cooperative tier
   int32_t* big_seg = nullptr;    // subtasks of the cooperative tier
+  int64_t* big_chunk = nullptr;  // (subtask << 32) | first position offset, one per chunk
   // cooperative tier: pair table, exact entries, per-position probe masks and slots
   int64_t table_cap = 0;
   int64_t xcap = 0;

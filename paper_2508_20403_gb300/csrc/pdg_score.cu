@@ -1,7 +1,9 @@
 // Step A3: score every off-tree edge (Algorithm 1 step 1: LCA_query,
 // distance_query, compute_resistance).
 //
-//   l   = LCA_T(u, v) by binary lifting over the pointer-jumping table
+//   l   = LCA_T(u, v) by binary lifting over the pointer-jumping table; the
+//         children of l toward u and v fall out of the same search and give
+//         the record orientation used by the acceptance step (side[i])
 //   R_T = D(u) + D(v) - 2 D(l)                       (Eq. RT), exact integer
 //         then ONE round-to-nearest-even conversion to FP64
 //   score = fl(w * R_T) (STRETCH) or R_T (RESISTANCE)
@@ -58,7 +60,8 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
                                                   const int32_t* __restrict__ parent,
                                                   const int32_t* __restrict__ up, int64_t n, int64_t E,
                                                   const DevScalars* __restrict__ dsc, int score_mode,
-                                                  uint64_t* __restrict__ key, int32_t* __restrict__ lca) {
+                                                  uint64_t* __restrict__ key, int32_t* __restrict__ lca,
+                                                  uint8_t* __restrict__ side) {
   const int S = 52 - dsc->e_min;
   // 2^-S as a double: S lies in [-848, 952] for weights in [2^-900, 2^900]
   const double scale = __longlong_as_double((long long)((uint64_t)(1023 - S) << 52));
@@ -68,13 +71,17 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
     const u128 Pu = P[u], Pv = P[v];
     int32_t a = u, b = v;
     uint32_t da = (uint32_t)Pu, db = (uint32_t)Pv;
-    if (da < db) {
+    const bool swapped = da < db;
+    if (swapped) {
       int32_t t = a; a = b; b = t;
       uint32_t s = da; da = db; db = s;
     }
+    const int32_t deep = a;
+    const uint32_t diff0 = da - db;
     // lift the deeper endpoint by the depth difference, one level per set bit
-    for (uint32_t diff = da - db; diff; diff &= diff - 1) a = up_level(parent, up, nn, __ffs(diff) - 1, a);
+    for (uint32_t diff = diff0; diff; diff &= diff - 1) a = up_level(parent, up, nn, __ffs(diff) - 1, a);
     int32_t l = a;
+    int32_t sd, so;  // children of the LCA toward the deeper / the other endpoint
     if (a != b) {
       for (int j = 31 - __clz((int)max(db, 1u)); j >= 0; j--) {
         const int32_t ua = up_level(parent, up, nn, j, a);
@@ -85,7 +92,16 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
         }
       }
       l = __ldg(parent + a);
+      sd = a;
+      so = b;
+    } else {
+      // the shallower endpoint is the LCA and is its own side; the deeper
+      // side is its ancestor diff0 - 1 levels up
+      so = l;
+      sd = deep;
+      for (uint32_t d = diff0 - 1; d; d &= d - 1) sd = up_level(parent, up, nn, __ffs(d) - 1, sd);
     }
+    side[i] = (swapped ? sd < so : so < sd) ? 1 : 0;
     const u128 Pl = P[l];
     const u128 r_fixed = (Pu >> 32) + (Pv >> 32) - ((Pl >> 32) << 1);
     const double R = fixed_to_double_fast(r_fixed, S, scale);
@@ -101,7 +117,7 @@ int step_score(Handle& h, int score_mode) {
   if (h.E_off == 0) return PDG_OK;
   ++h.launches;
   k_score<<<grid_for(h, h.E_off), kBlock, 0, h.stream>>>(h.off_u, h.off_v, h.off_w, h.P[h.p_final], h.parent, h.up,
-                                                          h.n, h.E_off, h.dsc, score_mode, h.key, h.lca);
+                                                          h.n, h.E_off, h.dsc, score_mode, h.key, h.lca, h.side);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
