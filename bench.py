@@ -186,8 +186,8 @@ def step_bytes(n, nnz, E, J, R, k):
     """Compulsory DRAM bytes of each step of the GPU pipeline (each stream
     once, gathers at element size), per recovery."""
     return {
-        # read row_ptr, col, w, parent; write r(v) and the off-tree SoA (u, v, id: 4 B, w: 8 B)
-        "classify": 8 * (n + 1) + 12 * nnz + 4 * n + 8 * n + 20 * E,
+        # stream the canonical edge list (u, v: 4 B, w: 8 B), read parent, write r(v) and the off-tree SoA
+        "classify": 16 * (nnz // 2) + 4 * n + 8 * n + 20 * E,
         # read parent + r; per pointer-jumping round read P,jump (20 B), gather P,jump (20 B), write (20 B)
         "tree": 12 * n + 16 * n + J * 60 * n,
         # read (u, v, w) 16 B, gather P(u), P(v), P(LCA) 48 B, write key + lca 12 B
