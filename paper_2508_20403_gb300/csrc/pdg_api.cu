@@ -118,6 +118,7 @@ __global__ void k_reset_recover(DevScalars* dsc) {
   dsc->err = 0;
   dsc->e_min = INT_MAX;
   dsc->e_max = INT_MIN;
+  dsc->score_ticket = 0;
 }
 
 __global__ void k_reset_attempt(DevScalars* dsc) {

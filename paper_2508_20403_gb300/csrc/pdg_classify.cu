@@ -8,12 +8,15 @@
 // build_edge_list at init), so every recovery classifies by streaming that
 // list: edge (u, v) is a tree edge iff parent[v] == u or parent[u] == v.  The
 // write pass also records, for every non-root vertex x, r(x) =
-// fl(1/w(x, parent x)) (the resistive weight W_re = 1/w of Eq. RT).
+// fl(1/w(x, parent x)) (the resistive weight W_re = 1/w of Eq. RT), and the
+// exponent range of these r that fixes the fixed-point scale of step A2.
 //
 // Layout: each block owns a contiguous chunk of edges (CSR entries for the
 // edge-list build), taken in tiles of kTile; each thread reads kItems
 // consecutive items with vector loads.  Two passes: a count pass, then a
 // write pass that places each tile's output as one contiguous run.
+#include <climits>
+
 #include "pdg_internal.cuh"
 
 namespace pdg {
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__
                                                      const int64_t* __restrict__ off_off,
                                                      double* __restrict__ rtree, int32_t* __restrict__ ou,
                                                      int32_t* __restrict__ ov, int32_t* __restrict__ oid,
-                                                     double* __restrict__ ow) {
+                                                     double* __restrict__ ow, DevScalars* __restrict__ dsc) {
   __shared__ int64_t sm[kBlock / 32 + 1];
   // write pass: per-warp queue of (child, weight) for the reciprocals, then
   // the tile's off-tree records (a tile holds at most kTile entries of each)
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__
   const int64_t b1 = min(m, b0 + chunk);
   int64_t run_off = WRITE ? off_off[blockIdx.x] : 0;
   int64_t tot_off = 0;
+  int e_lo = INT_MAX, e_hi = INT_MIN;  // exponent range of the r(x) this thread writes
   for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
     const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
     int32_t a[kItems], b[kItems], child[kItems];
@@ -253,7 +257,11 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__
       const int tot = __shfl_sync(0xffffffffu, incl, 31);
       for (int j = lane; j < tot; j += 32) {
         const int q = wid * (kTile / (kBlock / 32)) + j;
-        rtree[st_u[q]] = 1.0 / st_w[q];
+        const double r = 1.0 / st_w[q];
+        rtree[st_u[q]] = r;
+        const int e = (int)(((uint64_t)__double_as_longlong(r) >> 52) & 0x7ff) - 1023;
+        e_lo = min(e_lo, e);
+        e_hi = max(e_hi, e);
       }
     }
     int64_t tile_tot;
@@ -284,6 +292,26 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__
   if (!WRITE) {
     tot_off = block_sum(tot_off, sm);
     if (threadIdx.x == 0) cnt_off[blockIdx.x] = tot_off;
+  } else {
+    // the exponent range of r over the tree (it fixes the fixed-point scale of
+    // step A2): one atomic pair per block
+    e_lo = __reduce_min_sync(0xffffffffu, e_lo);
+    e_hi = __reduce_max_sync(0xffffffffu, e_hi);
+    __shared__ int s_lo, s_hi;
+    if (threadIdx.x == 0) {
+      s_lo = INT_MAX;
+      s_hi = INT_MIN;
+    }
+    __syncthreads();
+    if (lane == 0) {
+      atomicMin(&s_lo, e_lo);
+      atomicMax(&s_hi, e_hi);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_lo != INT_MAX) atomicMin(&dsc->e_min, s_lo);
+      if (s_hi != INT_MIN) atomicMax(&dsc->e_max, s_hi);
+    }
   }
 }
 
@@ -313,13 +341,13 @@ int step_classify(Handle& h) {
   int64_t* off_off = h.blk_a + 2560;
   ++h.launches;
   k_classify<false><<<nb, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, cnt_off, nullptr, nullptr,
-                                                 nullptr, nullptr, nullptr, nullptr);
+                                                 nullptr, nullptr, nullptr, nullptr, h.dsc);
   PDG_CUDA(cudaGetLastError());
   int st = scan_excl_i64(h, cnt_off, off_off, nb, nullptr, nb);
   if (st) return st;
   ++h.launches;
   k_classify<true><<<nb, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, nullptr, off_off, h.rtree, h.off_u,
-                                                h.off_v, h.off_id, h.off_w);
+                                                h.off_v, h.off_id, h.off_w, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

@@ -64,6 +64,7 @@ struct DevScalars {
   int64_t n_cand_wanted;  // candidates the selection produced (may exceed capacity)
   int64_t n_constrained;  // cooperative tier: candidates with a possible earlier marker
   int64_t n_big_chunk;    // cooperative tier: chunks of at most kBigChunk positions
+  unsigned long long score_ticket;  // step A3: next tile of off-tree edges to score
 };
 
 // Cooperative tier: pair table slot (16 bytes; all-ones = empty) and exact

@@ -17,6 +17,8 @@ namespace pdg {
 
 namespace {
 
+constexpr int kScoreTile = 256;  // off-tree edges per warp ticket
+
 __device__ __forceinline__ int32_t up_level(const int32_t* __restrict__ parent, const int32_t* __restrict__ up,
                                             uint32_t n, int j, int32_t x) {
   // level j >= 1 starts at up + (j - 1) n (a 32 x 32 -> 64-bit product)
@@ -55,59 +57,93 @@ __device__ __forceinline__ double fixed_to_double_fast(u128 x, int S, double sca
   return fixed_to_double(x, S);
 }
 
-__global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou, const int32_t* __restrict__ ov,
-                                                  const double* __restrict__ ow, const u128* __restrict__ P,
-                                                  const int32_t* __restrict__ parent,
-                                                  const int32_t* __restrict__ up, int64_t n, int64_t E,
-                                                  const DevScalars* __restrict__ dsc, int score_mode,
-                                                  uint64_t* __restrict__ key, int32_t* __restrict__ lca,
-                                                  uint8_t* __restrict__ side) {
-  const int S = 52 - dsc->e_min;
-  // 2^-S as a double: S lies in [-848, 952] for weights in [2^-900, 2^900]
-  const double scale = __longlong_as_double((long long)((uint64_t)(1023 - S) << 52));
-  const uint32_t nn = (uint32_t)n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = ou[i], v = ov[i];
-    const u128 Pu = P[u], Pv = P[v];
-    int32_t a = u, b = v;
-    uint32_t da = (uint32_t)Pu, db = (uint32_t)Pv;
-    const bool swapped = da < db;
-    if (swapped) {
-      int32_t t = a; a = b; b = t;
-      uint32_t s = da; da = db; db = s;
-    }
-    const int32_t deep = a;
-    const uint32_t diff0 = da - db;
-    // lift the deeper endpoint by the depth difference, one level per set bit
-    for (uint32_t diff = diff0; diff; diff &= diff - 1) a = up_level(parent, up, nn, __ffs(diff) - 1, a);
-    int32_t l = a;
-    int32_t sd, so;  // children of the LCA toward the deeper / the other endpoint
-    if (a != b) {
-      for (int j = 31 - __clz((int)max(db, 1u)); j >= 0; j--) {
-        const int32_t ua = up_level(parent, up, nn, j, a);
-        const int32_t ub = up_level(parent, up, nn, j, b);
-        if (ua != ub) {
-          a = ua;
-          b = ub;
-        }
+struct ScoreArgs {
+  const int32_t* ou;
+  const int32_t* ov;
+  const double* ow;
+  const u128* P;
+  const int32_t* parent;
+  const int32_t* up;
+  uint32_t n;
+  int S;
+  double scale;  // 2^-S
+  int score_mode;
+  uint64_t* key;
+  int32_t* lca;
+  uint8_t* side;
+};
+
+__device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i) {
+  const int32_t* __restrict__ parent = A.parent;
+  const int32_t* __restrict__ up = A.up;
+  const int32_t u = A.ou[i], v = A.ov[i];
+  const u128 Pu = A.P[u], Pv = A.P[v];
+  int32_t a = u, b = v;
+  uint32_t da = (uint32_t)Pu, db = (uint32_t)Pv;
+  const bool swapped = da < db;
+  if (swapped) {
+    int32_t t = a; a = b; b = t;
+    uint32_t s = da; da = db; db = s;
+  }
+  const int32_t deep = a;
+  const uint32_t diff0 = da - db;
+  // lift the deeper endpoint by the depth difference, one level per set bit
+  for (uint32_t diff = diff0; diff; diff &= diff - 1) a = up_level(parent, up, A.n, __ffs(diff) - 1, a);
+  int32_t l = a;
+  int32_t sd, so;  // children of the LCA toward the deeper / the other endpoint
+  if (a != b) {
+    for (int j = 31 - __clz((int)max(db, 1u)); j >= 0; j--) {
+      const int32_t ua = up_level(parent, up, A.n, j, a);
+      const int32_t ub = up_level(parent, up, A.n, j, b);
+      if (ua != ub) {
+        a = ua;
+        b = ub;
       }
-      l = __ldg(parent + a);
-      sd = a;
-      so = b;
-    } else {
-      // the shallower endpoint is the LCA and is its own side; the deeper
-      // side is its ancestor diff0 - 1 levels up
-      so = l;
-      sd = deep;
-      for (uint32_t d = diff0 - 1; d; d &= d - 1) sd = up_level(parent, up, nn, __ffs(d) - 1, sd);
     }
-    side[i] = (swapped ? sd < so : so < sd) ? 1 : 0;
-    const u128 Pl = P[l];
-    const u128 r_fixed = (Pu >> 32) + (Pv >> 32) - ((Pl >> 32) << 1);
-    const double R = fixed_to_double_fast(r_fixed, S, scale);
-    const double s = (score_mode == PDG_SCORE_RESISTANCE) ? R : __dmul_rn(ow[i], R);
-    key[i] = (uint64_t)__double_as_longlong(s);
-    lca[i] = l;
+    l = __ldg(parent + a);
+    sd = a;
+    so = b;
+  } else {
+    // the shallower endpoint is the LCA and is its own side; the deeper
+    // side is its ancestor diff0 - 1 levels up
+    so = l;
+    sd = deep;
+    for (uint32_t d = diff0 - 1; d; d &= d - 1) sd = up_level(parent, up, A.n, __ffs(d) - 1, sd);
+  }
+  A.side[i] = (swapped ? sd < so : so < sd) ? 1 : 0;
+  const u128 Pl = A.P[l];
+  const u128 r_fixed = (Pu >> 32) + (Pv >> 32) - ((Pl >> 32) << 1);
+  const double R = fixed_to_double_fast(r_fixed, A.S, A.scale);
+  const double sc = (A.score_mode == PDG_SCORE_RESISTANCE) ? R : __dmul_rn(A.ow[i], R);
+  A.key[i] = (uint64_t)__double_as_longlong(sc);
+  A.lca[i] = l;
+}
+
+// Long edge lists (a big packed batch) are scored in tiles of kScoreTile
+// edges that warps take in id order from a ticket counter: the edges in
+// flight then stay a narrow window, so the tree tables being gathered from
+// (those of a few graphs) stay in L2 however many graphs the batch holds.
+// Shorter lists use a plain grid-stride loop, whose window is narrower still.
+constexpr int64_t kTicketMinEdges = 1ll << 24;
+
+__global__ void __launch_bounds__(kBlock) k_score(ScoreArgs A, int64_t E, DevScalars* __restrict__ dsc) {
+  A.S = 52 - dsc->e_min;
+  // 2^-S as a double: S lies in [-848, 952] for weights in [2^-900, 2^900]
+  A.scale = __longlong_as_double((long long)((uint64_t)(1023 - A.S) << 52));
+  if (E < kTicketMinEdges) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x)
+      score_edge(A, i);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(&dsc->score_ticket, 1ull);
+    tk = __shfl_sync(0xffffffffu, tk, 0);
+    const int64_t i0 = (int64_t)tk * kScoreTile;
+    if (i0 >= E) break;
+    const int64_t i1 = min(E, i0 + kScoreTile);
+    for (int64_t i = i0 + lane; i < i1; i += 32) score_edge(A, i);
   }
 }
 
@@ -116,8 +152,9 @@ __global__ void __launch_bounds__(kBlock) k_score(const int32_t* __restrict__ ou
 int step_score(Handle& h, int score_mode) {
   if (h.E_off == 0) return PDG_OK;
   ++h.launches;
-  k_score<<<grid_for(h, h.E_off), kBlock, 0, h.stream>>>(h.off_u, h.off_v, h.off_w, h.P[h.p_final], h.parent, h.up,
-                                                          h.n, h.E_off, h.dsc, score_mode, h.key, h.lca, h.side);
+  ScoreArgs A{h.off_u, h.off_v, h.off_w, h.P[h.p_final], h.parent, h.up, (uint32_t)h.n, 0, 0.0, score_mode,
+              h.key,   h.lca,   h.side};
+  k_score<<<grid_for(h, h.E_off), kBlock, 0, h.stream>>>(A, h.E_off, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

@@ -24,32 +24,6 @@ namespace pdg {
 
 namespace {
 
-__global__ void k_rexp(const int32_t* __restrict__ parent, const double* __restrict__ rtree, int64_t n,
-                       DevScalars* dsc) {
-  __shared__ int smin, smax;
-  if (threadIdx.x == 0) {
-    smin = INT_MAX;
-    smax = INT_MIN;
-  }
-  __syncthreads();
-  int lmin = INT_MAX, lmax = INT_MIN;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    if (parent[v] >= 0) {
-      uint64_t b = (uint64_t)__double_as_longlong(rtree[v]);
-      int e = (int)((b >> 52) & 0x7ff) - 1023;
-      lmin = min(lmin, e);
-      lmax = max(lmax, e);
-    }
-  }
-  atomicMin(&smin, lmin);
-  atomicMax(&smax, lmax);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicMin(&dsc->e_min, smin);
-    atomicMax(&dsc->e_max, smax);
-  }
-}
-
 __global__ void k_tree_init(const int32_t* __restrict__ parent, const double* __restrict__ rtree, int64_t n,
                             int dep_bits, DevScalars* dsc, u128* __restrict__ P0) {
   const int e_min = dsc->e_min, e_max = dsc->e_max;
@@ -90,8 +64,6 @@ __global__ void __launch_bounds__(kBlock) k_tree_jump(const u128* __restrict__ P
 int step_tree(Handle& h) {
   const int64_t n = h.n;
   const int grid = grid_for(h, n);
-  ++h.launches;
-  k_rexp<<<grid, kBlock, 0, h.stream>>>(h.parent, h.rtree, n, h.dsc);
   int dep_bits = 0;
   while ((1ll << dep_bits) <= h.max_depth) dep_bits++;
   ++h.launches;
