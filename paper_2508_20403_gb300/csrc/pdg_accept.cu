@@ -241,7 +241,7 @@ constexpr int kBigChunk = 1024;  // positions per warp when listing the cooperat
 __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
                            const int32_t* __restrict__ rec_rank, uint8_t* __restrict__ acc_flag,
                            int32_t* __restrict__ warp_seg, int32_t* __restrict__ big_seg,
-                           int64_t* __restrict__ big_chunk) {
+                           int64_t* __restrict__ big_chunk, int64_t* __restrict__ seg_regs) {
   const int64_t S = dsc->n_seg;
   const int lane = threadIdx.x & 31;
   int64_t mx = 0;
@@ -252,9 +252,22 @@ __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
     const int64_t sz = (q < S) ? seg_begin[q + 1] - b : 0;
     if (sz == 1) acc_flag[rec_rank[b]] = 1;
     warp_append(sz >= 2 && sz <= warp_max, (int32_t)q, warp_seg, &dsc->n_warp_seg);
-    warp_append(sz > warp_max, (int32_t)q, big_seg, &dsc->n_big_seg);
+    // the cooperative subtask list (x = index in big_seg)
+    const bool big = sz > warp_max;
+    const unsigned bm = __ballot_sync(0xffffffffu, big);
+    int64_t x = -1;
+    if (bm) {
+      unsigned long long xb = 0;
+      if (lane == 0) xb = atomicAdd((unsigned long long*)&dsc->n_big_seg, (unsigned long long)__popc(bm));
+      xb = __shfl_sync(0xffffffffu, xb, 0);
+      if (big) {
+        x = (int64_t)xb + __popc(bm & ((1u << lane) - 1));
+        big_seg[x] = (int32_t)q;
+        seg_regs[x] = 0;
+      }
+    }
     // cooperative subtasks are also cut into chunks, one warp each below
-    const int nch = (sz > warp_max) ? (int)((sz + kBigChunk - 1) / kBigChunk) : 0;
+    const int nch = big ? (int)((sz + kBigChunk - 1) / kBigChunk) : 0;
     const int incl = warp_incl_scan(nch);
     const int wtot = __shfl_sync(0xffffffffu, incl, 31);
     if (wtot) {
@@ -262,7 +275,7 @@ __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
       if (lane == 31) base = atomicAdd((unsigned long long*)&dsc->n_big_chunk, (unsigned long long)wtot);
       base = __shfl_sync(0xffffffffu, base, 31);
       for (int k = 0; k < nch; k++)
-        big_chunk[base + incl - nch + k] = ((int64_t)q << 32) | (int64_t)k * kBigChunk;
+        big_chunk[base + incl - nch + k] = (x << 32) | (int64_t)k * kBigChunk;
     }
     mx = max(mx, sz);
   }
@@ -271,32 +284,40 @@ __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
 }
 
 // One warp per chunk of a cooperative subtask: its positions join big_pos
-// (contiguous, in order) and start undecided; pair registrations are counted.
-__global__ void k_big_positions(const int64_t* __restrict__ big_chunk, const int32_t* __restrict__ seg_begin,
-                                DevScalars* dsc, const uint8_t* __restrict__ rec_b, int32_t* __restrict__ big_pos,
-                                uint8_t* __restrict__ state) {
+// (contiguous, in order), start undecided and learn their subtask index x;
+// pair registrations are counted per subtask (they size its table region).
+__global__ void k_big_positions(const int64_t* __restrict__ big_chunk, const int32_t* __restrict__ big_seg,
+                                const int32_t* __restrict__ seg_begin, DevScalars* dsc,
+                                const uint8_t* __restrict__ rec_b, int32_t* __restrict__ big_pos,
+                                uint8_t* __restrict__ state, int32_t* __restrict__ pos_x,
+                                int64_t* __restrict__ seg_regs) {
   const int64_t nch = dsc->n_big_chunk;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long regs = 0;
-  for (int64_t x = warp; x < nch; x += nwarps) {
-    const int64_t c = big_chunk[x];
-    const int32_t q = (int32_t)(c >> 32);
+  unsigned long long regs_all = 0;
+  for (int64_t w = warp; w < nch; w += nwarps) {
+    const int64_t c = big_chunk[w];
+    const int32_t x = (int32_t)(c >> 32);
+    const int32_t q = big_seg[x];
     const int32_t b = seg_begin[q] + (int32_t)(c & 0xffffffff);
     const int32_t e = min(seg_begin[q + 1], b + kBigChunk);
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd((unsigned long long*)&dsc->n_big, (unsigned long long)(e - b));
     base = __shfl_sync(0xffffffffu, base, 0);
+    unsigned long long regs = 0;
     for (int32_t s = b + lane; s < e; s += 32) {
       big_pos[base + (s - b)] = s;
       state[s] = ST_UNDECIDED;
+      pos_x[s] = x;
       const unsigned bb = rec_b[s];
       if (bb > 0) regs += (unsigned long long)(bb + 1) * (bb + 1);
     }
+    for (int o = 16; o; o >>= 1) regs += __shfl_down_sync(0xffffffffu, regs, o);
+    if (lane == 0 && regs) atomicAdd((unsigned long long*)&seg_regs[x], regs);
+    regs_all += regs;
   }
-  for (int o = 16; o; o >>= 1) regs += __shfl_down_sync(0xffffffffu, regs, o);
-  if (lane == 0 && regs) atomicAdd((unsigned long long*)&dsc->big_regs, regs);
+  if (lane == 0 && regs_all) atomicAdd((unsigned long long*)&dsc->big_regs, regs_all);
 }
 
 // ------------------------------------------------------------------ warp tier
@@ -347,9 +368,6 @@ __device__ __forceinline__ uint64_t pair_key(int32_t z1, int32_t z2) {
   return ((uint64_t)(uint32_t)z1 << 32) | (uint64_t)(uint32_t)z2;
 }
 
-__device__ __forceinline__ int64_t slot_of(uint64_t key, uint64_t cap) {
-  return (int64_t)__umul64hi(mix64(key), cap);
-}
 
 
 __device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
@@ -370,7 +388,26 @@ struct CoopArgs {
   uint32_t* flagbits;  // one bit per pair slot: the pair has an exact block
   int32_t* und_list;   // positions left undecided by phase A (any order)
   int64_t* n_und;      // their number
+  const int32_t* pos_x;     // per position: index of its cooperative subtask
+  const int64_t* seg_pref;  // exclusive prefix of the subtasks' registrations
 };
+
+// The pair table is cut into one region per cooperative subtask (pairs never
+// cross subtasks): region x holds 2 * registrations + 16 slots, so a thread
+// works inside its own subtask's region, and the regions of the subtasks in
+// flight stay few and small enough for L2.
+struct Region {
+  uint64_t base, size;
+};
+
+__device__ __forceinline__ Region region_of(const CoopArgs& a, int32_t x) {
+  const int64_t p0 = a.seg_pref[x], p1 = a.seg_pref[x + 1];
+  return Region{(uint64_t)(2 * p0 + 16 * (int64_t)x), (uint64_t)(2 * (p1 - p0) + 16)};
+}
+
+__device__ __forceinline__ uint32_t region_slot(const Region& r, uint64_t key) {
+  return (uint32_t)(r.base + __umul64hi(mix64(key), r.size));
+}
 
 __device__ __forceinline__ bool slot_flagged(const uint32_t* __restrict__ bits, int32_t slot) {
   return (bits[slot >> 5] >> (slot & 31)) & 1u;
@@ -378,9 +415,10 @@ __device__ __forceinline__ bool slot_flagged(const uint32_t* __restrict__ bits, 
 
 __global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ flagbits, DevScalars* dsc,
                              int64_t table_cap, uint64_t* __restrict__ cap_out, int64_t* __restrict__ n_flag,
-                             int64_t* __restrict__ n_und) {
-  // effective capacity: twice the registrations (load <= 0.5), at least 1024
-  int64_t want = 2 * dsc->big_regs;
+                             int64_t* __restrict__ n_und, const int64_t* __restrict__ seg_pref) {
+  // slots of all subtask regions: twice the registrations (load <= 0.5) + 16 each
+  const int64_t nbs = dsc->n_big_seg;
+  int64_t want = 2 * seg_pref[nbs] + 16 * nbs;
   if (want < 1024) want = 1024;
   if (want > table_cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&dsc->err, ERR_TABLE);
@@ -407,13 +445,15 @@ __global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ 
 // as many rounds as its longest chain, not for the sum of its chains.
 template <int C>
 __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScalars* dsc) {
+  if (dsc->err & ERR_TABLE) return;  // the regions do not fit: the host retries with a larger table
   const int64_t nb = dsc->n_big;
-  const uint64_t cap = *a.cap;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.big_pos[q];
     Rec r;
     load_rec(a.ra, s, C, r);
     if (r.b == 0) continue;  // a 0-hop neighbourhood pair only matches the edge itself
+    const Region rg = region_of(a, a.pos_x[s]);
+    const uint32_t rend = (uint32_t)(rg.base + rg.size);
     constexpr int NP = (C + 1) * (C + 1);
     uint64_t key[NP];
     uint32_t slot[NP];  // capacities stay below 2^32 slots
@@ -422,11 +462,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
     for (int t = 0; t < NP; t++) {
       const int j = t / (C + 1), jp = t % (C + 1);
       key[t] = pair_key(r.U[j], r.V[jp]);
-      slot[t] = slot_of(key[t], cap);
+      slot[t] = region_slot(rg, key[t]);
       if (j <= r.b && jp <= r.b) want |= 1u << t;
     }
     uint32_t pend = want;
-    for (uint64_t step = 0; pend && step < cap; step++) {
+    for (uint64_t step = 0; pend && step < rg.size; step++) {
       unsigned long long old[NP];
 #pragma unroll
       for (int t = 0; t < NP; t++)
@@ -437,7 +477,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
       for (int t = 0; t < NP; t++) {
         if (!(pend >> t & 1u)) continue;
         if (old[t] == kEmptyKey || old[t] == key[t]) pend &= ~(1u << t);
-        else if (++slot[t] == cap) slot[t] = 0;
+        else if (++slot[t] == rend) slot[t] = (uint32_t)rg.base;
       }
     }
     if (pend) {  // the table is full: report; the host retries with a larger one
@@ -459,8 +499,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
 // together, one slot per round, like the inserts of phase A1.
 template <int C>
 __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars* dsc) {
+  if (dsc->err & ERR_TABLE) return;  // the regions do not fit: the host retries with a larger table
   const int64_t nb = dsc->n_big;
-  const uint64_t cap = *a.cap;
   unsigned long long cons = 0;
   const int lane = threadIdx.x & 31;
   // warp-uniform loop: every lane of a warp runs the same iterations
@@ -474,6 +514,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
     uint32_t pm = 0;
     int nclaim = 0;
     constexpr int NQ = (C + 1) * (C + 1);
+    const Region rg = valid ? region_of(a, a.pos_x[s]) : Region{0, 1};
+    const uint32_t rend = (uint32_t)(rg.base + rg.size);
 #pragma unroll
     for (int o = 0; o < 2 && valid; o++) {
       if (o == 1 && r.du > 0 && r.dv > 0) break;  // records are side-ordered: one orientation suffices
@@ -487,10 +529,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
         const int32_t z1 = o ? r.V[i] : r.U[i];
         const int32_t z2 = o ? r.U[ip] : r.V[ip];
         key[t] = pair_key(z1, z2);
-        slot[t] = slot_of(key[t], cap);
+        slot[t] = region_slot(rg, key[t]);
         if (i <= dx && ip <= dy) pend |= 1u << t;
       }
-      for (uint64_t step = 0; pend && step < cap; step++) {
+      for (uint64_t step = 0; pend && step < rg.size; step++) {
         unsigned long long k[NQ];
 #pragma unroll
         for (int t = 0; t < NQ; t++) k[t] = (pend >> t & 1u) ? a.ptab[slot[t]].key : 0ull;
@@ -502,8 +544,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
             pend &= ~(1u << t);
           } else if (k[t] == kEmptyKey) {
             pend &= ~(1u << t);
-          } else if (++slot[t] == cap) {
-            slot[t] = 0;
+          } else if (++slot[t] == rend) {
+            slot[t] = (uint32_t)rg.base;
           }
         }
       }
@@ -803,10 +845,13 @@ int step_accept(Handle& h, int c) {
       h.rec_lca, h.dsc, h.seg_begin, h.scan_status, h.scan_ctr, h.opt.spin_limit);
   ++h.launches;
   k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.rec_rank, h.acc_flag,
-                                            h.warp_seg, h.big_seg, h.big_chunk);
+                                            h.warp_seg, h.big_seg, h.big_chunk, h.seg_regs);
   ++h.launches;
-  k_big_positions<<<grid, kBlock, 0, h.stream>>>(h.big_chunk, h.seg_begin, h.dsc, h.rec_b, h.big_pos, h.state);
+  k_big_positions<<<grid, kBlock, 0, h.stream>>>(h.big_chunk, h.big_seg, h.seg_begin, h.dsc, h.rec_b, h.big_pos,
+                                                 h.state, h.pos_x, h.seg_regs);
   PDG_CUDA(cudaGetLastError());
+  // table regions of the cooperative subtasks
+  if ((st = scan_excl_i64(h, h.seg_regs, h.seg_pref, 0, &h.dsc->n_big_seg, cap))) return st;
   const RecArrays ra{h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, cap};
   // warp tier
   ++h.launches;
@@ -820,9 +865,11 @@ int step_accept(Handle& h, int c) {
   const int R = std::max(1, std::min(h.opt.max_rounds, 64));
   PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
   ++h.launches;
-  k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.flagbits, h.dsc, h.table_cap, d_cap, n_flag, n_und);
-  const CoopArgs a{ra,        h.big_pos, h.state, h.pmask,    h.reg_slot, h.pslot, h.ptab, h.xtab,
-                   d_cap,     n_flag,    h.xcap,  und_count,  h.flagbits, h.und_list, n_und};
+  k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.flagbits, h.dsc, h.table_cap, d_cap, n_flag, n_und,
+                                              h.seg_pref);
+  const CoopArgs a{ra,        h.big_pos, h.state,   h.pmask,    h.reg_slot, h.pslot, h.ptab, h.xtab,
+                   d_cap,     n_flag,    h.xcap,    und_count,  h.flagbits, h.und_list, n_und, h.pos_x,
+                   h.seg_pref};
   switch (c) {
     case 0: st = run_coop<0>(h, a, grid, R); break;
     case 1: st = run_coop<1>(h, a, grid, R); break;

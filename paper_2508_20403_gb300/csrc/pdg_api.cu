@@ -184,6 +184,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
     void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp,
                    h.radix_status, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
                    h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg, h.big_chunk,
+                   h.pos_x, h.seg_regs, h.seg_pref,
                    h.pmask, h.reg_slot, h.pslot, h.und_list};
     for (void* p : old) device_release(h, p);
     const int64_t tiles = (R + kTile - 1) / kTile;
@@ -197,6 +198,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
         (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
         (st = alloc_n(h, &h.acc_flag, R)) || (st = alloc_n(h, &h.seg_begin, R + 1)) ||
         (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) || (st = alloc_n(h, &h.big_chunk, R)) ||
+        (st = alloc_n(h, &h.pos_x, R)) || (st = alloc_n(h, &h.seg_regs, R)) || (st = alloc_n(h, &h.seg_pref, R + 1)) ||
         (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R)) || (st = alloc_n(h, &h.und_list, R)) ||
         (st = alloc_n(h, &h.pslot, 32 * R))) {
       h.Rcap = 0;
@@ -205,7 +207,8 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
     h.Rcap = R;
   }
   if ((st = ensure_scan_status(h, h.Rcap + 1))) return st;
-  return grow_tables(h, std::max<int64_t>(1024, 2 * (int64_t)(c + 1) * (c + 1) * h.Rcap), 0);
+  // pair table: twice the registrations plus 16 slots per cooperative subtask (at most R / 33 subtasks)
+  return grow_tables(h, std::max<int64_t>(1024, 2 * (int64_t)(c + 1) * (c + 1) * h.Rcap + h.Rcap), 0);
 }
 
 // pair table of `slots` slots; exact entries for slots / 16 flagged pairs (or `xblocks`)
@@ -630,7 +633,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
     }
     if (err & ERR_TABLE) {
       // pair table too small for the registrations, or too few exact blocks
-      const int64_t slots = std::max<int64_t>(h.table_cap, 2 * h.hsc->big_regs + 1024);
+      const int64_t slots = std::max<int64_t>(h.table_cap, 2 * h.hsc->big_regs + 16 * h.hsc->n_big_seg + 1024);
       if ((st = grow_tables(h, slots, 4 * h.xcap))) return st;
       continue;
     }

@@ -188,7 +188,10 @@ struct Handle {
   int32_t* warp_seg = nullptr;   // subtasks of the warp tier
   int32_t* big_pos = nullptr;    // positions of the cooperative tier
   int32_t* big_seg = nullptr;    // subtasks of the cooperative tier
-  int64_t* big_chunk = nullptr;  // (subtask << 32) | first position offset, one per chunk
+  int64_t* big_chunk = nullptr;  // (subtask index << 32) | first position offset, one per chunk
+  int32_t* pos_x = nullptr;      // per position: index of its cooperative subtask
+  int64_t* seg_regs = nullptr;   // per cooperative subtask: pair registrations
+  int64_t* seg_pref = nullptr;   // their exclusive prefix (R + 1)
   // cooperative tier: pair table, exact entries, per-position probe masks and slots
   int64_t table_cap = 0;
   int64_t xcap = 0;
