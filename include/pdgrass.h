@@ -196,7 +196,8 @@ int pdg_handle_info(pdg_handle h, int64_t* n, int64_t* m, int64_t* n_offtree, in
  * the cooperative tier, prefix retries, attempts, kernels launched by the
  * recovery, cooperative-tier candidates that showed an earlier registrant of
  * one of their pairs ("constrained"), ancestor pairs registered by the
- * cooperative tier, and one reserved zero.  stats must hold 12 int64.
+ * cooperative tier, and the site of a failed internal index check (0 if none;
+ * such a recovery returns PDG_E_CUDA).  stats must hold 12 int64.
  */
 int pdg_last_stats(pdg_handle h, int64_t* stats);
 

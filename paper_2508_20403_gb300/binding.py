@@ -194,7 +194,7 @@ class Sparsifier:
         a = np.zeros(12, dtype=np.int64)
         self._L.pdg_last_stats(self._h, a.ctypes.data)
         keys = ("candidates", "subtasks", "max_subtask", "warp_or_single", "coop_candidates", "coop_rounds",
-                "retries", "attempts", "launches", "coop_constrained", "coop_pairs")
+                "retries", "attempts", "launches", "coop_constrained", "coop_pairs", "bounds_site")
         return dict(zip(keys, (int(x) for x in a)))
 
     def last_timings(self) -> dict:

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kBlock) k_build_records(
     int c, const DevScalars* __restrict__ dsc, int64_t cap, int32_t* __restrict__ rec_u, int32_t* __restrict__ rec_v,
     int32_t* __restrict__ rec_anc, int32_t* __restrict__ rec_du, int32_t* __restrict__ rec_dv,
     uint8_t* __restrict__ rec_b, int32_t* __restrict__ rec_rank, int32_t* __restrict__ rec_lca) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   const int32_t* up1 = up;  // level 1 (anc_2), nullptr for trees of depth <= 1
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
@@ -242,6 +243,7 @@ __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
                            const int32_t* __restrict__ rec_rank, uint8_t* __restrict__ acc_flag,
                            int32_t* __restrict__ warp_seg, int32_t* __restrict__ big_seg,
                            int64_t* __restrict__ big_chunk, int64_t* __restrict__ seg_regs) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t S = dsc->n_seg;
   const int lane = threadIdx.x & 31;
   int64_t mx = 0;
@@ -291,6 +293,7 @@ __global__ void k_big_positions(const int64_t* __restrict__ big_chunk, const int
                                 const uint8_t* __restrict__ rec_b, int32_t* __restrict__ big_pos,
                                 uint8_t* __restrict__ state, int32_t* __restrict__ pos_x,
                                 int64_t* __restrict__ seg_regs) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t nch = dsc->n_big_chunk;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -326,6 +329,7 @@ __global__ void __launch_bounds__(kBlock) k_accept_warp(const int32_t* __restric
                                                         const DevScalars* __restrict__ dsc,
                                                         const int32_t* __restrict__ seg_begin, int c, RecArrays ra,
                                                         uint8_t* __restrict__ acc_flag) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t nw = dsc->n_warp_seg;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -372,6 +376,17 @@ __device__ __forceinline__ uint64_t pair_key(int32_t z1, int32_t z2) {
 
 __device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
 
+// A saved index failed its range check: report (first site wins) and skip.
+__device__ __noinline__ void bounds_fail(DevScalars* dsc, int site, int where = 0, int64_t pos = -1,
+                                        int64_t val = -1) {
+  if (atomicCAS(&dsc->bounds_site, 0, site) == 0) {
+    dsc->bounds_where = where;
+    dsc->bounds_pos = pos;
+    dsc->bounds_val = val;
+  }
+  atomicOr(&dsc->err, ERR_BOUNDS);
+}
+
 struct CoopArgs {
   RecArrays ra;
   const int32_t* big_pos;
@@ -390,6 +405,7 @@ struct CoopArgs {
   int64_t* n_und;      // their number
   const int32_t* pos_x;     // per position: index of its cooperative subtask
   const int64_t* seg_pref;  // exclusive prefix of the subtasks' registrations
+  DevScalars* dsc;
 };
 
 // The pair table is cut into one region per cooperative subtask (pairs never
@@ -401,6 +417,10 @@ struct Region {
 };
 
 __device__ __forceinline__ Region region_of(const CoopArgs& a, int32_t x) {
+  if (x < 0 || x >= a.dsc->n_big_seg) {
+    bounds_fail(a.dsc, 1);
+    x = 0;
+  }
   const int64_t p0 = a.seg_pref[x], p1 = a.seg_pref[x + 1];
   return Region{(uint64_t)(2 * p0 + 16 * (int64_t)x), (uint64_t)(2 * (p1 - p0) + 16)};
 }
@@ -416,6 +436,7 @@ __device__ __forceinline__ bool slot_flagged(const uint32_t* __restrict__ bits, 
 __global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ flagbits, DevScalars* dsc,
                              int64_t table_cap, uint64_t* __restrict__ cap_out, int64_t* __restrict__ n_flag,
                              int64_t* __restrict__ n_und, const int64_t* __restrict__ seg_pref) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   // slots of all subtask regions: twice the registrations (load <= 0.5) + 16 each
   const int64_t nbs = dsc->n_big_seg;
   int64_t want = 2 * seg_pref[nbs] + 16 * nbs;
@@ -445,7 +466,7 @@ __global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ 
 // as many rounds as its longest chain, not for the sum of its chains.
 template <int C>
 __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScalars* dsc) {
-  if (dsc->err & ERR_TABLE) return;  // the regions do not fit: the host retries with a larger table
+  if (attempt_aborted(dsc)) return;  // e.g. the regions do not fit: the host retries with a larger table
   const int64_t nb = dsc->n_big;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.big_pos[q];
@@ -499,7 +520,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
 // together, one slot per round, like the inserts of phase A1.
 template <int C>
 __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars* dsc) {
-  if (dsc->err & ERR_TABLE) return;  // the regions do not fit: the host retries with a larger table
+  if (attempt_aborted(dsc)) return;  // e.g. the regions do not fit: the host retries with a larger table
   const int64_t nb = dsc->n_big;
   unsigned long long cons = 0;
   const int lane = threadIdx.x & 31;
@@ -627,9 +648,15 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
     sl[t] = (j <= b && jp <= b) ? a.reg_slot[(int64_t)s * 16 + j * 4 + jp] : -1;
   }
   if (FIRST) {
+    const uint64_t cap = *a.cap;
 #pragma unroll
-    for (int t = 0; t < NP; t++)
+    for (int t = 0; t < NP; t++) {
+      if (sl[t] >= 0 && (uint64_t)sl[t] >= cap) {
+        bounds_fail(a.dsc, 2);
+        sl[t] = -1;
+      }
       xi[t] = (sl[t] >= 0 && slot_flagged(a.flagbits, sl[t])) ? a.ptab[sl[t]].xidx : kNone;
+    }
     if (!accepted) {
 #pragma unroll
       for (int t = 0; t < NP; t++) {
@@ -644,6 +671,10 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
 #pragma unroll
   for (int t = 0; t < NP; t++) {
     if (xi[t] == kNone) continue;
+    if ((int64_t)xi[t] >= a.xcap) {
+      bounds_fail(a.dsc, FIRST ? 3 : 4);
+      continue;
+    }
     const int j = t / (C + 1), jp = t % (C + 1);
     ExactEnt* e = a.xtab + (int64_t)xi[t] * 16 + j * 4 + jp;
     if (accepted) atomicMin(&e->acc, (uint32_t)rank);
@@ -656,7 +687,8 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
 // first round replaces them by the exact-block indices.  The entries one
 // flagged probe may read are loaded together.
 template <int C, bool WITH_UND, bool FIRST>
-__device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const Rec& r, uint32_t pm, uint64_t tag) {
+__device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const Rec& r, uint32_t pm, uint64_t tag,
+                                           int where) {
   int res = 0;
   uint32_t xis[2][C + 1][C + 1];
 #pragma unroll
@@ -666,8 +698,17 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
 #pragma unroll
       for (int ip = 0; ip <= C; ip++) {
         const int bit = o * 16 + i * 4 + ip;
-        const int32_t v = (pm & (1u << bit)) ? a.pslot[(int64_t)s * 32 + bit] : -1;
-        xis[o][i][ip] = (FIRST && v >= 0) ? a.ptab[v].xidx : (uint32_t)v;
+        int32_t v = (pm & (1u << bit)) ? a.pslot[(int64_t)s * 32 + bit] : -1;
+        if (FIRST && v >= 0 && (uint64_t)v >= *a.cap) {
+          bounds_fail(a.dsc, 5);
+          v = -1;
+        }
+        uint32_t xv = (FIRST && v >= 0) ? a.ptab[v].xidx : (uint32_t)v;
+        if (xv != kNone && (int64_t)xv >= a.xcap) {
+          bounds_fail(a.dsc, FIRST ? 6 : 7, where, (int64_t)s * 64 + bit, (int64_t)xv);
+          xv = kNone;
+        }
+        xis[o][i][ip] = xv;
       }
   if (FIRST) {
 #pragma unroll
@@ -716,6 +757,7 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
 
 template <int C>
 __global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalars* dsc, int round) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
   // round 1 also registers the candidates phase A accepted; later rounds only
@@ -749,6 +791,7 @@ __global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalar
 
 template <int C>
 __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* dsc, int round) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
   const int64_t nb = *a.n_und;
@@ -759,8 +802,8 @@ __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* 
     if (a.state[s] != ST_UNDECIDED) continue;
     Rec r;
     load_rec(a.ra, s, C, r);
-    const int res = (round == 1) ? exact_probe<C, true, true>(a, s, r, a.pmask[s], tag)
-                                 : exact_probe<C, true, false>(a, s, r, a.pmask[s], tag);
+    const int res = (round == 1) ? exact_probe<C, true, true>(a, s, r, a.pmask[s], tag, round)
+                                 : exact_probe<C, true, false>(a, s, r, a.pmask[s], tag, round);
     if (res == 2) a.state[s] = ST_REJECTED;
     else if (res == 0) a.state[s] = ST_ACCEPTED_NEW;
     else waiting++;
@@ -774,6 +817,7 @@ __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* 
 template <int C>
 __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __restrict__ big_seg,
                                const int32_t* __restrict__ seg_begin, int last_round) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0 || a.und_count[last_round] == 0) return;
   const int64_t ns = dsc->n_big_seg;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ns; x += (int64_t)gridDim.x * blockDim.x) {
@@ -783,7 +827,7 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
       if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
       Rec r;
       load_rec(a.ra, s, C, r);
-      if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0) == 2) {
+      if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0, 99) == 2) {
         a.state[s] = ST_REJECTED;
         continue;
       }
@@ -796,6 +840,7 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
 __global__ void k_big_flags(const int32_t* __restrict__ big_pos, const uint8_t* __restrict__ state,
                             const int32_t* __restrict__ rec_rank, const DevScalars* __restrict__ dsc,
                             uint8_t* __restrict__ acc_flag) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t nb = dsc->n_big;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = big_pos[q];
@@ -869,7 +914,7 @@ int step_accept(Handle& h, int c) {
                                               h.seg_pref);
   const CoopArgs a{ra,        h.big_pos, h.state,   h.pmask,    h.reg_slot, h.pslot, h.ptab, h.xtab,
                    d_cap,     n_flag,    h.xcap,    und_count,  h.flagbits, h.und_list, n_und, h.pos_x,
-                   h.seg_pref};
+                   h.seg_pref, h.dsc};
   switch (c) {
     case 0: st = run_coop<0>(h, a, grid, R); break;
     case 1: st = run_coop<1>(h, a, grid, R); break;

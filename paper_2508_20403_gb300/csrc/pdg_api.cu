@@ -1,6 +1,7 @@
 // C ABI of the library (include/pdgrass.h): handle life cycle, input upload,
 // the recovery driver (steps A1-A7 on the handle's stream, with the prefix
 // retry of step A7) and small queries.
+#include <cstdio>
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -123,6 +124,7 @@ __global__ void k_reset_recover(DevScalars* dsc) {
 
 __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->err &= ERR_RANGE;
+  dsc->bounds_site = 0;
   dsc->rounds_used = 0;
   dsc->n_cand = 0;
   dsc->n_seg = 0;
@@ -460,6 +462,8 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       cudaStreamSynchronize(h.stream) != cudaSuccess)
     return fail(PDG_E_CUDA);
   h.want_h.assign(num_graphs, 0);
+  h.want_mem.assign(num_graphs, 0);
+  h.k_mem.assign(num_graphs, -1);
   *out = hp;
   return PDG_OK;
 }
@@ -478,6 +482,35 @@ int sparsify_init(pdg_handle* out, int64_t n, const int64_t* row_ptr, const int3
 namespace pdg {
 
 // The recovery driver shared by recover_offtree and recover_offtree_batch.
+// Diagnostics for a failed index check: where position p sits in the
+// segment and tier lists of the attempt that failed.
+static void debug_position(Handle& h, int64_t p) {
+  const int64_t N = h.hsc->n_cand, S = h.hsc->n_seg, NB = h.hsc->n_big, NBS = h.hsc->n_big_seg;
+  std::vector<int32_t> seg(S + 1), bpos(NB), bseg(NBS);
+  std::vector<uint8_t> st(N);
+  cudaMemcpy(seg.data(), h.seg_begin, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost);
+  cudaMemcpy(bpos.data(), h.big_pos, sizeof(int32_t) * NB, cudaMemcpyDeviceToHost);
+  cudaMemcpy(bseg.data(), h.big_seg, sizeof(int32_t) * NBS, cudaMemcpyDeviceToHost);
+  cudaMemcpy(st.data(), h.state, N, cudaMemcpyDeviceToHost);
+  int64_t q = std::upper_bound(seg.begin(), seg.end(), (int32_t)p) - seg.begin() - 1;
+  bool mono = true;
+  for (int64_t i = 0; i < S; i++)
+    if (seg[i + 1] <= seg[i]) mono = false;
+  const bool in_bpos = std::find(bpos.begin(), bpos.end(), (int32_t)p) != bpos.end();
+  const bool seg_big = std::find(bseg.begin(), bseg.end(), (int32_t)q) != bseg.end();
+  std::vector<char> seen(N, 0);
+  int64_t dup = 0;
+  for (int32_t v : bpos)
+    if (v >= 0 && v < N) dup += seen[v]++ ? 1 : 0;
+  int64_t big_total = 0;
+  for (int32_t x : bseg)
+    if (x >= 0 && x < S) big_total += seg[x + 1] - seg[x];
+  fprintf(stderr, "pdgrass debug: p %lld N %lld n_seg %lld mono %d seg %lld [%d, %d) in_big_pos %d seg_in_big_seg %d "
+                  "state %d n_big %lld sum_big_seg_sizes %lld dups %lld seg_end %d\n",
+          (long long)p, (long long)N, (long long)S, (int)mono, (long long)q, seg[q], seg[q + 1], (int)in_bpos,
+          (int)seg_big, (int)st[p], (long long)NB, (long long)big_total, (long long)dup, seg[S]);
+}
+
 static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, const int64_t* user_out_ptr,
                         int32_t* out_ids, double* out_scores, int out_mem_kind, int64_t* out_count,
                         int32_t* graph_status) {
@@ -516,6 +549,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
     total_k += take;
     int64_t want = (int64_t)std::ceil((double)k * h.opt.candidate_factor) + 32;
     if (want < k) want = k;
+    if (h.k_mem[g] == k && h.c_mem == c && h.mode_mem == h.opt.score_mode) want = std::max(want, h.want_mem[g]);
     h.want_h[g] = std::min(want, eoff[g]);
     s.k[g] = k;
     s.out_ptr[g] = user_out_ptr[g];
@@ -625,16 +659,26 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
     const int err = h.hsc->err;
     if (err & ERR_RANGE) return PDG_E_RANGE;
     if (err & ERR_TIMEOUT) return PDG_E_TIMEOUT;
-    if (err & ERR_CAPACITY) {
-      const int64_t wanted = h.hsc->n_cand_wanted;
-      if (wanted <= h.Rcap) return PDG_E_CUDA;  // inconsistent selection
-      if ((st = ensure_candidates(h, wanted + wanted / 8 + 4096, c))) return st;
-      continue;
-    }
     if (err & ERR_TABLE) {
       // pair table too small for the registrations, or too few exact blocks
       const int64_t slots = std::max<int64_t>(h.table_cap, 2 * h.hsc->big_regs + 16 * h.hsc->n_big_seg + 1024);
       if ((st = grow_tables(h, slots, 4 * h.xcap))) return st;
+      continue;
+    }
+    if (err & ERR_BOUNDS) {  // an internal index check failed (the access was skipped)
+      h.stats[11] = h.hsc->bounds_site;
+      if (getenv("PDG_DEBUG_BOUNDS"))
+        fprintf(stderr, "pdgrass: bounds check %d failed (round %d, pos*64+bit %lld, value %lld; n_big %lld, "
+                        "constrained %lld, rounds %d, attempt %d)\n", h.hsc->bounds_site, h.hsc->bounds_where,
+                (long long)h.hsc->bounds_pos, (long long)h.hsc->bounds_val, (long long)h.hsc->n_big,
+                (long long)h.hsc->n_constrained, h.hsc->rounds_used, attempts);
+      if (getenv("PDG_DEBUG_BOUNDS") && h.hsc->bounds_pos >= 0) debug_position(h, h.hsc->bounds_pos / 64);
+      return PDG_E_CUDA;
+    }
+    if (err & ERR_CAPACITY) {
+      const int64_t wanted = h.hsc->n_cand_wanted;
+      if (wanted <= h.Rcap) return PDG_E_CUDA;  // inconsistent selection
+      if ((st = ensure_candidates(h, wanted + wanted / 8 + 4096, c))) return st;
       continue;
     }
     if (err) return PDG_E_CUDA;
@@ -645,6 +689,12 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
         again = true;
       }
     if (!again) {
+      for (int32_t g = 0; g < G; g++) {
+        h.want_mem[g] = h.want_h[g];
+        h.k_mem[g] = kg[g];
+      }
+      h.c_mem = c;
+      h.mode_mem = h.opt.score_mode;
       if (first && !replayed && h.opt.use_graph && attempts == 1) {
         // this call needed one attempt: capture it for replay by later calls
         const cudaStream_t user = h.stream;

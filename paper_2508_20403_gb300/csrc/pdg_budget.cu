@@ -16,6 +16,7 @@ __global__ void k_budget_graph(const int64_t* __restrict__ scan, const int64_t* 
                                const int64_t* __restrict__ kk, const GraphSel* __restrict__ sel, int32_t G,
                                int32_t* __restrict__ gstat, int64_t* __restrict__ gcount,
                                const DevScalars* __restrict__ dsc) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_cand != cand_ptr[G]) return;  // selection overflowed: the host grows and repeats
   for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
     const int64_t cnt = scan[cand_ptr[g + 1]] - scan[cand_ptr[g]];
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(kBlock) k_budget_write(
     const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ rank_cand, const int32_t* __restrict__ cand_idx,
     const int32_t* __restrict__ off_id, const uint64_t* __restrict__ key, const int64_t* __restrict__ edge_ptr,
     const DevScalars* __restrict__ dsc, int32_t* __restrict__ out_ids, double* __restrict__ out_scores) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   if (N != cand_ptr[G]) return;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {

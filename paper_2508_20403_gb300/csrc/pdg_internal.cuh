@@ -33,6 +33,7 @@ enum : int {
   ERR_TIMEOUT = 64,
   ERR_CAPACITY = 128,
   ERR_TABLE = 256,
+  ERR_BOUNDS = 512,  // a saved index was out of range (checked and skipped; bounds_site says where)
 };
 
 // candidate state in the cooperative tier
@@ -42,6 +43,12 @@ enum : uint8_t { ST_UNDECIDED = 0, ST_ACCEPTED = 1, ST_REJECTED = 2, ST_ACCEPTED
 enum : int32_t { G_OK = 0, G_UNDER = 1, G_RETRY = 2 };
 
 // Scalars that kernels produce and the host reads back in one copy.
+// Errors that invalidate the current attempt: the host discards it (and
+// retries with larger tables where that helps).  Kernels that index with
+// data produced earlier in the attempt return at once when one is set, so an
+// attempt cut short never reads half-built structures.
+constexpr int kAbortErr = ERR_TABLE | ERR_TIMEOUT | ERR_BOUNDS;
+
 struct DevScalars {
   int32_t err;          // ERR_* bits
   int32_t e_min;        // min / max binary exponent of r = 1/w over tree edges
@@ -65,7 +72,14 @@ struct DevScalars {
   int64_t n_constrained;  // cooperative tier: candidates with a possible earlier marker
   int64_t n_big_chunk;    // cooperative tier: chunks of at most kBigChunk positions
   unsigned long long score_ticket;  // step A3: next tile of off-tree edges to score
+  int32_t bounds_site;  // first failed bounds check (see ERR_BOUNDS)
+  int32_t bounds_where;  // its round (99: serial finisher)
+  int64_t bounds_pos, bounds_val;  // its position and offending value
 };
+
+__device__ __forceinline__ bool attempt_aborted(const DevScalars* d) {
+  return (*reinterpret_cast<const volatile int32_t*>(&d->err) & kAbortErr) != 0;
+}
 
 // Cooperative tier: pair table slot (16 bytes; all-ones = empty) and exact
 // entry (16 bytes; 16 per flagged pair, indexed j * 4 + j').
@@ -155,6 +169,11 @@ struct Handle {
   uint32_t* hist = nullptr;  // G * kSelBins
   GraphSel* sel = nullptr;   // G
   std::vector<int64_t> want_h;  // requested prefix per graph
+  // prefix that sufficed per graph in the last call, for the budget k_mem and
+  // (c_mem, score mode mode_mem): a later call with the same parameters starts
+  // there (any prefix holding the first k recovered edges gives the same set)
+  std::vector<int64_t> want_mem, k_mem;
+  int c_mem = -1, mode_mem = -1;
   int64_t* d_cand_ptr = nullptr;  // G+1
   int64_t* d_graph_tmp = nullptr;  // G+1 scratch
 

@@ -255,6 +255,7 @@ namespace {
 __global__ void k_key_graph(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1, const int32_t* __restrict__ v0,
                             const int32_t* __restrict__ v1, const int64_t* __restrict__ cand_ptr, int32_t G,
                             DevScalars* dsc) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   uint64_t* k = dsc->radix_sel ? k1 : k0;
   const int32_t* v = dsc->radix_sel ? v1 : v0;
@@ -266,6 +267,7 @@ __global__ void k_key_graph(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1
 __global__ void k_key_lca(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1, int32_t* __restrict__ v0,
                           int32_t* __restrict__ v1, const int32_t* __restrict__ cand_idx,
                           const int32_t* __restrict__ lca, int32_t* __restrict__ rank_cand, DevScalars* dsc) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   uint64_t* k = dsc->radix_sel ? k1 : k0;
   int32_t* v = dsc->radix_sel ? v1 : v0;
@@ -279,6 +281,7 @@ __global__ void k_key_lca(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1, 
 
 __global__ void k_copy_vals(const int32_t* __restrict__ v0, const int32_t* __restrict__ v1, int32_t* __restrict__ out,
                             DevScalars* dsc) {
+  if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   const int32_t* v = dsc->radix_sel ? v1 : v0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)

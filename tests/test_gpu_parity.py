@@ -112,6 +112,26 @@ def test_retry_path_small_factor(B):
     assert stats["attempts"] >= 1
 
 
+def test_prefix_memory_across_calls(B):
+    """A call that needed a longer prefix remembers it: the next call with the
+    same budget starts there (one attempt) and returns the same edges; a call
+    with another budget still matches the oracle."""
+    g = W.grid_graph(60, seed=3)
+    o = B.default_options(candidate_factor=1.0)
+    ost, oids, osc, _ = O.recover(g, 0.2, c=2)
+    with B.Sparsifier.from_graph(g, options=o) as sp:
+        st, ids, sc, _ = sp.recover(0.2, 2, capacity=g.m)
+        first = sp.last_stats()
+        assert np.array(ids).tolist() == oids.tolist()
+        st, ids, sc, _ = sp.recover(0.2, 2, capacity=g.m)
+        second = sp.last_stats()
+        assert np.array(ids).tolist() == oids.tolist() and np.array_equal(np.array(sc), osc)
+        assert first["attempts"] > 1 and second["attempts"] == 1
+        ost2, oids2, _, _ = O.recover(g, 0.05, c=2)
+        st, ids, sc, _ = sp.recover(0.05, 2, capacity=g.m)
+        assert np.array(ids).tolist() == oids2.tolist()
+
+
 def test_under_budget(B):
     g = W.grid_graph(10, seed=4)
     st, ids, sc, _ = _gpu_recover(B, g, 0.0, c=2, k_override=g.n_offtree + 5)
