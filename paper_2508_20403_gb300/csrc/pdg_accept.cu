@@ -416,9 +416,10 @@ struct Region {
   uint64_t base, size;
 };
 
-__device__ __forceinline__ Region region_of(const CoopArgs& a, int32_t x) {
-  if (x < 0 || x >= a.dsc->n_big_seg) {
-    bounds_fail(a.dsc, 1);
+// (a subtask index outside [0, nbs) sets `bad`, which the caller reports)
+__device__ __forceinline__ Region region_of(const CoopArgs& a, int32_t x, int64_t nbs, bool& bad) {
+  if (x < 0 || x >= nbs) {
+    bad = true;
     x = 0;
   }
   const int64_t p0 = a.seg_pref[x], p1 = a.seg_pref[x + 1];
@@ -467,13 +468,14 @@ __global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ 
 template <int C>
 __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScalars* dsc) {
   if (attempt_aborted(dsc)) return;  // e.g. the regions do not fit: the host retries with a larger table
-  const int64_t nb = dsc->n_big;
+  const int64_t nb = dsc->n_big, nbs = dsc->n_big_seg;
+  bool bad = false;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.big_pos[q];
     Rec r;
     load_rec(a.ra, s, C, r);
     if (r.b == 0) continue;  // a 0-hop neighbourhood pair only matches the edge itself
-    const Region rg = region_of(a, a.pos_x[s]);
+    const Region rg = region_of(a, a.pos_x[s], nbs, bad);
     const uint32_t rend = (uint32_t)(rg.base + rg.size);
     constexpr int NP = (C + 1) * (C + 1);
     uint64_t key[NP];
@@ -513,6 +515,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
       a.reg_slot[(int64_t)s * 16 + j * 4 + jp] = (int32_t)slot[t];
     }
   }
+  if (bad) bounds_fail(dsc, 1);
 }
 
 // Phase A2: free candidates are recovered; probed pairs with an earlier
@@ -521,7 +524,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
 template <int C>
 __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars* dsc) {
   if (attempt_aborted(dsc)) return;  // e.g. the regions do not fit: the host retries with a larger table
-  const int64_t nb = dsc->n_big;
+  const int64_t nb = dsc->n_big, nbs = dsc->n_big_seg;
+  bool bad = false;
   unsigned long long cons = 0;
   const int lane = threadIdx.x & 31;
   // warp-uniform loop: every lane of a warp runs the same iterations
@@ -535,7 +539,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
     uint32_t pm = 0;
     int nclaim = 0;
     constexpr int NQ = (C + 1) * (C + 1);
-    const Region rg = valid ? region_of(a, a.pos_x[s]) : Region{0, 1};
+    const Region rg = valid ? region_of(a, a.pos_x[s], nbs, bad) : Region{0, 1};
     const uint32_t rend = (uint32_t)(rg.base + rg.size);
 #pragma unroll
     for (int o = 0; o < 2 && valid; o++) {
@@ -627,6 +631,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
   }
   for (int o = 16; o; o >>= 1) cons += __shfl_down_sync(0xffffffffu, cons, o);
   if ((threadIdx.x & 31) == 0 && cons) atomicAdd((unsigned long long*)&dsc->n_constrained, cons);
+  if (bad) bounds_fail(dsc, 1);
 }
 
 // exact registration of one candidate's flagged pairs (its pair slots, their
@@ -637,7 +642,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars
 // rounds and the finisher read directly.
 template <int C, bool FIRST>
 __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int b, int32_t rank, bool accepted,
-                                               uint64_t und_val) {
+                                               uint64_t und_val, uint64_t cap) {
   if (b == 0) return;  // never registered (matches only itself)
   constexpr int NP = (C + 1) * (C + 1);
   int32_t sl[NP];
@@ -647,12 +652,12 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
     const int j = t / (C + 1), jp = t % (C + 1);
     sl[t] = (j <= b && jp <= b) ? a.reg_slot[(int64_t)s * 16 + j * 4 + jp] : -1;
   }
+  uint32_t bad = 0;  // failed range checks (1: pair slot, 2: exact block), reported once below
   if (FIRST) {
-    const uint64_t cap = *a.cap;
 #pragma unroll
     for (int t = 0; t < NP; t++) {
       if (sl[t] >= 0 && (uint64_t)sl[t] >= cap) {
-        bounds_fail(a.dsc, 2);
+        bad |= 1u;
         sl[t] = -1;
       }
       xi[t] = (sl[t] >= 0 && slot_flagged(a.flagbits, sl[t])) ? a.ptab[sl[t]].xidx : kNone;
@@ -672,7 +677,7 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
   for (int t = 0; t < NP; t++) {
     if (xi[t] == kNone) continue;
     if ((int64_t)xi[t] >= a.xcap) {
-      bounds_fail(a.dsc, FIRST ? 3 : 4);
+      bad |= 2u;
       continue;
     }
     const int j = t / (C + 1), jp = t % (C + 1);
@@ -680,6 +685,7 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
     if (accepted) atomicMin(&e->acc, (uint32_t)rank);
     else atomicMin(&e->und, (unsigned long long)und_val);
   }
+  if (bad) bounds_fail(a.dsc, (bad & 1u) ? 2 : (FIRST ? 3 : 4), 0, s);
 }
 
 // exact probes: 2 = rejected, 1 = must wait, 0 = free of earlier markers.
@@ -688,9 +694,10 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
 // flagged probe may read are loaded together.
 template <int C, bool WITH_UND, bool FIRST>
 __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const Rec& r, uint32_t pm, uint64_t tag,
-                                           int where) {
+                                           int where, uint64_t cap) {
   int res = 0;
   uint32_t xis[2][C + 1][C + 1];
+  uint32_t bad = 0;  // failed range checks (1: pair slot, 2: exact block), reported once below
 #pragma unroll
   for (int o = 0; o < 2; o++)
 #pragma unroll
@@ -699,17 +706,18 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
       for (int ip = 0; ip <= C; ip++) {
         const int bit = o * 16 + i * 4 + ip;
         int32_t v = (pm & (1u << bit)) ? a.pslot[(int64_t)s * 32 + bit] : -1;
-        if (FIRST && v >= 0 && (uint64_t)v >= *a.cap) {
-          bounds_fail(a.dsc, 5);
+        if (FIRST && v >= 0 && (uint64_t)v >= cap) {
+          bad |= 1u;
           v = -1;
         }
         uint32_t xv = (FIRST && v >= 0) ? a.ptab[v].xidx : (uint32_t)v;
         if (xv != kNone && (int64_t)xv >= a.xcap) {
-          bounds_fail(a.dsc, FIRST ? 6 : 7, where, (int64_t)s * 64 + bit, (int64_t)xv);
+          bad |= 2u;
           xv = kNone;
         }
         xis[o][i][ip] = xv;
       }
+  if (bad) bounds_fail(a.dsc, (bad & 1u) ? 5 : (FIRST ? 6 : 7), where, s);
   if (FIRST) {
 #pragma unroll
     for (int o = 0; o < 2; o++)
@@ -764,6 +772,7 @@ __global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalar
   // touch the positions phase A left undecided
   const int64_t nb = (round == 1) ? dsc->n_big : *a.n_und;
   const int32_t* pos = (round == 1) ? a.big_pos : a.und_list;
+  const uint64_t cap = *a.cap;
   const uint64_t tag = und_tag(round);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = pos[q];
@@ -773,16 +782,16 @@ __global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalar
     const int32_t rank = a.ra.rank[s];
     if (round == 1) {
       if (st == ST_UNDECIDED) {
-        exact_register<C, true>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank);
+        exact_register<C, true>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank, cap);
       } else {
-        exact_register<C, true>(a, s, b, rank, true, 0);
+        exact_register<C, true>(a, s, b, rank, true, 0, cap);
         a.state[s] = ST_ACCEPTED;
       }
     } else {
       if (st == ST_UNDECIDED) {
-        exact_register<C, false>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank);
+        exact_register<C, false>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank, cap);
       } else {
-        exact_register<C, false>(a, s, b, rank, true, 0);
+        exact_register<C, false>(a, s, b, rank, true, 0, cap);
         a.state[s] = ST_ACCEPTED;
       }
     }
@@ -796,14 +805,15 @@ __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* 
   if (round > 1 && a.und_count[round - 1] == 0) return;
   const int64_t nb = *a.n_und;
   const uint64_t tag = und_tag(round);
+  const uint64_t cap = *a.cap;
   unsigned long long waiting = 0;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.und_list[q];
     if (a.state[s] != ST_UNDECIDED) continue;
     Rec r;
     load_rec(a.ra, s, C, r);
-    const int res = (round == 1) ? exact_probe<C, true, true>(a, s, r, a.pmask[s], tag, round)
-                                 : exact_probe<C, true, false>(a, s, r, a.pmask[s], tag, round);
+    const int res = (round == 1) ? exact_probe<C, true, true>(a, s, r, a.pmask[s], tag, round, cap)
+                                 : exact_probe<C, true, false>(a, s, r, a.pmask[s], tag, round, cap);
     if (res == 2) a.state[s] = ST_REJECTED;
     else if (res == 0) a.state[s] = ST_ACCEPTED_NEW;
     else waiting++;
@@ -820,6 +830,7 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
   if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0 || a.und_count[last_round] == 0) return;
   const int64_t ns = dsc->n_big_seg;
+  const uint64_t cap = *a.cap;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ns; x += (int64_t)gridDim.x * blockDim.x) {
     const int32_t q = big_seg[x];
     for (int32_t s = seg_begin[q]; s < seg_begin[q + 1]; s++) {
@@ -827,11 +838,11 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
       if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
       Rec r;
       load_rec(a.ra, s, C, r);
-      if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0, 99) == 2) {
+      if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0, 99, cap) == 2) {
         a.state[s] = ST_REJECTED;
         continue;
       }
-      exact_register<C, false>(a, s, r.b, r.rank, true, 0);
+      exact_register<C, false>(a, s, r.b, r.rank, true, 0, cap);
       a.state[s] = ST_ACCEPTED;
     }
   }

@@ -77,9 +77,8 @@ struct DevScalars {
   int64_t bounds_pos, bounds_val;  // its position and offending value
 };
 
-__device__ __forceinline__ bool attempt_aborted(const DevScalars* d) {
-  return (*reinterpret_cast<const volatile int32_t*>(&d->err) & kAbortErr) != 0;
-}
+// (set by earlier kernels of the stream, so a plain load sees it)
+__device__ __forceinline__ bool attempt_aborted(const DevScalars* d) { return (d->err & kAbortErr) != 0; }
 
 // Cooperative tier: pair table slot (16 bytes; all-ones = empty) and exact
 // entry (16 bytes; 16 per flagged pair, indexed j * 4 + j').
