@@ -19,7 +19,7 @@ constexpr int kItems = 8;           // items per thread in blocked tiles
 constexpr int kTile = kBlock * kItems;
 constexpr int kSelBins = 4096;      // 12-bit digits of the candidate selection
 constexpr int kRadixPassesMax = 16; // 8 score digits + <= 4 graph digits + <= 4 LCA digits
-constexpr int kRadixHistWords = 16 * 256 + kRadixPassesMax;
+constexpr int kRadixHistWords = 16 * 256 + 2 * kRadixPassesMax;  // + skip flags, buffer choices
 constexpr uint64_t kEmptyKey = ~0ull;
 
 // error bits raised by validation kernels (mapped to a status on the host)
@@ -184,9 +184,9 @@ struct Handle {
   int32_t* rank_cand = nullptr;    // rank -> candidate index
   int32_t* lsort_rank = nullptr;   // position in (lca, rank) order -> rank
   int64_t* scan_tmp = nullptr;     // Rcap + 1
-  uint32_t* radix_hist = nullptr;      // [8][256] histograms, [8][256] offsets, skip flags (fixed size)
+  uint32_t* radix_hist = nullptr;      // [8][256] histograms, [8][256] offsets, skip flags, buffer choices
   uint32_t* radix_status = nullptr;    // look-back words: kRadixPassesMax * tiles * 256
-  uint32_t* radix_counters = nullptr;  // per pass: tile ticket, blocks finished
+  uint32_t* radix_counters = nullptr;  // per pass: tile ticket (and one spare word)
   uint64_t* scan_status = nullptr;     // single-pass scan: flag | value per tile, zero between scans
   uint32_t* scan_ctr = nullptr;        // single-pass scan: tile ticket, blocks finished
   int64_t scan_tiles_cap = 0;

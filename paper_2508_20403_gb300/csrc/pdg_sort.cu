@@ -11,8 +11,8 @@
 //      index-linked lists per LCA, here a segment CSR).
 //
 // One-sweep LSD: one kernel histograms every digit position of a key set at
-// once, one kernel scans those histograms, and each pass is then a single
-// scatter kernel.  Its blocks take tiles in order from an atomic counter,
+// once, one kernel scans those histograms (and fixes which ping-pong buffer
+// each pass reads), and each pass is then a single scatter kernel.  Its blocks take tiles in order from an atomic counter,
 // rank the tile's digits stably (ballot peer masks + per-warp counters), publish the
 // tile's digit counts and obtain the counts of all earlier tiles by looking
 // back through published values ("decoupled look-back"), a window of tiles
@@ -28,16 +28,19 @@ namespace pdg {
 namespace {
 
 constexpr int kRdxBins = 256;
-// Scatter tiles are 512 threads x 4 keys = 2048 keys: at the candidate counts
-// of a recovery (10^5 .. 10^7 keys) a pass then spreads over all SMs, and a
-// warp ranks its keys in 4 rounds; the look-back reads 16 tiles per round trip.
+// Scatter tiles are 512 threads x 6 keys = 3072 keys and the look-back reads
+// 8 tiles per round trip: at the candidate counts of a recovery (10^5 .. 10^7
+// keys) a pass is a chain of dependent steps rather than a stream, and these
+// sizes gave the shortest passes on the 3 x 10^5-key mesh 128^3 sort among
+// 2048..8192-key tiles and 4..32-tile windows (fewer tiles shorten the
+// look-back chain; more keys per thread lengthen the ranking).
 constexpr int kOsThreads = 512;
-constexpr int kOsItems = 4;
+constexpr int kOsItems = 6;
 constexpr int kOsTile = kOsThreads * kOsItems;
 constexpr int kRdxWarps = kOsThreads / 32;
-constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // 128 items, 4 rounds of 32
+constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // 192 items, 6 rounds of 32
 constexpr int kMaxDigits = 8;
-constexpr int kLookWin = 16;  // look-back words fetched per round trip
+constexpr int kLookWin = 8;  // look-back words fetched per round trip
 constexpr uint32_t kFlagA = 1u << 30;  // tile aggregate published
 constexpr uint32_t kFlagP = 2u << 30;  // inclusive prefix published
 constexpr uint32_t kCountMask = (1u << 30) - 1;
@@ -65,11 +68,13 @@ __global__ void __launch_bounds__(kBlock) k_os_hist(const uint64_t* k0, const ui
 }
 
 // Exclusive scan of each digit's 256 bins (one warp per digit) and the
-// uniform-digit test; also clears the histogram for the next key set.
-__global__ void k_os_scan(uint32_t* __restrict__ ghist, int ndig, const DevScalars* dsc, uint32_t* __restrict__ goff,
-                          int32_t* __restrict__ skip) {
-  const int lane = threadIdx.x & 31, d = threadIdx.x >> 5;
-  if (d >= ndig) return;
+// uniform-digit test; also clears the histogram for the next key set.  The
+// passes' ping-pong buffer choices follow from the skips, so they are fixed
+// here (sel[d]: the buffer pass d reads) together with the final choice.
+__global__ void k_os_scan(uint32_t* __restrict__ ghist, int ndig, DevScalars* dsc, uint32_t* __restrict__ goff,
+                          int32_t* __restrict__ skip, int32_t* __restrict__ sel) {
+  __shared__ int32_t s_skip[kMaxDigits];
+  const int lane = threadIdx.x & 31, d = threadIdx.x >> 5;  // launched with 32 * ndig threads
   const uint32_t N = (uint32_t)dsc->n_cand;
   uint32_t v[8], s = 0;
   for (int i = 0; i < 8; i++) {
@@ -86,7 +91,19 @@ __global__ void k_os_scan(uint32_t* __restrict__ ghist, int ndig, const DevScala
     ghist[d * kRdxBins + lane * 8 + i] = 0;
   }
   uniform = __any_sync(0xffffffffu, uniform) || N == 0;
-  if (lane == 0) skip[d] = uniform ? 1 : 0;
+  if (lane == 0) {
+    skip[d] = uniform ? 1 : 0;
+    s_skip[d] = uniform ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int cur = dsc->radix_sel;
+    for (int q = 0; q < ndig; q++) {
+      sel[q] = cur;
+      if (!s_skip[q]) cur ^= 1;
+    }
+    dsc->radix_sel = cur;
+  }
 }
 
 // Dynamic shared memory of one scatter block: the tile's keys and values
@@ -98,7 +115,8 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0
                                                        const int32_t* v1, uint64_t* ko0, uint64_t* ko1, int32_t* vo0,
                                                        int32_t* vo1, DevScalars* dsc, int shift,
                                                        const uint32_t* __restrict__ goff, const int32_t* skip,
-                                                       uint32_t* status, uint32_t* counters, int64_t spin_limit) {
+                                                       const int32_t* selp, uint32_t* status, uint32_t* counters,
+                                                       int64_t spin_limit) {
   extern __shared__ __align__(16) unsigned char os_smem[];
   uint64_t* skey = reinterpret_cast<uint64_t*>(os_smem);                        // [kOsTile]
   int32_t* sval = reinterpret_cast<int32_t*>(skey + kOsTile);                   // [kOsTile]
@@ -108,9 +126,8 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0
   uint32_t* s_wsum = s_base + kRdxBins;    // per-warp totals of the digit scan
   __shared__ int64_t s_tile;
   const int64_t N = dsc->n_cand;
-  const int sel = dsc->radix_sel;
-  const bool moves = !*skip;
-  if (moves) {
+  const int sel = *selp;
+  if (!*skip) {
     const uint64_t* keys = sel ? k1 : k0;
     const int32_t* vals = sel ? v1 : v0;
     uint64_t* ko = sel ? ko0 : ko1;
@@ -234,12 +251,6 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0
       }
     }
   }
-  // the last block to finish flips the ping-pong buffers (if the pass moved data)
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&counters[1], 1u) == gridDim.x - 1 && moves) dsc->radix_sel = sel ^ 1;
-  }
 }
 
 }  // namespace
@@ -299,10 +310,11 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
   uint32_t* ghist = h.radix_hist;                // [8][256], kept zero between uses
   uint32_t* goff = h.radix_hist + 8 * kRdxBins;  // [8][256]
   int32_t* skip = reinterpret_cast<int32_t*>(h.radix_hist + 16 * kRdxBins) + pass0;
+  int32_t* sel = reinterpret_cast<int32_t*>(h.radix_hist + 16 * kRdxBins) + kRadixPassesMax + pass0;
   ++h.launches;
   k_os_hist<<<grid_hist, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.dsc, shift0, ndig, ghist);
   ++h.launches;
-  k_os_scan<<<1, 32 * ndig, 0, h.stream>>>(ghist, ndig, h.dsc, goff, skip);
+  k_os_scan<<<1, 32 * ndig, 0, h.stream>>>(ghist, ndig, h.dsc, goff, skip, sel);
   for (int d = 0; d < ndig; d++) {
     const int p = pass0 + d;
     uint32_t* status = h.radix_status + (int64_t)p * tiles_max * kRdxBins;
@@ -310,7 +322,7 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
     ++h.launches;
     k_os_scatter<<<(int)std::max<int64_t>(tiles_max, 1), kOsThreads, kOsSmem, h.stream>>>(
         h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.dsc, shift0 + 8 * d,
-        goff + d * kRdxBins, skip + d, status, counters, h.opt.spin_limit);
+        goff + d * kRdxBins, skip + d, sel + d, status, counters, h.opt.spin_limit);
   }
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
