@@ -68,7 +68,8 @@ typedef struct pdg_options {
   int32_t use_graph;        /* 1: capture the recovery pipeline in a CUDA graph and replay it */
   int64_t spin_limit;       /* iteration bound of every device-side wait */
   int32_t profile;          /* 1: time every step with CUDA events (see pdg_last_timings) */
-  int32_t reserved;
+  int32_t block_tier_max;   /* subtasks with warp_tier_max+1..block_tier_max candidates get one block each
+                               (shared-memory marker table); 0 turns the block tier off; at most 896 */
 } pdg_options;
 
 typedef struct pdg_sparsifier* pdg_handle; /* opaque, owned by the library */

@@ -18,6 +18,11 @@
 //                     iff no earlier survivor's bit is set in its mask) runs
 //                     as a 32-step shuffle loop -- the sequential semantics
 //                     without any shared-memory round trip;
+//   ..block_tier_max  one block per subtask, chunks of 32 in rank order: the
+//                     recovered candidates of earlier chunks are markers in
+//                     a shared-memory pair table, each chunk is resolved like
+//                     a warp-tier subtask (the paper's per-subtask marking,
+//                     with the marked set kept as ancestor pairs);
 //   larger            the cooperative tier: all candidates of all large
 //                     subtasks at once, in two phases over hash indexes.
 //
@@ -239,14 +244,16 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t value, int32_t* _
 // subtask is recorded.
 constexpr int kBigChunk = 1024;  // positions per warp when listing the cooperative tier
 
-__global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max,
+__global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* dsc, int warp_max, int block_max,
                            const int32_t* __restrict__ rec_rank, uint8_t* __restrict__ acc_flag,
-                           int32_t* __restrict__ warp_seg, int32_t* __restrict__ big_seg,
-                           int64_t* __restrict__ big_chunk, int64_t* __restrict__ seg_regs) {
+                           int32_t* __restrict__ warp_seg, int32_t* __restrict__ block_seg,
+                           int32_t* __restrict__ big_seg, int64_t* __restrict__ big_chunk,
+                           int64_t* __restrict__ seg_regs) {
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t S = dsc->n_seg;
   const int lane = threadIdx.x & 31;
   int64_t mx = 0;
+  unsigned long long nblk = 0;
   for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); q0 < S;
        q0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = q0 + lane;
@@ -254,8 +261,11 @@ __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
     const int64_t sz = (q < S) ? seg_begin[q + 1] - b : 0;
     if (sz == 1) acc_flag[rec_rank[b]] = 1;
     warp_append(sz >= 2 && sz <= warp_max, (int32_t)q, warp_seg, &dsc->n_warp_seg);
+    const bool blk = sz > warp_max && sz <= block_max;
+    warp_append(blk, (int32_t)q, block_seg, &dsc->n_block_seg);
+    nblk += blk ? sz : 0;
     // the cooperative subtask list (x = index in big_seg)
-    const bool big = sz > warp_max;
+    const bool big = sz > max(warp_max, block_max);
     const unsigned bm = __ballot_sync(0xffffffffu, big);
     int64_t x = -1;
     if (bm) {
@@ -283,6 +293,8 @@ __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
   }
   mx = __reduce_max_sync(0xffffffffu, (unsigned)min(mx, (int64_t)0x7fffffff));
   if (lane == 0 && mx) atomicMax((unsigned long long*)&dsc->max_seg, (unsigned long long)mx);
+  for (int o = 16; o; o >>= 1) nblk += __shfl_down_sync(0xffffffffu, nblk, o);
+  if (lane == 0 && nblk) atomicAdd((unsigned long long*)&dsc->n_block, nblk);
 }
 
 // One warp per chunk of a cooperative subtask: its positions join big_pos
@@ -366,15 +378,9 @@ __global__ void __launch_bounds__(kBlock) k_accept_warp(const int32_t* __restric
   }
 }
 
-// ------------------------------------------------------------- cooperative tier
-
 __device__ __forceinline__ uint64_t pair_key(int32_t z1, int32_t z2) {
   return ((uint64_t)(uint32_t)z1 << 32) | (uint64_t)(uint32_t)z2;
 }
-
-
-
-__device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
 
 // A saved index failed its range check: report (first site wins) and skip.
 __device__ __noinline__ void bounds_fail(DevScalars* dsc, int site, int where = 0, int64_t pos = -1,
@@ -386,6 +392,159 @@ __device__ __noinline__ void bounds_fail(DevScalars* dsc, int site, int where = 
   }
   atomicOr(&dsc->err, ERR_BOUNDS);
 }
+
+// ------------------------------------------------------------------ block tier
+//
+// One warp-sized block per subtask of warp_tier_max+1 .. block_tier_max
+// candidates, in chunks of 32 in rank order.  The RECOVERED candidates of the
+// earlier chunks live in a shared-memory marker table: a recovered e = (u, v)
+// with b = beta*_e enters every pair (anc_j(u), anc_j'(v)), j, j' <= b, with
+// the bit of its slack (b - j, b - j').  A later e' hits the pair at (i, i')
+// (its own ancestors anc_i, anc_i') exactly when i + j <= b and i' + j' <= b,
+// i.e. when some stored slack dominates (i, i') -- the same reach test as the
+// cooperative tier's exact entries, so a hit is a true marker and every
+// marker hits.  Inside a chunk the warp tier's conflict masks and 32-step
+// resolution decide the candidates that no earlier chunk marked; the
+// recovered ones then enter the table.  Sequential semantics, no global
+// atomics but the subtask ticket.
+
+constexpr uint32_t kSlackBits = 4;  // slack index s * 4 + s' (c <= 3)
+
+// slack bits (s, s') with s >= i and s' >= i'
+__device__ __forceinline__ uint32_t dominating(int i, int ip) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int s = 0; s < 4; s++)
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++)
+      if (s >= i && sp >= ip) m |= 1u << (s * kSlackBits + sp);
+  return m;
+}
+
+template <int C>
+__global__ void __launch_bounds__(32) k_accept_block(const int32_t* __restrict__ block_seg, DevScalars* dsc,
+                                                     const int32_t* __restrict__ seg_begin, RecArrays ra,
+                                                     int slots_log2, uint8_t* __restrict__ acc_flag) {
+  extern __shared__ __align__(16) unsigned char bt_smem[];
+  uint64_t* keys = reinterpret_cast<uint64_t*>(bt_smem);
+  uint32_t* slack = reinterpret_cast<uint32_t*>(keys + (1 << slots_log2));
+  if (attempt_aborted(dsc)) return;  // the attempt is void
+  const int lane = threadIdx.x;
+  const int64_t nb = dsc->n_block_seg;
+  bool bad = false;
+  for (;;) {
+    unsigned long long x = 0;
+    if (lane == 0) x = atomicAdd(&dsc->block_ticket, 1ull);
+    x = __shfl_sync(0xffffffffu, x, 0);
+    if ((int64_t)x >= nb) break;
+    const int32_t q = block_seg[x];
+    const int32_t b0 = seg_begin[q];
+    const int sz = seg_begin[q + 1] - b0;
+    // table of this subtask: load <= 1/2 even if every candidate is recovered
+    int tl = 6;
+    while ((1 << tl) < 2 * (C + 1) * (C + 1) * sz && tl < slots_log2) tl++;
+    const uint32_t tmask = (1u << tl) - 1;
+    for (int i = lane; i <= (int)tmask; i += 32) {
+      keys[i] = kEmptyKey;
+      slack[i] = 0;
+    }
+    __syncwarp();
+    for (int p0 = 0; p0 < sz; p0 += 32) {
+      const int n = min(32, sz - p0);
+      const bool valid = lane < n;
+      Rec me;
+      if (valid) {
+        load_rec(ra, b0 + p0 + lane, C, me);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kA; j++) me.U[j] = me.V[j] = -1;
+        me.du = me.dv = me.b = 0;
+        me.rank = 0;
+      }
+      // 1. markers recovered in earlier chunks
+      bool marked = false;
+      if (valid && p0 > 0) {
+#pragma unroll
+        for (int o = 0; o < 2; o++) {
+          if (o == 1 && me.du > 0 && me.dv > 0) break;  // records are side-ordered
+#pragma unroll
+          for (int i = 0; i <= C; i++)
+#pragma unroll
+            for (int ip = 0; ip <= C; ip++) {
+              const int32_t z1 = o ? me.V[i] : me.U[i], z2 = o ? me.U[ip] : me.V[ip];
+              if (marked || z1 < 0 || z2 < 0) continue;
+              const uint64_t key = pair_key(z1, z2);
+              uint32_t h = (uint32_t)mix64(key) & tmask;
+              for (uint32_t k = 0; k <= tmask; k++) {
+                const uint64_t kk = keys[h];
+                if (kk == key) {
+                  if (slack[h] & dominating(i, ip)) marked = true;
+                  break;
+                }
+                if (kk == kEmptyKey) break;
+                h = (h + 1) & tmask;
+              }
+            }
+        }
+      }
+      // 2. the chunk's own order among the candidates no earlier chunk marked
+      const unsigned live = __ballot_sync(0xffffffffu, valid && !marked);
+      unsigned mask = 0;  // bit s: my edge is strictly similar to lane s's edge (s < me)
+      for (int s2 = 0; s2 < n - 1; s2++) {
+        if (!((live >> s2) & 1u)) continue;  // uniform over the warp
+        int32_t U[kA], V[kA];
+#pragma unroll
+        for (int j = 0; j < kA; j++) {
+          U[j] = __shfl_sync(0xffffffffu, me.U[j], s2);
+          V[j] = __shfl_sync(0xffffffffu, me.V[j], s2);
+        }
+        const int bs = __shfl_sync(0xffffffffu, me.b, s2);
+        if (lane > s2 && ((live >> lane) & 1u) && strictly_similar(me.U, me.V, U, V, bs)) mask |= 1u << s2;
+      }
+      unsigned acc = 0;
+      for (int s2 = 0; s2 < n; s2++) {
+        const unsigned ms = __shfl_sync(0xffffffffu, mask, s2);
+        if (((live >> s2) & 1u) && (ms & acc) == 0) acc |= 1u << s2;
+      }
+      const bool accepted = (acc >> lane) & 1u;
+      if (valid) acc_flag[me.rank] = accepted ? 1 : 0;
+      // 3. the recovered candidates become markers for the later chunks
+      if (accepted && me.b > 0 && p0 + 32 < sz) {
+#pragma unroll
+        for (int j = 0; j <= C; j++)
+#pragma unroll
+          for (int jp = 0; jp <= C; jp++) {
+            if (j > me.b || jp > me.b) continue;
+            const uint64_t key = pair_key(me.U[j], me.V[jp]);
+            const uint32_t bit = 1u << ((me.b - j) * kSlackBits + (me.b - jp));
+            uint32_t h = (uint32_t)mix64(key) & tmask;
+            uint32_t k = 0;
+            for (; k <= tmask; k++) {
+              const unsigned long long old =
+                  atomicCAS(reinterpret_cast<unsigned long long*>(&keys[h]), (unsigned long long)kEmptyKey,
+                            (unsigned long long)key);
+              if (old == kEmptyKey || old == key) {
+                atomicOr(&slack[h], bit);
+                break;
+              }
+              h = (h + 1) & tmask;
+            }
+            if (k > tmask) bad = true;  // cannot happen at load <= 1/2
+          }
+      }
+      __syncwarp();
+    }
+    __syncwarp();  // the next subtask clears the table
+  }
+  if (bad) bounds_fail(dsc, 8);
+}
+
+// ------------------------------------------------------------- cooperative tier
+
+
+
+
+__device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
 
 struct CoopArgs {
   RecArrays ra;
@@ -883,6 +1042,22 @@ int run_coop(Handle& h, const CoopArgs& a, int grid, int rounds) {
 
 }  // namespace
 
+// The block tier's size bound for this c: the table of a subtask of S
+// candidates holds 2 (c+1)^2 S slots, at most kBlockTierSlots.
+static int block_tier_max(const Handle& h, int c) {
+  const int fit = kBlockTierSlots / (2 * (c + 1) * (c + 1));
+  return std::min(h.opt.block_tier_max, fit);
+}
+
+int accept_setup() {
+  const int smem = kBlockTierSlots * (int)(sizeof(uint64_t) + sizeof(uint32_t));
+  PDG_CUDA(cudaFuncSetAttribute(k_accept_block<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  PDG_CUDA(cudaFuncSetAttribute(k_accept_block<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  PDG_CUDA(cudaFuncSetAttribute(k_accept_block<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  PDG_CUDA(cudaFuncSetAttribute(k_accept_block<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return PDG_OK;
+}
+
 int step_accept(Handle& h, int c) {
   const int grid = h.num_sms * 8;
   const int64_t cap = h.Rcap;
@@ -900,8 +1075,10 @@ int step_accept(Handle& h, int c) {
   k_seg_starts<<<(int)std::max<int64_t>(lb_tiles, 1), kLbThreads, 0, h.stream>>>(
       h.rec_lca, h.dsc, h.seg_begin, h.scan_status, h.scan_ctr, h.opt.spin_limit);
   ++h.launches;
-  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, h.rec_rank, h.acc_flag,
-                                            h.warp_seg, h.big_seg, h.big_chunk, h.seg_regs);
+  const int block_max = block_tier_max(h, c);
+  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, block_max, h.rec_rank,
+                                            h.acc_flag, h.warp_seg, h.block_seg, h.big_seg, h.big_chunk,
+                                            h.seg_regs);
   ++h.launches;
   k_big_positions<<<grid, kBlock, 0, h.stream>>>(h.big_chunk, h.big_seg, h.seg_begin, h.dsc, h.rec_b, h.big_pos,
                                                  h.state, h.pos_x, h.seg_regs);
@@ -913,6 +1090,23 @@ int step_accept(Handle& h, int c) {
   ++h.launches;
   k_accept_warp<<<grid, kBlock, 0, h.stream>>>(h.warp_seg, h.dsc, h.seg_begin, c, ra, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
+  // block tier
+  if (block_max > h.opt.warp_tier_max) {
+    int tl = 6;
+    while ((1 << tl) < 2 * (c + 1) * (c + 1) * block_max) tl++;
+    const size_t smem = ((size_t)1 << tl) * (sizeof(uint64_t) + sizeof(uint32_t));
+    // as many one-warp blocks as the shared memory of an SM holds (227 KB, 1 KB reserved per block)
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(32, (size_t)(227 * 1024) / (smem + 1024)));
+    const int bgrid = h.num_sms * per_sm;
+    ++h.launches;
+    switch (c) {
+      case 0: k_accept_block<0><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+      case 1: k_accept_block<1><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+      case 2: k_accept_block<2><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+      default: k_accept_block<3><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+    }
+    PDG_CUDA(cudaGetLastError());
+  }
   // cooperative tier; blk_a[9800..9916) is reserved for it (other steps use [0, 9729))
   uint64_t* d_cap = reinterpret_cast<uint64_t*>(h.blk_a + 9800);
   int64_t* n_flag = h.blk_a + 9801;

@@ -129,6 +129,9 @@ __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->n_cand = 0;
   dsc->n_seg = 0;
   dsc->n_warp_seg = 0;
+  dsc->n_block_seg = 0;
+  dsc->block_ticket = 0;
+  dsc->n_block = 0;
   dsc->n_big = 0;
   dsc->n_big_seg = 0;
   dsc->max_seg = 0;
@@ -185,7 +188,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
   if (R > h.Rcap) {
     void* old[] = {h.cand_idx, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rank_cand, h.lsort_rank, h.scan_tmp,
                    h.radix_status, h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_rank,
-                   h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.big_pos, h.big_seg, h.big_chunk,
+                   h.rec_lca, h.rec_b, h.state, h.acc_flag, h.seg_begin, h.warp_seg, h.block_seg, h.big_pos, h.big_seg, h.big_chunk,
                    h.pos_x, h.seg_regs, h.seg_pref,
                    h.pmask, h.reg_slot, h.pslot, h.und_list};
     for (void* p : old) device_release(h, p);
@@ -199,7 +202,7 @@ int ensure_candidates(Handle& h, int64_t R, int c) {
         (st = alloc_n(h, &h.rec_du, R)) || (st = alloc_n(h, &h.rec_dv, R)) || (st = alloc_n(h, &h.rec_rank, R)) ||
         (st = alloc_n(h, &h.rec_lca, R)) || (st = alloc_n(h, &h.rec_b, R)) || (st = alloc_n(h, &h.state, R)) ||
         (st = alloc_n(h, &h.acc_flag, R)) || (st = alloc_n(h, &h.seg_begin, R + 1)) ||
-        (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) || (st = alloc_n(h, &h.big_chunk, R)) ||
+        (st = alloc_n(h, &h.warp_seg, R)) || (st = alloc_n(h, &h.block_seg, R)) || (st = alloc_n(h, &h.big_pos, R)) || (st = alloc_n(h, &h.big_seg, R)) || (st = alloc_n(h, &h.big_chunk, R)) ||
         (st = alloc_n(h, &h.pos_x, R)) || (st = alloc_n(h, &h.seg_regs, R)) || (st = alloc_n(h, &h.seg_pref, R + 1)) ||
         (st = alloc_n(h, &h.pmask, R)) || (st = alloc_n(h, &h.reg_slot, 16 * R)) || (st = alloc_n(h, &h.und_list, R)) ||
         (st = alloc_n(h, &h.pslot, 32 * R))) {
@@ -273,7 +276,7 @@ void pdg_default_options(pdg_options* opt) {
   opt->use_graph = 0;
   opt->spin_limit = 1ll << 26;
   opt->profile = 0;
-  opt->reserved = 0;
+  opt->block_tier_max = kBlockTierDefault;
 }
 
 const char* pdg_status_string(int status) {
@@ -338,6 +341,8 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
   Handle& h = hp->h;
   if (opt) h.opt = *opt; else pdg_default_options(&h.opt);
   if (h.opt.warp_tier_max < 1 || h.opt.warp_tier_max > 32) h.opt.warp_tier_max = 32;
+  if (h.opt.block_tier_max < 0) h.opt.block_tier_max = 0;
+  if (h.opt.block_tier_max > kBlockTierMax) h.opt.block_tier_max = kBlockTierMax;
   if (!(h.opt.candidate_factor >= 1.0)) h.opt.candidate_factor = 1.5;
   if (h.opt.max_rounds < 1) h.opt.max_rounds = 1;
   if (h.opt.max_rounds > 64) h.opt.max_rounds = 64;
@@ -359,7 +364,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
     sparsifier_free(hp);
     return code;
   };
-  if ((st = sort_setup())) return fail(st);
+  if ((st = sort_setup()) || (st = accept_setup())) return fail(st);
   const cudaMemcpyKind kind = (mem_kind == PDG_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   // nnz
   int64_t ends[2];

@@ -19,6 +19,12 @@ constexpr int kItems = 8;           // items per thread in blocked tiles
 constexpr int kTile = kBlock * kItems;
 constexpr int kSelBins = 4096;      // 12-bit digits of the candidate selection
 constexpr int kRadixPassesMax = 16; // 8 score digits + <= 4 graph digits + <= 4 LCA digits
+// Block tier: one block per subtask of warp_tier_max+1 .. block_tier_max
+// candidates, its markers in a shared-memory table of at most kBlockTierSlots
+// pair slots (12 bytes each); a subtask of S candidates needs 2 (c+1)^2 S.
+constexpr int kBlockTierSlots = 16384;
+constexpr int kBlockTierMax = 896;      // <= kBlockTierSlots / (2 * 9)
+constexpr int kBlockTierDefault = 0;  // off: on the mesh and R-MAT workloads the cooperative tier is faster
 constexpr int kRadixHistWords = 16 * 256 + 2 * kRadixPassesMax;  // + skip flags, buffer choices
 constexpr uint64_t kEmptyKey = ~0ull;
 
@@ -57,6 +63,9 @@ struct DevScalars {
   int64_t n_cand;       // candidates selected (all graphs)
   int64_t n_seg;        // subtasks among the candidates
   int64_t n_warp_seg;   // subtasks handled by the warp tier
+  int64_t n_block_seg;  // subtasks handled by the block tier
+  int64_t n_block;      // candidates in the block tier
+  unsigned long long block_ticket;  // block tier: next subtask to take
   int64_t n_big;        // candidates in the cooperative tier
   int64_t n_big_seg;    // subtasks in the cooperative tier
   int64_t max_seg;      // largest subtask
@@ -204,6 +213,7 @@ struct Handle {
   uint8_t* acc_flag = nullptr;   // accepted, by rank
   int32_t* seg_begin = nullptr;  // Rcap + 1
   int32_t* warp_seg = nullptr;   // subtasks of the warp tier
+  int32_t* block_seg = nullptr;  // subtasks of the block tier
   int32_t* big_pos = nullptr;    // positions of the cooperative tier
   int32_t* big_seg = nullptr;    // subtasks of the cooperative tier
   int64_t* big_chunk = nullptr;  // (subtask index << 32) | first position offset, one per chunk
@@ -422,6 +432,7 @@ int step_tree(Handle& h);                       // A2
 int step_score(Handle& h, int score_mode);      // A3
 int step_select(Handle& h);                     // A4a: candidate prefix per graph
 int sort_setup();                               // per-device kernel attributes of the sort
+int accept_setup();                             // per-device kernel attributes of the block tier
 int step_sort(Handle& h);                       // A4b: (graph, score desc, id asc) then (lca, rank)
 int step_accept(Handle& h, int c);              // A5 + A6
 int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7

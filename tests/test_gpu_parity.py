@@ -59,7 +59,8 @@ def test_random_small_graphs(B, seed):
         mode = int(rng.integers(0, 2))
         k = int(rng.integers(0, g.m + 1))
         wm = int(rng.choice([1, 2, 4, 32]))
-        _compare(B, g, 0.0, c=c, mode=mode, k_override=k, warp_tier_max=wm, candidate_factor=1.0)
+        bm = int(rng.choice([0, 3, 8, 896]))
+        _compare(B, g, 0.0, c=c, mode=mode, k_override=k, warp_tier_max=wm, block_tier_max=bm, candidate_factor=1.0)
 
 
 def test_scores_bit_exact_all_edges(B):
@@ -324,6 +325,18 @@ def test_mesh48_cooperative_tier_only(B):
     g = W.mesh3d_graph(48, seed=44)
     _compare(B, g, 0.1, warp_tier_max=1)
     _compare(B, g, 0.1, warp_tier_max=1, max_rounds=1)
+
+
+@pytest.mark.parametrize("wm,bm", [(1, 896), (32, 0), (32, 64), (8, 33), (32, 896)])
+def test_block_tier_bounds(B, wm, bm):
+    """The block tier (shared-memory markers, chunks of 32) against the oracle: every non-singleton subtask in
+    it, none, a band just above the warp tier, and the widest band (multi-chunk subtasks up to 896)."""
+    g = W.mesh3d_graph(48, seed=44)
+    stats = _compare(B, g, 0.1, warp_tier_max=wm, block_tier_max=bm)
+    assert stats["max_subtask"] > 64
+    g = W.rmat_graph(13, seed=77)
+    for c in (1, 2, 3):
+        _compare(B, g, 0.1, c=c, warp_tier_max=wm, block_tier_max=bm)
 
 
 @pytest.mark.parametrize("alpha", [0.02, 0.10])
