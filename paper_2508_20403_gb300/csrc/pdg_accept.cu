@@ -1049,6 +1049,12 @@ static int block_tier_max(const Handle& h, int c) {
   return std::min(h.opt.block_tier_max, fit);
 }
 
+int coop_rounds(const Handle& h, int c) {
+  int R = std::max(1, std::min(h.opt.max_rounds, 64));
+  if (h.rounds_mem > 0 && h.c_mem == c && h.mode_mem == h.opt.score_mode) R = std::min(R, h.rounds_mem + 1);
+  return R;
+}
+
 int accept_setup() {
   const int smem = kBlockTierSlots * (int)(sizeof(uint64_t) + sizeof(uint32_t));
   PDG_CUDA(cudaFuncSetAttribute(k_accept_block<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -1112,7 +1118,7 @@ int step_accept(Handle& h, int c) {
   int64_t* n_flag = h.blk_a + 9801;
   int64_t* und_count = h.blk_a + 9850;  // [0 .. max_rounds], max_rounds <= 64
   int64_t* n_und = h.blk_a + 9802;
-  const int R = std::max(1, std::min(h.opt.max_rounds, 64));
+  const int R = coop_rounds(h, c);
   PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
   ++h.launches;
   k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.flagbits, h.dsc, h.table_cap, d_cap, n_flag, n_und,

@@ -637,7 +637,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
     }
     if ((st = ensure_candidates(h, std::max<int64_t>(h.Rcap, need + need / 4 + 4096), c))) return st;
     // the launch sequence a CUDA graph bakes in
-    const GraphKey key{c, h.opt.score_mode, any_select ? 1 : 0, h.Rcap, h.table_cap, h.xcap,
+    const GraphKey key{c, h.opt.score_mode, any_select ? 1 : 0, coop_rounds(h, c), h.Rcap, h.table_cap, h.xcap,
                        (void*)dev_ids, (void*)dev_scores, out_total};
     bool replayed = false;
     if (first && h.opt.use_graph && h.gexec && key == h.gkey) {
@@ -700,6 +700,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
       }
       h.c_mem = c;
       h.mode_mem = h.opt.score_mode;
+      h.rounds_mem = h.hsc->rounds_used;
       if (first && !replayed && h.opt.use_graph && attempts == 1) {
         // this call needed one attempt: capture it for replay by later calls
         const cudaStream_t user = h.stream;
@@ -716,6 +717,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
             h.gexec = nullptr;
             if (cudaGraphInstantiate(&h.gexec, graph, 0) == cudaSuccess) {
               h.gkey = key;
+              h.gkey.rounds = coop_rounds(h, c);  // the capture already used the remembered round count
               h.glaunches = h.launches;
             } else {
               h.gexec = nullptr;

@@ -117,13 +117,13 @@ struct GraphSel {
 // What a captured recovery graph depends on besides the pinned parameters it
 // reads at replay time (budgets, prefix sizes, output offsets).
 struct GraphKey {
-  int c = -1, score_mode = -1, any_select = -1;
+  int c = -1, score_mode = -1, any_select = -1, rounds = -1;
   int64_t Rcap = -1, table_cap = -1, xcap = -1;
   void* out_ids = nullptr;
   void* out_scores = nullptr;
   int64_t out_total = -1;
   bool operator==(const GraphKey& o) const {
-    return c == o.c && score_mode == o.score_mode && any_select == o.any_select && Rcap == o.Rcap &&
+    return c == o.c && score_mode == o.score_mode && any_select == o.any_select && rounds == o.rounds && Rcap == o.Rcap &&
            table_cap == o.table_cap && xcap == o.xcap && out_ids == o.out_ids && out_scores == o.out_scores &&
            out_total == o.out_total;
   }
@@ -182,6 +182,10 @@ struct Handle {
   // there (any prefix holding the first k recovered edges gives the same set)
   std::vector<int64_t> want_mem, k_mem;
   int c_mem = -1, mode_mem = -1;
+  // cooperative-tier rounds the last recovery with (c_mem, mode_mem) ran; a
+  // later one launches one round more than that (the serial finisher
+  // completes whatever a short round count leaves, so any count is exact)
+  int rounds_mem = 0;
   int64_t* d_cand_ptr = nullptr;  // G+1
   int64_t* d_graph_tmp = nullptr;  // G+1 scratch
 
@@ -433,6 +437,7 @@ int step_score(Handle& h, int score_mode);      // A3
 int step_select(Handle& h);                     // A4a: candidate prefix per graph
 int sort_setup();                               // per-device kernel attributes of the sort
 int accept_setup();                             // per-device kernel attributes of the block tier
+int coop_rounds(const Handle& h, int c);        // cooperative-tier rounds the next recovery launches
 int step_sort(Handle& h);                       // A4b: (graph, score desc, id asc) then (lca, rank)
 int step_accept(Handle& h, int c);              // A5 + A6
 int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7

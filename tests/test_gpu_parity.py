@@ -133,6 +133,20 @@ def test_prefix_memory_across_calls(B):
         assert np.array(ids).tolist() == oids2.tolist()
 
 
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_round_memory_across_budgets(B, use_graph):
+    """A handle launches one cooperative round more than its last recovery needed; a later budget that needs
+    more rounds leaves the rest to the serial finisher and must still match the oracle, replayed or not."""
+    g = W.rmat_graph(13, seed=77)
+    o = B.default_options(use_graph=use_graph)
+    with B.Sparsifier.from_graph(g, options=o) as sp:
+        for alpha in (0.02, 0.02, 0.5, 0.5, 0.1, 0.02, 0.5):
+            _, oids, osc, _ = O.recover(g, alpha, c=2)
+            st, ids, sc, _ = sp.recover(alpha, 2, capacity=g.m)
+            assert np.array(ids).tolist() == oids.tolist(), (alpha, sp.last_stats())
+            assert np.array_equal(np.array(sc), osc)
+
+
 def test_under_budget(B):
     g = W.grid_graph(10, seed=4)
     st, ids, sc, _ = _gpu_recover(B, g, 0.0, c=2, k_override=g.n_offtree + 5)
