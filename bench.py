@@ -255,7 +255,11 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
     log(f"[rank {rank}] generated {g.name} n={g.n} m={g.m} E_off={g.n_offtree} in {time.time() - t0:.1f}s")
     k = int(math.floor(args.alpha * g.n))
     # timed handle: the recovery is captured once and replayed as a CUDA graph
-    opt = B.default_options(use_graph=0 if args.no_graph else 1)
+    # launch shape (tier bounds, sort tiles) from the autotuner's cache for this GPU and graph class
+    from paper_2508_20403_gb300 import autotune as AT
+
+    opt = AT.options_for(g, use_graph=0 if args.no_graph else 1)
+    tuned = {k: getattr(opt, k) for k in AT.SPACE}
     sp = B.Sparsifier.from_graph(g, device=True, options=opt, stream=stream)
     info = sp.info()
     out_ids = torch.zeros(max(k, 1), dtype=torch.int32, device=dev)
@@ -289,7 +293,7 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
     stats = sp.last_stats()
     sp.close()
     # per-step breakdown: a second handle, launched step by step with CUDA events
-    sp = B.Sparsifier.from_graph(g, device=True, options=B.default_options(profile=1), stream=stream)
+    sp = B.Sparsifier.from_graph(g, device=True, options=AT.options_for(g, profile=1), stream=stream)
     for i in range(args.warmup + args.steps):
         flush.fill_(i & 0xff)
         one()
@@ -324,6 +328,8 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
         "min_ms": float(np.min(times)), "median_ms": float(np.median(times)),
         "step_ms": {nm: round(avg[nm], 4) for nm in names},
         "recovery_stats": stats,
+        "launch_shape": dict(tuned, source="autotune cache" if AT.lookup(AT.load_cache(), AT.device_key(),
+                                                                          AT.class_of(g)) else "defaults"),
         "roofline": {"bound": "hbm", "kernel": DOMINANT_KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes": dom_bytes, "duration_ms": dom_ms},
@@ -364,7 +370,9 @@ def batch_leg(args, graphs, dev, B, torch):
     G = len(graphs)
     alphas = np.full(G, args.batch_alpha)
     e_off = int(sum(g.n_offtree for g in graphs))
-    opt = B.default_options(use_graph=1)
+    from paper_2508_20403_gb300 import autotune as AT
+
+    opt = AT.options_for(pk, use_graph=1)  # the autotuner's launch shape for this class, if cached
     bs = B.BatchSparsifier.from_packed(pk, device=True, options=opt, stream=stream)
     op = bs.out_ptr_for(alphas)
     out = torch.zeros(max(int(op[-1]), 1), dtype=torch.int32, device=dev)
@@ -406,6 +414,7 @@ def batch_leg(args, graphs, dev, B, torch):
     mb, mp = float(np.mean(tb)), float(np.mean(tp))
     return {"graphs": G, "n": int(pk.n), "m": int(sum(g.m for g in graphs)), "n_offtree": e_off,
             "alpha": args.batch_alpha, "c": args.c, "identical_output": bool(identical),
+            "launch_shape": {k: getattr(opt, k) for k in AT.SPACE}, "graph_class": AT.class_of(pk),
             "batched": {"ms": mb, "graphs_per_s": G / (mb / 1e3), "edges_per_s": e_off / (mb / 1e3),
                         "launch": "one recover_offtree_batch (CUDA graph replay)", "stats": bstats},
             "per_graph": {"ms": mp, "graphs_per_s": G / (mp / 1e3), "edges_per_s": e_off / (mp / 1e3),

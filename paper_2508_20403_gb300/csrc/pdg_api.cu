@@ -277,6 +277,8 @@ void pdg_default_options(pdg_options* opt) {
   opt->spin_limit = 1ll << 26;
   opt->profile = 0;
   opt->block_tier_max = kBlockTierDefault;
+  opt->sort_tile_keys = 3072;
+  opt->reserved = 0;
 }
 
 const char* pdg_status_string(int status) {
@@ -343,6 +345,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
   if (h.opt.warp_tier_max < 1 || h.opt.warp_tier_max > 32) h.opt.warp_tier_max = 32;
   if (h.opt.block_tier_max < 0) h.opt.block_tier_max = 0;
   if (h.opt.block_tier_max > kBlockTierMax) h.opt.block_tier_max = kBlockTierMax;
+  if (h.opt.sort_tile_keys != 2048 && h.opt.sort_tile_keys != 4096) h.opt.sort_tile_keys = 3072;
   if (!(h.opt.candidate_factor >= 1.0)) h.opt.candidate_factor = 1.5;
   if (h.opt.max_rounds < 1) h.opt.max_rounds = 1;
   if (h.opt.max_rounds > 64) h.opt.max_rounds = 64;

@@ -34,18 +34,17 @@ constexpr int kRdxBins = 256;
 // sizes gave the shortest passes on the 3 x 10^5-key mesh 128^3 sort among
 // 2048..8192-key tiles and 4..32-tile windows (fewer tiles shorten the
 // look-back chain; more keys per thread lengthen the ranking).
+// The keys per thread are a template parameter (4, 6 or 8: 2048, 3072 or
+// 4096-key tiles) that the sort_tile_keys option, and so the autotuner, picks.
 constexpr int kOsThreads = 512;
-constexpr int kOsItems = 6;
-constexpr int kOsTile = kOsThreads * kOsItems;
+constexpr int kOsItemsDefault = 6;
 constexpr int kRdxWarps = kOsThreads / 32;
-constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // 192 items, 6 rounds of 32
 constexpr int kMaxDigits = 8;
 constexpr int kLookWin = 8;  // look-back words fetched per round trip
 constexpr uint32_t kFlagA = 1u << 30;  // tile aggregate published
 constexpr uint32_t kFlagP = 2u << 30;  // inclusive prefix published
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 
-__device__ __forceinline__ int64_t tiles_of(int64_t N) { return (N + kOsTile - 1) / kOsTile; }
 
 // Histograms of `ndig` digit positions (starting at bit `shift0`) of the keys
 // in the current buffer: ghist[d][bin].
@@ -108,15 +107,20 @@ __global__ void k_os_scan(uint32_t* __restrict__ ghist, int ndig, DevScalars* ds
 
 // Dynamic shared memory of one scatter block: the tile's keys and values
 // bucketed by digit, the per-warp digit counters and the per-digit offsets.
-constexpr size_t kOsSmem = (size_t)kOsTile * (sizeof(uint64_t) + sizeof(int32_t)) +
-                           sizeof(uint32_t) * ((size_t)kRdxWarps * kRdxBins + 2 * kRdxBins + 32);
+constexpr size_t os_smem_bytes(int items) {
+  return (size_t)kOsThreads * items * (sizeof(uint64_t) + sizeof(int32_t)) +
+         sizeof(uint32_t) * ((size_t)kRdxWarps * kRdxBins + 2 * kRdxBins + 32);
+}
 
+template <int kOsItems>
 __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0, const uint64_t* k1, const int32_t* v0,
                                                        const int32_t* v1, uint64_t* ko0, uint64_t* ko1, int32_t* vo0,
                                                        int32_t* vo1, DevScalars* dsc, int shift,
                                                        const uint32_t* __restrict__ goff, const int32_t* skip,
                                                        const int32_t* selp, uint32_t* status, uint32_t* counters,
                                                        int64_t spin_limit) {
+  constexpr int kOsTile = kOsThreads * kOsItems;
+  constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // kOsItems rounds of 32
   extern __shared__ __align__(16) unsigned char os_smem[];
   uint64_t* skey = reinterpret_cast<uint64_t*>(os_smem);                        // [kOsTile]
   int32_t* sval = reinterpret_cast<int32_t*>(skey + kOsTile);                   // [kOsTile]
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0
     const int32_t* vals = sel ? v1 : v0;
     uint64_t* ko = sel ? ko0 : ko1;
     int32_t* vo = sel ? vo0 : vo1;
-    const int64_t T = tiles_of(N);
+    const int64_t T = (N + kOsTile - 1) / kOsTile;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1;
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&counters[0], 1u);  // tiles in launch order
@@ -256,7 +260,9 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0
 }  // namespace
 
 int sort_setup() {
-  PDG_CUDA(cudaFuncSetAttribute(k_os_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsSmem));
+  PDG_CUDA(cudaFuncSetAttribute(k_os_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem_bytes(4)));
+  PDG_CUDA(cudaFuncSetAttribute(k_os_scatter<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem_bytes(6)));
+  PDG_CUDA(cudaFuncSetAttribute(k_os_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem_bytes(8)));
   return PDG_OK;
 }
 
@@ -301,12 +307,27 @@ __global__ void k_copy_vals(const int32_t* __restrict__ v0, const int32_t* __res
 
 }  // namespace
 
+// keys per thread of the scatter tiles (option sort_tile_keys = 2048, 3072 or 4096)
+static int sort_items(const Handle& h) {
+  switch (h.opt.sort_tile_keys) {
+    case 2048: return 4;
+    case 4096: return 8;
+    default: return kOsItemsDefault;
+  }
+}
+
+static int64_t sort_tiles(const Handle& h) {
+  const int64_t tile = (int64_t)kOsThreads * sort_items(h);
+  return (h.Rcap + tile - 1) / tile;
+}
+
 // Sort the current key buffer by `ndig` 8-bit digits starting at bit shift0;
 // `pass0` indexes this key set's passes in the status / skip / counter arrays.
 static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
   if (ndig <= 0) return PDG_OK;  // a single possible key value: already sorted
   const int grid_hist = h.num_sms * 2;
-  const int64_t tiles_max = (h.Rcap + kOsTile - 1) / kOsTile;
+  const int64_t tiles_max = sort_tiles(h);
+  const int items = sort_items(h);
   uint32_t* ghist = h.radix_hist;                // [8][256], kept zero between uses
   uint32_t* goff = h.radix_hist + 8 * kRdxBins;  // [8][256]
   int32_t* skip = reinterpret_cast<int32_t*>(h.radix_hist + 16 * kRdxBins) + pass0;
@@ -320,9 +341,15 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
     uint32_t* status = h.radix_status + (int64_t)p * tiles_max * kRdxBins;
     uint32_t* counters = h.radix_counters + 2 * p;
     ++h.launches;
-    k_os_scatter<<<(int)std::max<int64_t>(tiles_max, 1), kOsThreads, kOsSmem, h.stream>>>(
-        h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.dsc, shift0 + 8 * d,
-        goff + d * kRdxBins, skip + d, sel + d, status, counters, h.opt.spin_limit);
+    const int grid = (int)std::max<int64_t>(tiles_max, 1);
+#define PDG_OS_SCATTER(I)                                                                                    \
+  k_os_scatter<I><<<grid, kOsThreads, os_smem_bytes(I), h.stream>>>(                                         \
+      h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.dsc, shift0 + 8 * d,         \
+      goff + d * kRdxBins, skip + d, sel + d, status, counters, h.opt.spin_limit)
+    if (items == 4) PDG_OS_SCATTER(4);
+    else if (items == 8) PDG_OS_SCATTER(8);
+    else PDG_OS_SCATTER(6);
+#undef PDG_OS_SCATTER
   }
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
@@ -330,7 +357,7 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
 
 int step_sort(Handle& h) {
   const int grid = h.num_sms * 4;
-  const int64_t tiles_max = (h.Rcap + kOsTile - 1) / kOsTile;
+  const int64_t tiles_max = sort_tiles(h);
   // look-back status and tile counters start clean for every pass
   PDG_CUDA(cudaMemsetAsync(h.radix_status, 0, sizeof(uint32_t) * (size_t)kRadixPassesMax * tiles_max * kRdxBins,
                            h.stream));

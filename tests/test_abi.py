@@ -67,3 +67,29 @@ def test_library_is_required_not_replaced(tmp_path):
 
     with pytest.raises(ImportError):
         binding.load(str(tmp_path / "missing.so"))
+
+
+def test_options_layout_matches_header(tmp_path):
+    """The ctypes mirror of pdg_options has the C struct's size and field offsets (compiled from the header)."""
+    import shutil
+    import subprocess
+
+    from paper_2508_20403_gb300 import binding
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in binding.Options._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdgrass.h"', "int main(void) {",
+             '  printf("size %zu\\n", sizeof(pdg_options));']
+    lines += [f'  printf("{f} %zu\\n", offsetof(pdg_options, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call([cc, "-I", inc, str(src), "-o", str(exe)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(out["size"]) == ctypes.sizeof(binding.Options)
+    for f in fields:
+        assert int(out[f]) == getattr(binding.Options, f).offset, f

@@ -353,6 +353,21 @@ def test_block_tier_bounds(B, wm, bm):
         _compare(B, g, 0.1, c=c, warp_tier_max=wm, block_tier_max=bm)
 
 
+@pytest.mark.parametrize("keys", [2048, 4096])
+def test_sort_tile_sizes(B, keys):
+    """The radix-sort scatter tiles the autotuner may pick (2048 / 4096 keys; 3072 is the default everywhere
+    else) sort exactly: mesh and R-MAT against the oracle, and a packed batch against its graphs one by one."""
+    _compare(B, W.mesh3d_graph(48, seed=44), 0.1, sort_tile_keys=keys)
+    _compare(B, W.rmat_graph(13, seed=77), 0.5, sort_tile_keys=keys)
+    graphs = [W.batch_member(i, n_hi=3e4) for i in range(6)]
+    pk = W.pack_graphs(graphs)
+    with B.BatchSparsifier.from_packed(pk, options=B.default_options(sort_tile_keys=keys)) as bs:
+        st, op, ids, sc, counts, gst = bs.recover_batch(np.full(len(graphs), 0.1), c=2)
+    for i, g in enumerate(graphs):
+        _, oids, osc, _ = O.recover(g, 0.1, c=2)
+        assert np.array(ids[op[i]:op[i] + counts[i]]).tolist() == oids.tolist()
+
+
 @pytest.mark.parametrize("alpha", [0.02, 0.10])
 def test_rmat16(B, alpha):
     _compare(B, W.rmat_graph(16, seed=16), alpha)
