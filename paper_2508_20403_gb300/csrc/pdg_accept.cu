@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
 // registrant are flagged and get a block of exact entries.  Lookups advance
 // together, one slot per round, like the inserts of phase A1.
 template <int C>
-__global__ void __launch_bounds__(kBlock, 3) k_pair_probe(CoopArgs a, DevScalars* dsc) {
+__global__ void __launch_bounds__(kBlock, 4) k_pair_probe(CoopArgs a, DevScalars* dsc) {
   if (attempt_aborted(dsc)) return;  // e.g. the regions do not fit: the host retries with a larger table
   const int64_t nb = dsc->n_big, nbs = dsc->n_big_seg;
   bool bad = false;
