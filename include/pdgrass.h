@@ -239,6 +239,36 @@ int pdg_last_timings(pdg_handle h, float* ms);
  * current; make that first call before any stream capture.
  * Returns PDG_OK, PDG_E_INVALID_ARG (bad size or id) or PDG_E_CUDA.
  */
+/*
+ * pdg_spanning_tree -- generate the spanning tree that recovery starts from
+ * (Sec. 2.2: feGRASS's first step builds the tree from the effective weight,
+ * Eq. weff; the plain maximum-weight tree is the other common choice).
+ *
+ *   n, row_ptr, col, w, mem_kind  the graph, as in sparsify_init (symmetric
+ *                 CSR, sorted rows, no self loops, weights in [2^-900, 2^900]).
+ *   tree_kind     PDG_TREE_MAX_WEIGHT: the maximum spanning forest for the
+ *                 order (w descending, canonical edge id ascending);
+ *                 PDG_TREE_FEGRASS: the maximum spanning tree for the order
+ *                 (W_eff descending, id ascending) with
+ *                 W_eff(e) = fl(fl(w * fl(log(max(deg u, deg v)))) / (d(u) + d(v))),
+ *                 d = unweighted BFS distance from the maximum-degree vertex
+ *                 (the graph must be connected).
+ *   parent_out    int32[n]: the tree as a parent array, each component rooted
+ *                 at its maximum-degree vertex (ties: smaller id), -1 there.
+ *   out_mem_kind  memory kind of parent_out.
+ *   stream        cudaStream_t for the device work.
+ *
+ * Both orders are strict, so the tree is unique and the call deterministic.
+ * Device memory is allocated for the call and released before it returns.
+ * Returns PDG_OK, PDG_E_INVALID_ARG (bad arguments, or PDG_TREE_FEGRASS on a
+ * disconnected graph), PDG_E_NOT_CSR, PDG_E_NOT_SYMMETRIC, PDG_E_BAD_WEIGHT,
+ * PDG_E_OOM or PDG_E_CUDA.
+ */
+#define PDG_TREE_MAX_WEIGHT 0
+#define PDG_TREE_FEGRASS 1
+int pdg_spanning_tree(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, int mem_kind,
+                      int tree_kind, int32_t* parent_out, int out_mem_kind, void* stream);
+
 #define PDG_NOALLOC_MAX_N (1 << 21)
 int pdg_edge_endpoints_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* ids,
                                int64_t count, int32_t* u, int32_t* v, void* stream);

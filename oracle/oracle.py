@@ -25,6 +25,8 @@ SCORE_STRETCH = 0
 SCORE_RESISTANCE = 1
 METHOD_WALK = 0
 METHOD_DISTS = 1
+TREE_MAX_WEIGHT = 0
+TREE_FEGRASS = 1
 
 
 def build(force: bool = False) -> str:
@@ -49,6 +51,8 @@ def lib():
             L.orc_exact_sum.argtypes = [P, i64]
             L.orc_offtree_scores.restype = ctypes.c_int
             L.orc_offtree_scores.argtypes = [i64, P, P, P, P, i32, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P, P]
+            L.orc_spanning_tree.restype = ctypes.c_int
+            L.orc_spanning_tree.argtypes = [i64, P, P, P, ctypes.c_int, P]
             L.orc_recover.restype = ctypes.c_int
             L.orc_recover.argtypes = [i64, P, P, P, P, f64, i32, ctypes.c_int, i64, P, P, i64, P, P]
             _lib = L
@@ -104,3 +108,16 @@ def recover(g, alpha: float, c: int = 2, score_mode: int = SCORE_STRETCH, k_over
         raise RuntimeError(f"oracle recover failed: {st}")
     k = int(cnt[0])
     return st, ids[:k].copy(), sc[:k].copy(), (int(full[0]) if full_count else None)
+
+
+def spanning_tree(g, kind: int = TREE_MAX_WEIGHT) -> np.ndarray:
+    """Parent array of the maximum spanning forest for (key desc, id asc), key = w (TREE_MAX_WEIGHT) or the
+    effective weight of Eq. weff (TREE_FEGRASS), each component rooted at its maximum-degree vertex."""
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    w = np.ascontiguousarray(g.w, dtype=np.float64)
+    parent = np.zeros(g.n, dtype=np.int32)
+    st = lib().orc_spanning_tree(g.n, _p(rp), _p(col), _p(w), int(kind), _p(parent))
+    if st != OK:
+        raise ValueError(f"oracle spanning_tree failed: {st}")
+    return parent

@@ -723,3 +723,184 @@ done:
   tree_free(&t);
   return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Spanning-tree generation, the step before recovery (Sec. 2.2: feGRASS     */
+/* first builds a spanning tree from the effective weight of Eq. weff).      */
+/*                                                                            */
+/* Kruskal: visit the edges in the order (key descending, canonical edge id  */
+/* ascending) and keep every edge that joins two different trees of the      */
+/* forest built so far (union-find).  Keys:                                   */
+/*   ORC_TREE_MAX_WEIGHT  key = w(e)                                          */
+/*   ORC_TREE_FEGRASS     key = W_eff(e) = (w * log(max(deg u, deg v)))       */
+/*                        / (d(u) + d(v)), each operation rounded to double,  */
+/*                        d = BFS hop distance in G from the vertex of        */
+/*                        maximum degree (ties: smaller id); G connected.     */
+/* Rooting: every component is rooted at its maximum-degree vertex (ties:    */
+/* smaller id) and parents come from a BFS over the tree edges.              */
+/* Returns ORC_OK or ORC_E_ARG (FEGRASS on a disconnected graph).            */
+
+#define ORC_TREE_MAX_WEIGHT 0
+#define ORC_TREE_FEGRASS 1
+
+typedef struct {
+  double key;
+  int32_t id;
+} orc_kedge;
+
+static int kedge_order(const void* a, const void* b) {
+  const orc_kedge* x = (const orc_kedge*)a;
+  const orc_kedge* y = (const orc_kedge*)b;
+  if (x->key > y->key) return -1;
+  if (x->key < y->key) return 1;
+  return (x->id < y->id) ? -1 : (x->id > y->id);
+}
+
+static int32_t uf_find(int32_t* up, int32_t x) {
+  while (up[x] != x) {
+    up[x] = up[up[x]];
+    x = up[x];
+  }
+  return x;
+}
+
+/* better root: larger degree, then smaller id */
+static int better_root(const int64_t* rp, int32_t a, int32_t b) {
+  const int64_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
+  return da > db || (da == db && a < b);
+}
+
+int orc_spanning_tree(int64_t n, const int64_t* rp, const int32_t* col, const double* w, int kind,
+                      int32_t* parent) {
+  const int64_t m = rp[n] / 2;
+  int32_t *eu = malloc(sizeof(int32_t) * (m + 1)), *ev = malloc(sizeof(int32_t) * (m + 1));
+  double* ew = malloc(sizeof(double) * (m + 1));
+  orc_kedge* ord = malloc(sizeof(orc_kedge) * (m + 1));
+  int32_t* up = malloc(sizeof(int32_t) * n);
+  int32_t* dist = malloc(sizeof(int32_t) * n);
+  int32_t* queue = malloc(sizeof(int32_t) * n);
+  uint8_t* in_tree = calloc((size_t)m + 1, 1);
+  int64_t* tptr = calloc((size_t)n + 1, sizeof(int64_t));
+  int32_t* tadj = malloc(sizeof(int32_t) * (2 * n + 1));
+  int32_t* best = malloc(sizeof(int32_t) * n);
+  int st = ORC_OK;
+  if (!eu || !ev || !ew || !ord || !up || !dist || !queue || !in_tree || !tptr || !tadj || !best) {
+    st = ORC_E_OOM;
+    goto done;
+  }
+  /* canonical edges: entries (u, v) with u < v in row-major order */
+  int64_t e = 0;
+  for (int64_t u = 0; u < n; u++)
+    for (int64_t p = rp[u]; p < rp[u + 1]; p++)
+      if (col[p] > u) {
+        eu[e] = (int32_t)u;
+        ev[e] = col[p];
+        ew[e] = w[p];
+        e++;
+      }
+  /* keys */
+  if (kind == ORC_TREE_FEGRASS) {
+    int32_t root = 0;
+    for (int32_t v = 1; v < n; v++)
+      if (better_root(rp, v, root)) root = v;
+    for (int64_t v = 0; v < n; v++) dist[v] = -1;
+    int64_t head = 0, tail = 0;
+    dist[root] = 0;
+    queue[tail++] = root;
+    while (head < tail) {
+      const int32_t x = queue[head++];
+      for (int64_t p = rp[x]; p < rp[x + 1]; p++)
+        if (dist[col[p]] < 0) {
+          dist[col[p]] = dist[x] + 1;
+          queue[tail++] = col[p];
+        }
+    }
+    if (tail != n) {
+      st = ORC_E_ARG;
+      goto done;
+    }
+    for (int64_t i = 0; i < m; i++) {
+      const int64_t du = rp[eu[i] + 1] - rp[eu[i]], dv = rp[ev[i] + 1] - rp[ev[i]];
+      const double lg = log((double)(du > dv ? du : dv));
+      const double num = ew[i] * lg;
+      ord[i].key = num / (double)(dist[eu[i]] + dist[ev[i]]);
+      ord[i].id = (int32_t)i;
+    }
+  } else {
+    for (int64_t i = 0; i < m; i++) {
+      ord[i].key = ew[i];
+      ord[i].id = (int32_t)i;
+    }
+  }
+  /* Kruskal */
+  qsort(ord, (size_t)m, sizeof(orc_kedge), kedge_order);
+  for (int64_t v = 0; v < n; v++) up[v] = (int32_t)v;
+  for (int64_t i = 0; i < m; i++) {
+    const int32_t id = ord[i].id;
+    const int32_t a = uf_find(up, eu[id]), b = uf_find(up, ev[id]);
+    if (a == b) continue;
+    up[a] = b;
+    in_tree[id] = 1;
+  }
+  /* tree adjacency */
+  for (int64_t i = 0; i < m; i++)
+    if (in_tree[i]) {
+      tptr[eu[i] + 1]++;
+      tptr[ev[i] + 1]++;
+    }
+  for (int64_t v = 0; v < n; v++) tptr[v + 1] += tptr[v];
+  for (int64_t v = 0; v < n; v++) best[v] = -1;
+  {
+    int64_t* fill = calloc((size_t)n, sizeof(int64_t));
+    if (!fill) {
+      st = ORC_E_OOM;
+      goto done;
+    }
+    for (int64_t i = 0; i < m; i++)
+      if (in_tree[i]) {
+        tadj[tptr[eu[i]] + fill[eu[i]]++] = ev[i];
+        tadj[tptr[ev[i]] + fill[ev[i]]++] = eu[i];
+      }
+    free(fill);
+  }
+  /* root of every component, then BFS over the tree from it */
+  for (int64_t v = 0; v < n; v++) {
+    const int32_t r = uf_find(up, (int32_t)v);
+    if (best[r] < 0 || better_root(rp, (int32_t)v, best[r])) best[r] = (int32_t)v;
+  }
+  for (int64_t v = 0; v < n; v++) {
+    parent[v] = -1;
+    dist[v] = -1;
+  }
+  for (int64_t v = 0; v < n; v++) {
+    if (best[v] < 0) continue; /* v is not a union-find root */
+    const int32_t root = best[v];
+    int64_t head = 0, tail = 0;
+    dist[root] = 0;
+    queue[tail++] = root;
+    while (head < tail) {
+      const int32_t x = queue[head++];
+      for (int64_t p = tptr[x]; p < tptr[x + 1]; p++) {
+        const int32_t y = tadj[p];
+        if (dist[y] < 0) {
+          dist[y] = dist[x] + 1;
+          parent[y] = x;
+          queue[tail++] = y;
+        }
+      }
+    }
+  }
+done:
+  free(eu);
+  free(ev);
+  free(ew);
+  free(ord);
+  free(up);
+  free(dist);
+  free(queue);
+  free(in_tree);
+  free(tptr);
+  free(tadj);
+  free(best);
+  return st;
+}

@@ -32,10 +32,12 @@ MEM_DEVICE = 1
 SCORE_STRETCH = 0
 SCORE_RESISTANCE = 1
 MAX_C = 3
+TREE_MAX_WEIGHT = 0
+TREE_FEGRASS = 1
 
 EXPORTS = ("pdg_default_options", "pdg_status_string", "sparsify_init", "recover_offtree", "sparsifier_free",
            "pdg_edge_endpoints", "sparsify_batch_init", "recover_offtree_batch", "pdg_handle_info",
-           "pdg_last_stats", "pdg_last_timings")
+           "pdg_last_stats", "pdg_last_timings", "pdg_spanning_tree")
 STEP_NAMES = ("classify", "tree", "score", "select", "sort", "accept", "budget", "total")
 
 
@@ -89,9 +91,28 @@ def load(path: Optional[str] = None):
     L.pdg_last_timings.restype = c_int
     L.pdg_edge_endpoints_noalloc.argtypes = [i64, P, P, P, i64, P, P, P]
     L.pdg_edge_endpoints_noalloc.restype = c_int
+    L.pdg_spanning_tree.argtypes = [i64, P, P, P, c_int, c_int, P, c_int, P]
+    L.pdg_spanning_tree.restype = c_int
     if path is None:
         _lib = L
     return L
+
+
+def spanning_tree(n: int, row_ptr, col, w, kind: int = TREE_MAX_WEIGHT, parent_out=None, stream=None):
+    """pdg_spanning_tree: the parent array of the generated spanning tree (numpy int32, or written into the
+    given device tensor `parent_out`).  Inputs are numpy arrays or CUDA tensors (all in one memory)."""
+    L = load()
+    kind_in = _mem_kind([row_ptr, col, w])
+    if kind_in == MEM_HOST:
+        row_ptr = _host_arr(row_ptr, np.int64)
+        col = _host_arr(col, np.int32)
+        w = _host_arr(w, np.float64)
+    out = parent_out if parent_out is not None else np.zeros(int(n), dtype=np.int32)
+    st = L.pdg_spanning_tree(int(n), _ptr(row_ptr), _ptr(col), _ptr(w), kind_in, int(kind), _ptr(out),
+                             _mem_kind([out]), _stream_ptr(stream))
+    if st != PDG_OK:
+        raise PdgError(st, "pdg_spanning_tree")
+    return out
 
 
 def status_string(status: int) -> str:

@@ -438,6 +438,8 @@ int step_select(Handle& h);                     // A4a: candidate prefix per gra
 int sort_setup();                               // per-device kernel attributes of the sort
 int accept_setup();                             // per-device kernel attributes of the block tier
 int coop_rounds(const Handle& h, int c);        // cooperative-tier rounds the next recovery launches
+int validate_csr(Handle& h);                    // CSR shape, symmetry and weights only
+int spanning_tree(Handle& h, int tree_kind, int32_t* parent);  // parent array of the generated tree (device)
 int step_sort(Handle& h);                       // A4b: (graph, score desc, id asc) then (lca, rank)
 int step_accept(Handle& h, int c);              // A5 + A6
 int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7

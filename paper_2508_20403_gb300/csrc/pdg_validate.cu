@@ -129,6 +129,28 @@ __global__ void k_val_active_reset(DevScalars* dsc) { dsc->active = 0; }
 
 }  // namespace
 
+// The CSR checks alone (spanning-tree generation has no parent array yet).
+int validate_csr(Handle& h) {
+  const int64_t n = h.n;
+  const int grid = grid_for(h, std::max<int64_t>(n, h.nnz));
+  auto fetch = [&]() -> bool {
+    return cudaMemcpyAsync(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h.stream) == cudaSuccess &&
+           cudaStreamSynchronize(h.stream) == cudaSuccess;
+  };
+  k_val_reset<<<1, 1, 0, h.stream>>>(h.dsc);
+  k_val_rowptr<<<grid, kBlock, 0, h.stream>>>(h.row_ptr, n, h.dsc);
+  if (!fetch()) return check_cuda(cudaGetLastError());
+  if (h.hsc->err) return PDG_E_NOT_CSR;  // the entry checks below search rows: only on a monotone row_ptr
+  if (h.nnz > 0) k_val_entries<<<grid, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, n, h.nnz, h.d_vtx_ptr, h.G, h.dsc);
+  if (!fetch()) return check_cuda(cudaGetLastError());
+  const int err = h.hsc->err;
+  if (err & ERR_NOT_CSR) return PDG_E_NOT_CSR;
+  if (err & ERR_BAD_WEIGHT) return PDG_E_BAD_WEIGHT;
+  if (err & ERR_CROSS_GRAPH) return PDG_E_INVALID_ARG;
+  if (err & ERR_NOT_SYMMETRIC) return PDG_E_NOT_SYMMETRIC;
+  return PDG_OK;
+}
+
 int validate_graph(Handle& h) {
   const int64_t n = h.n;
   const int grid = grid_for(h, std::max<int64_t>(n, h.nnz));
