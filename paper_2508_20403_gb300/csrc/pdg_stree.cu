@@ -383,6 +383,13 @@ int spanning_tree(Handle& h, int tree_kind, int32_t* parent) {
   ST_CK(cudaMemsetAsync(cur, 0, sizeof(int32_t) * n, s));
   k_st_tdeg<<<gm, kBlock, 0, s>>>(h.el_u, h.el_v, tflag, m, tdeg);
   if ((st = ensure_scan_status(h, n)) || (st = scan_excl_i32(h, tdeg, tptr, n, nullptr, n))) return fail(st);
+  {  // a forest has at most n - 1 edges: the arc arrays are sized for that
+    int64_t arcs = 0;
+    if (cudaMemcpyAsync(&arcs, tptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(PDG_E_CUDA);
+    if (arcs < 0 || arcs > A) return fail(PDG_E_CUDA);
+  }
   k_st_fill<<<gm, kBlock, 0, s>>>(h.el_u, h.el_v, tflag, m, tptr, cur, tadj, rev, arc_uv);
   const int ga = grid_for(h, std::max<int64_t>(A, 1));
   k_st_succ<<<ga, kBlock, 0, s>>>(tadj, rev, tptr, tdeg, n, succ[0], rd[0]);
