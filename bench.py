@@ -344,6 +344,8 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
     del flush
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e_leg(args, g, dev, B, torch)
+    if rank == 0 and not args.no_tree:
+        result["tree_build"] = tree_leg(args, g, dev, B, torch)
     if batch_graphs is not None:
         t0 = time.time()
         result["batch"] = batch_leg(args, batch_graphs, dev, B, torch)
@@ -491,6 +493,42 @@ def cpu_sample_graph():
     return W.mesh3d_graph(64, seed=W.SEED_BASE + 1)
 
 
+def tree_leg(args, g, dev, B, torch):
+    """Spanning-tree generation (pdg_spanning_tree) on the headline mesh, device CSR in and device parent out,
+    both trees; the maximum-weight tree must equal the workload's own (scipy) tree.  The oracle's Kruskal is
+    timed on the 64^3 sample."""
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    rp, col, w = t(g.row_ptr, torch.int64), t(g.col, torch.int32), t(g.w, torch.float64)
+    out = torch.zeros(g.n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": f"mesh {MESH_SIDE}^3 (n={g.n}, m={g.m})", "unit": "edges/s"}
+    for name, kind in (("max_weight", B.TREE_MAX_WEIGHT), ("fegrass_weff", B.TREE_FEGRASS)):
+        B.spanning_tree(g.n, rp, col, w, kind=kind, parent_out=out, stream=stream)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.spanning_tree(g.n, rp, col, w, kind=kind, parent_out=out, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        res[name] = {"ms": ms, "value": g.m / (ms / 1e3)}
+        if kind == B.TREE_MAX_WEIGHT:
+            res[name]["equals_workload_tree"] = bool(np.array_equal(out.cpu().numpy(), g.parent))
+    if not args.no_cpu:
+        from oracle import oracle as O
+
+        gs = cpu_sample_graph()
+        for name, kind in (("max_weight", O.TREE_MAX_WEIGHT), ("fegrass_weff", O.TREE_FEGRASS)):
+            t0 = time.perf_counter()
+            O.spanning_tree(gs, kind)
+            dt = time.perf_counter() - t0
+            res[name]["cpu_oracle"] = {"value": gs.m / dt, "unit": "edges/s", "cores": 1,
+                                       "sample": f"mesh 64^3 (m={gs.m}), single-threaded C Kruskal, {dt:.2f} s"}
+    return res
+
+
 def cpu_leg(args, g=None, repeats=1):
     """The oracle as it stands, single thread, on a bounded sample of the same
     workload family: the 64^3 mesh with the same weight law, alpha and c."""
@@ -562,6 +600,7 @@ def main():
     ap.add_argument("--c", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tree", action="store_true", help="skip the spanning-tree generation leg")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=2000)
