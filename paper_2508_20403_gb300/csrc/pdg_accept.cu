@@ -1064,6 +1064,8 @@ int accept_setup() {
   return PDG_OK;
 }
 
+static int accept_coop(Handle& h, int c, int grid, const RecArrays& ra);
+
 int step_accept(Handle& h, int c) {
   const int grid = h.num_sms * 8;
   const int64_t cap = h.Rcap;
@@ -1092,9 +1094,18 @@ int step_accept(Handle& h, int c) {
   // table regions of the cooperative subtasks
   if ((st = scan_excl_i64(h, h.seg_regs, h.seg_pref, 0, &h.dsc->n_big_seg, cap))) return st;
   const RecArrays ra{h.rec_u, h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, cap};
+  // The warp and block tiers decide other candidates than the cooperative
+  // tier: they run on the side stream beside it (a fork and a join, also in
+  // the captured graph), joined back before this step returns.
+  const bool fork = h.sstream != nullptr && h.ev_fork != nullptr && h.ev_join != nullptr;
+  const cudaStream_t side = fork ? h.sstream : h.stream;
+  if (fork) {
+    PDG_CUDA(cudaEventRecord(h.ev_fork, h.stream));
+    PDG_CUDA(cudaStreamWaitEvent(h.sstream, h.ev_fork, 0));
+  }
   // warp tier
   ++h.launches;
-  k_accept_warp<<<grid, kBlock, 0, h.stream>>>(h.warp_seg, h.dsc, h.seg_begin, c, ra, h.acc_flag);
+  k_accept_warp<<<grid, kBlock, 0, side>>>(h.warp_seg, h.dsc, h.seg_begin, c, ra, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
   // block tier
   if (block_max > h.opt.warp_tier_max) {
@@ -1106,13 +1117,22 @@ int step_accept(Handle& h, int c) {
     const int bgrid = h.num_sms * per_sm;
     ++h.launches;
     switch (c) {
-      case 0: k_accept_block<0><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
-      case 1: k_accept_block<1><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
-      case 2: k_accept_block<2><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
-      default: k_accept_block<3><<<bgrid, 32, smem, h.stream>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+      case 0: k_accept_block<0><<<bgrid, 32, smem, side>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+      case 1: k_accept_block<1><<<bgrid, 32, smem, side>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+      case 2: k_accept_block<2><<<bgrid, 32, smem, side>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
+      default: k_accept_block<3><<<bgrid, 32, smem, side>>>(h.block_seg, h.dsc, h.seg_begin, ra, tl, h.acc_flag); break;
     }
     PDG_CUDA(cudaGetLastError());
   }
+  if (fork) PDG_CUDA(cudaEventRecord(h.ev_join, h.sstream));
+  st = accept_coop(h, c, grid, ra);
+  if (fork && cudaStreamWaitEvent(h.stream, h.ev_join, 0) != cudaSuccess && st == PDG_OK) st = PDG_E_CUDA;
+  return st;
+}
+
+// the cooperative tier and the flags of its candidates (handle's stream)
+static int accept_coop(Handle& h, int c, int grid, const RecArrays& ra) {
+  int st;
   // cooperative tier; blk_a[9800..9916) is reserved for it (other steps use [0, 9729))
   uint64_t* d_cap = reinterpret_cast<uint64_t*>(h.blk_a + 9800);
   int64_t* n_flag = h.blk_a + 9801;

@@ -312,6 +312,12 @@ void sparsifier_free(pdg_handle hp) {
     if (e) cudaEventDestroy(e);
   if (h.gexec) cudaGraphExecDestroy(h.gexec);
   if (h.ev_order) cudaEventDestroy(h.ev_order);
+  if (h.ev_fork) cudaEventDestroy(h.ev_fork);
+  if (h.ev_join) cudaEventDestroy(h.ev_join);
+  if (h.sstream) {
+    cudaStreamSynchronize(h.sstream);
+    cudaStreamDestroy(h.sstream);
+  }
   if (h.gstream) cudaStreamDestroy(h.gstream);
   pinned_release(h.hsc, sizeof(DevScalars));
   HostStage& s = hp->stage;
@@ -358,6 +364,13 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       cudaGetLastError();
       h.opt.use_graph = 0;  // replay is an optimisation; run without it
     }
+  }
+  if (cudaStreamCreateWithFlags(&h.sstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (h.sstream) cudaStreamDestroy(h.sstream);
+    h.sstream = nullptr;  // the tiers then run one after the other on the handle's stream
   }
   h.G = num_graphs;
   h.n = n;

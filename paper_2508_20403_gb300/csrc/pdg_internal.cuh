@@ -251,6 +251,8 @@ struct Handle {
   // CUDA-graph replay of a whole recovery (opt.use_graph)
   cudaStream_t gstream = nullptr;  // private stream: capture and replay
   cudaEvent_t ev_order = nullptr;  // orders gstream after the caller's stream
+  cudaStream_t sstream = nullptr;  // side stream: the warp/block tiers beside the cooperative tier
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   GraphKey gkey;
   int64_t glaunches = 0;
