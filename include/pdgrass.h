@@ -269,6 +269,33 @@ int pdg_last_timings(pdg_handle h, float* ms);
 int pdg_spanning_tree(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, int mem_kind,
                       int tree_kind, int32_t* parent_out, int out_mem_kind, void* stream);
 
+/*
+ * pdg_pcg_quality -- measure a sparsifier the way Sec. 5 does: the number of
+ * preconditioned conjugate-gradient iterations that solving L_G x = b takes
+ * with the sparsifier's Laplacian L_P (the tree plus the given edges) as the
+ * preconditioner, to ||r|| <= tol ||b'||.
+ *
+ *   n, row_ptr, col, w, parent  the graph and its spanning tree, as in
+ *                 sparsify_init (one root: the graph is connected).
+ *   edge_ids      int32[n_edges]: distinct canonical ids of off-tree edges
+ *                 (e.g. a recovery's output), 0 <= n_edges <= 8192.
+ *   b             float64[n]: right-hand side; b' = b - mean(b) is solved
+ *                 (L_G is singular).
+ *   tol, max_iter stopping rule (tol > 0; max_iter >= 1).
+ *   mem_kind      memory kind of all array inputs.
+ *   out_iters, out_relres  host: iterations run and the final ||r|| / ||b'||.
+ *
+ * x starts at 0; the preconditioner solves L_P z = r exactly (grounded at
+ * the tree root, then centred): tree solves over the Euler tour plus a
+ * k x k capacitance matrix for the k extra edges (Woodbury).  Device memory
+ * is allocated for the call and released before it returns.  Returns PDG_OK
+ * or PDG_E_INVALID_ARG (arguments, an edge id out of range, a tree edge or a
+ * repeated id), the errors of sparsify_init, PDG_E_OOM or PDG_E_CUDA.
+ */
+int pdg_pcg_quality(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
+                    const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
+                    int mem_kind, int32_t* out_iters, double* out_relres, void* stream);
+
 #define PDG_NOALLOC_MAX_N (1 << 21)
 int pdg_edge_endpoints_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* ids,
                                int64_t count, int32_t* u, int32_t* v, void* stream);

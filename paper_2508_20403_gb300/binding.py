@@ -37,7 +37,7 @@ TREE_FEGRASS = 1
 
 EXPORTS = ("pdg_default_options", "pdg_status_string", "sparsify_init", "recover_offtree", "sparsifier_free",
            "pdg_edge_endpoints", "sparsify_batch_init", "recover_offtree_batch", "pdg_handle_info",
-           "pdg_last_stats", "pdg_last_timings", "pdg_spanning_tree")
+           "pdg_last_stats", "pdg_last_timings", "pdg_spanning_tree", "pdg_pcg_quality")
 STEP_NAMES = ("classify", "tree", "score", "select", "sort", "accept", "budget", "total")
 
 
@@ -93,6 +93,8 @@ def load(path: Optional[str] = None):
     L.pdg_edge_endpoints_noalloc.restype = c_int
     L.pdg_spanning_tree.argtypes = [i64, P, P, P, c_int, c_int, P, c_int, P]
     L.pdg_spanning_tree.restype = c_int
+    L.pdg_pcg_quality.argtypes = [i64, P, P, P, P, P, i64, P, f64, i32, c_int, P, P, P]
+    L.pdg_pcg_quality.restype = c_int
     if path is None:
         _lib = L
     return L
@@ -113,6 +115,25 @@ def spanning_tree(n: int, row_ptr, col, w, kind: int = TREE_MAX_WEIGHT, parent_o
     if st != PDG_OK:
         raise PdgError(st, "pdg_spanning_tree")
     return out
+
+
+def pcg_quality(g, edge_ids, b, tol: float = 1e-3, max_iter: int = 1000, stream=None):
+    """pdg_pcg_quality on a workloads.Graph (host arrays): (iterations, final relative residual)."""
+    L = load()
+    rp = _host_arr(g.row_ptr, np.int64)
+    col = _host_arr(g.col, np.int32)
+    w = _host_arr(g.w, np.float64)
+    par = _host_arr(g.parent, np.int32)
+    ids = _host_arr(edge_ids, np.int32)
+    bb = _host_arr(b, np.float64)
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = L.pdg_pcg_quality(int(g.n), _ptr(rp), _ptr(col), _ptr(w), _ptr(par), _ptr(ids) if ids.size else None,
+                           int(ids.size), _ptr(bb), float(tol), int(max_iter), MEM_HOST, ctypes.byref(it),
+                           ctypes.byref(rel), _stream_ptr(stream))
+    if st != PDG_OK:
+        raise PdgError(st, "pdg_pcg_quality")
+    return int(it.value), float(rel.value)
 
 
 def status_string(status: int) -> str:

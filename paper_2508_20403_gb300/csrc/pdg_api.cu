@@ -552,6 +552,74 @@ int pdg_spanning_tree(int64_t n, const int64_t* row_ptr, const int32_t* col, con
   return PDG_OK;
 }
 
+int pdg_pcg_quality(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
+                    const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
+                    int mem_kind, int32_t* out_iters, double* out_relres, void* stream) {
+  if (n < 2 || n >= (1ll << 30) || !row_ptr || !parent || !b || !out_iters || !out_relres || n_edges < 0 ||
+      n_edges > kPcgMaxEdges || (n_edges > 0 && !edge_ids) || !(tol > 0) || max_iter < 1 ||
+      (mem_kind != PDG_MEM_HOST && mem_kind != PDG_MEM_DEVICE))
+    return PDG_E_INVALID_ARG;
+  pdg_sparsifier* hp = new (std::nothrow) pdg_sparsifier();
+  if (!hp) return PDG_E_OOM;
+  Handle& h = hp->h;
+  pdg_default_options(&h.opt);
+  cudaGetDevice(&h.device);
+  cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, h.device);
+  h.stream = (cudaStream_t)stream;
+  h.G = 1;
+  h.n = n;
+  h.vtx_ptr_h = {0, n};
+  auto fail = [&](int code) {
+    sparsifier_free(hp);
+    return code;
+  };
+  const cudaMemcpyKind kind = (mem_kind == PDG_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  int64_t ends[2];
+  if (mem_kind == PDG_MEM_HOST) {
+    ends[0] = row_ptr[0];
+    ends[1] = row_ptr[n];
+  } else if (cudaMemcpyAsync(&ends[0], row_ptr, 8, cudaMemcpyDeviceToHost, h.stream) != cudaSuccess ||
+             cudaMemcpyAsync(&ends[1], row_ptr + n, 8, cudaMemcpyDeviceToHost, h.stream) != cudaSuccess ||
+             cudaStreamSynchronize(h.stream) != cudaSuccess) {
+    return fail(PDG_E_CUDA);
+  }
+  if (ends[0] != 0 || ends[1] < 0) return fail(PDG_E_NOT_CSR);
+  h.nnz = ends[1];
+  if (h.nnz > 0 && (!col || !w)) return fail(PDG_E_INVALID_ARG);
+  if (h.nnz % 2) return fail(PDG_E_NOT_SYMMETRIC);
+  h.m = h.nnz / 2;
+  if (h.m >= (1ll << 31)) return fail(PDG_E_INVALID_ARG);
+  int st = PDG_OK;
+  const int64_t vp[2] = {0, n};
+  int32_t* d_ids = nullptr;
+  double* d_b = nullptr;
+  if (!(h.hsc = static_cast<DevScalars*>(pinned_alloc(sizeof(DevScalars))))) return fail(PDG_E_OOM);
+  if ((st = alloc_n(h, &h.dsc, 1)) || (st = alloc_n(h, &h.row_ptr, n + 1)) || (st = alloc_n(h, &h.col, h.nnz)) ||
+      (st = alloc_n(h, &h.w, h.nnz)) || (st = alloc_n(h, &h.parent, n)) || (st = alloc_n(h, &h.d_vtx_ptr, 2)) ||
+      (st = alloc_n(h, &h.blk_a, 10240)) || (st = alloc_n(h, &h.blk_b, 2048)) ||
+      (st = alloc_n(h, &d_ids, std::max<int64_t>(n_edges, 1))) || (st = alloc_n(h, &d_b, n)))
+    return fail(st);
+  if (cudaMemcpyAsync(h.row_ptr, row_ptr, sizeof(int64_t) * (n + 1), kind, h.stream) != cudaSuccess ||
+      (h.nnz && cudaMemcpyAsync(h.col, col, sizeof(int32_t) * h.nnz, kind, h.stream) != cudaSuccess) ||
+      (h.nnz && cudaMemcpyAsync(h.w, w, sizeof(double) * h.nnz, kind, h.stream) != cudaSuccess) ||
+      cudaMemcpyAsync(h.parent, parent, sizeof(int32_t) * n, kind, h.stream) != cudaSuccess ||
+      (n_edges && cudaMemcpyAsync(d_ids, edge_ids, sizeof(int32_t) * n_edges, kind, h.stream) != cudaSuccess) ||
+      cudaMemcpyAsync(d_b, b, sizeof(double) * n, kind, h.stream) != cudaSuccess ||
+      cudaMemcpyAsync(h.d_vtx_ptr, vp, sizeof(vp), cudaMemcpyHostToDevice, h.stream) != cudaSuccess)
+    return fail(PDG_E_CUDA);
+  if ((st = validate_graph(h))) return fail(st);
+  if ((st = alloc_n(h, &h.el_u, std::max<int64_t>(h.m, 1))) || (st = alloc_n(h, &h.el_v, std::max<int64_t>(h.m, 1))) ||
+      (st = alloc_n(h, &h.el_w, std::max<int64_t>(h.m, 1))) || (st = build_edge_list(h)))
+    return fail(st);
+  int32_t it = 0;
+  double rel = 0.0;
+  if ((st = pcg_quality(h, d_ids, n_edges, d_b, tol, max_iter, &it, &rel))) return fail(st);
+  *out_iters = it;
+  *out_relres = rel;
+  sparsifier_free(hp);
+  return PDG_OK;
+}
+
 int sparsify_init(pdg_handle* out, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w,
                   const int32_t* parent, int mem_kind, const pdg_options* opt, void* stream) {
   if (!out) return PDG_E_INVALID_ARG;

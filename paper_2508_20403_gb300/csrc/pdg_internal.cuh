@@ -442,6 +442,9 @@ int accept_setup();                             // per-device kernel attributes 
 int coop_rounds(const Handle& h, int c);        // cooperative-tier rounds the next recovery launches
 int validate_csr(Handle& h);                    // CSR shape, symmetry and weights only
 int spanning_tree(Handle& h, int tree_kind, int32_t* parent);  // parent array of the generated tree (device)
+constexpr int64_t kPcgMaxEdges = 8192;  // recovered edges of the PCG quality measure (dense k x k capacitance)
+int pcg_quality(Handle& h, const int32_t* ids, int64_t k, const double* b, double tol, int32_t max_iter,
+                int32_t* iters, double* relres);  // device ids and b; host results
 int step_sort(Handle& h);                       // A4b: (graph, score desc, id asc) then (lca, rank)
 int step_accept(Handle& h, int c);              // A5 + A6
 int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7

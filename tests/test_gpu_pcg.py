@@ -1,0 +1,69 @@
+"""GPU PCG sparsifier-quality measure (pdg_pcg_quality) against the oracle's PCG (exact sparse LU preconditioner).
+Both run the same iteration in FP64 with different summation orders, so the iteration counts may differ by one
+when a residual lands next to the tolerance; the bar is |iterations - oracle| <= 1 and the final residual within
+the tolerance."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import pcg as PC
+from paper_2508_20403_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2508_20403_gb300 import binding, build
+
+    build.build()
+    binding.load()
+    return binding
+
+
+def _check(B, g, ids, b, tol=1e-3):
+    it, rel = B.pcg_quality(g, ids, b, tol=tol)
+    oit, orel = PC.pcg_quality(g, ids, b, tol=tol)
+    assert abs(it - oit) <= 1, (g.name, len(ids), it, oit)
+    assert rel <= tol
+    return it, oit
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.02, 0.05, 0.10])
+def test_grid100_recovered(B, alpha):
+    g = W.grid_graph(100)
+    ids = O.recover(g, alpha, c=2)[1] if alpha > 0 else np.zeros(0, dtype=np.int32)
+    _check(B, g, ids, np.random.default_rng(0).standard_normal(g.n))
+
+
+def test_mesh_and_random_subsets(B):
+    g = W.mesh3d_graph(16, seed=3)
+    off = O.offtree_scores(g, c=0)["id"]
+    rng = np.random.default_rng(4)
+    for k in (1, 37, 400):
+        _check(B, g, rng.choice(off, size=k, replace=False), rng.standard_normal(g.n))
+    g = W.rmat_graph(11, seed=2)
+    _check(B, g, O.recover(g, 0.05, c=2)[1], rng.standard_normal(g.n))
+
+
+def test_exact_preconditioner_and_degenerate_rhs(B):
+    g = W.grid_graph(40)
+    off = O.offtree_scores(g, c=0)["id"]
+    it, rel = B.pcg_quality(g, off, np.random.default_rng(1).standard_normal(g.n), tol=1e-8)
+    assert it == 1 and rel <= 1e-8
+    it, rel = B.pcg_quality(g, off[:10], np.full(g.n, 3.0))  # b' = 0
+    assert it == 0 and rel == 0.0
+
+
+def test_rejects_bad_edge_lists(B):
+    g = W.grid_graph(20)
+    off = O.offtree_scores(g, c=0)["id"]
+    eu, ev, _ = PC.canonical_edges(g.n, g.row_ptr, g.col, g.w)
+    tree_id = next(i for i in range(len(eu)) if g.parent[ev[i]] == eu[i] or g.parent[eu[i]] == ev[i])
+    b = np.ones(g.n)
+    for bad in ([tree_id], [off[0], off[0]], [len(eu)], [-1]):
+        with pytest.raises(B.PdgError) as e:
+            B.pcg_quality(g, np.array(bad, dtype=np.int32), b)
+        assert e.value.status == B.PDG_E_INVALID_ARG

@@ -1,0 +1,83 @@
+"""Pins of the oracle's PCG sparsifier-quality measure (Sec. 5 evaluation) against independent statements:
+scipy's own conjugate gradients with the same preconditioner, the exact preconditioner (one iteration), and the
+finite-termination bound by the number of distinct generalised eigenvalues on tiny graphs."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import oracle as O
+from oracle import pcg as PC
+from paper_2508_20403_gb300 import workloads as W
+from tests import bruteforce as BF
+from tests.helpers import random_small_graph
+
+
+def _rhs(n, seed=0):
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def test_exact_preconditioner_converges_in_one_iteration():
+    g = W.grid_graph(30)
+    off = O.offtree_scores(g, c=0)["id"]
+    it, rel = PC.pcg_quality(g, off, _rhs(g.n), tol=1e-8)
+    assert it == 1 and rel <= 1e-8
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.10])
+def test_matches_scipy_cg(alpha):
+    g = W.grid_graph(60, seed=4)
+    _, ids, _, _ = O.recover(g, alpha, c=2)
+    b = _rhs(g.n, 1)
+    it, rel = PC.pcg_quality(g, ids, b, tol=1e-3)
+    # scipy's CG with the same preconditioner and stopping rule
+    LG = PC.laplacian_from_csr(g.n, g.row_ptr, g.col, g.w)
+    LP = PC.sparsifier_laplacian(g, ids)
+    root = int(np.flatnonzero(g.parent < 0)[0])
+    keep = np.flatnonzero(np.arange(g.n) != root)
+    lu = spla.splu(LP[keep][:, keep].tocsc())
+
+    def apply(r):
+        z = np.zeros(g.n)
+        z[keep] = lu.solve(np.asarray(r).ravel()[keep])
+        return z - z.mean()
+
+    M = spla.LinearOperator((g.n, g.n), matvec=apply)
+    count = [0]
+    bc = b - b.mean()
+    x, info = spla.cg(LG, bc, rtol=1e-3, atol=0.0, M=M, maxiter=1000, callback=lambda xk: count.__setitem__(0, count[0] + 1))
+    assert info == 0
+    assert abs(count[0] - it) <= 1
+    assert np.linalg.norm(bc - LG @ x) / np.linalg.norm(bc) <= 1e-3
+
+
+def test_iterations_bounded_by_distinct_eigenvalues():
+    rng = np.random.default_rng(9)
+    for _ in range(15):
+        g = random_small_graph(rng, n_lo=4, n_hi=12, tree="max")
+        off = O.offtree_scores(g, c=0)["id"]
+        ids = off[: max(0, len(off) // 3)]
+        it, rel = PC.pcg_quality(g, ids, _rhs(g.n, 3), tol=1e-9, max_iter=200)
+        eu, ev, ew = PC.canonical_edges(g.n, g.row_ptr, g.col, g.w)
+        LG = BF.laplacian(g.n, list(zip(eu, ev, ew)))
+        LP = PC.sparsifier_laplacian(g, ids).toarray()
+        ev_ = BF.generalized_eigs(LG, LP)
+        distinct = len(np.unique(np.round(ev_, 6)))
+        assert it <= distinct + 1, (it, distinct)
+
+
+def test_recovered_edges_precondition_better_than_random():
+    """The method's point (Sec. 5): the recovered (spectrally critical) edges give fewer PCG iterations than as
+    many random off-tree edges, and a larger budget gives fewer iterations than a smaller one."""
+    g = W.grid_graph(100)
+    b = _rhs(g.n, 2)
+    its = {}
+    for alpha in (0.02, 0.10):
+        _, ids, _, _ = O.recover(g, alpha, c=2)
+        its[alpha], _ = PC.pcg_quality(g, ids, b)
+        off = O.offtree_scores(g, c=0)["id"]
+        rnd = np.random.default_rng(5).choice(off, size=len(ids), replace=False)
+        it_rnd, _ = PC.pcg_quality(g, rnd, b)
+        assert its[alpha] < it_rnd
+    assert its[0.10] <= its[0.02]
