@@ -346,6 +346,8 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
         result["e2e"] = e2e_leg(args, g, dev, B, torch)
     if rank == 0 and not args.no_tree:
         result["tree_build"] = tree_leg(args, g, dev, B, torch)
+    if rank == 0 and not args.no_pcg:
+        result["pcg_quality"] = pcg_leg(args, B)
     if batch_graphs is not None:
         t0 = time.time()
         result["batch"] = batch_leg(args, batch_graphs, dev, B, torch)
@@ -529,6 +531,35 @@ def tree_leg(args, g, dev, B, torch):
     return res
 
 
+def pcg_leg(args, B):
+    """Sparsifier quality as Sec. 5 measures it: PCG iterations on L_G x = b (tol 1e-3) preconditioned by the
+    tree plus the recovered edges, on the 100x100 grid (weights U[1,10], max-weight tree) for alpha = 2/5/10 %
+    and the tree alone; the oracle's PCG (scipy LU) beside it unless --no-cpu."""
+    from paper_2508_20403_gb300 import workloads as W
+
+    g = W.grid_graph(100)
+    b = np.random.default_rng(0).standard_normal(g.n)
+    k_max = int(np.floor(0.10 * g.n))
+    rows = []
+    with B.Sparsifier.from_graph(g) as sp:
+        for alpha in (0.0, 0.02, 0.05, 0.10):
+            ids = np.zeros(0, dtype=np.int32)
+            if alpha > 0:
+                st, ids, _, _ = sp.recover(alpha, args.c, capacity=k_max)
+                ids = np.asarray(ids, dtype=np.int32)
+            t0 = time.perf_counter()
+            it, rel = B.pcg_quality(g, ids, b, tol=1e-3)
+            row = {"alpha": alpha, "edges": int(ids.size), "iterations": it, "relres": rel,
+                   "ms": (time.perf_counter() - t0) * 1e3}
+            if not args.no_cpu:
+                from oracle import pcg as PC
+
+                row["iterations_oracle"] = PC.pcg_quality(g, ids, b, tol=1e-3)[0]
+            rows.append(row)
+    return {"workload": f"grid 100x100 (n={g.n}, m={g.m}), weights U[1,10], max-weight tree, c={args.c}",
+            "tol": 1e-3, "rows": rows}
+
+
 def cpu_leg(args, g=None, repeats=1):
     """The oracle as it stands, single thread, on a bounded sample of the same
     workload family: the 64^3 mesh with the same weight law, alpha and c."""
@@ -601,6 +632,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tree", action="store_true", help="skip the spanning-tree generation leg")
+    ap.add_argument("--no-pcg", action="store_true", help="skip the PCG sparsifier-quality leg")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=2000)
