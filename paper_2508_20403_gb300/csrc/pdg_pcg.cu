@@ -452,6 +452,10 @@ int pcg_quality(Handle& h, const int32_t* ids, int64_t k, const double* b, doubl
     if (arcs != A) return fail(PDG_E_NOT_A_TREE);  // the parent links are the n - 1 tree edges
   }
   k_st_fill<<<gm, kBlock, 0, s>>>(h.el_u, h.el_v, tflag, m, tptr, cur, tadj, rev, arc_uv);
+  // rows in neighbour order: the tour, and so every sum along it, is the same on every run
+  k_tour_sort_rows<<<gn, kBlock, 0, s>>>(tptr, n, tadj);
+  k_tour_fix_rev<<<gn, kBlock, 0, s>>>(tptr, tadj, n, rev);
+  k_tour_fix_arcs<<<gm, kBlock, 0, s>>>(h.el_u, h.el_v, tflag, m, tptr, tadj, arc_uv);
   const int ga = grid_for(h, std::max<int64_t>(A, 1));
   k_st_succ<<<ga, kBlock, 0, s>>>(tadj, rev, tptr, tdeg, n, succ[0], rd[0]);
   k_pc_cut<<<1, 32, 0, s>>>(rev, tptr, tdeg, root, succ[0], rd[0]);

@@ -73,3 +73,54 @@ __global__ void k_st_rank(const int32_t* __restrict__ sin, const int32_t* __rest
 }  // namespace
 
 }  // namespace pdg
+
+namespace pdg {
+
+namespace {
+
+// Canonical tree adjacency (rows in increasing neighbour order) so that the
+// Euler tour, and every sum taken along it, does not depend on the order in
+// which the atomic fill placed the arcs.
+__global__ void k_tour_sort_rows(const int64_t* __restrict__ tptr, int64_t n, int32_t* __restrict__ tadj) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = tptr[v], e = tptr[v + 1];
+    for (int64_t p = b + 1; p < e; p++) {
+      const int32_t x = tadj[p];
+      int64_t q = p - 1;
+      while (q >= b && tadj[q] > x) {
+        tadj[q + 1] = tadj[q];
+        q--;
+      }
+      tadj[q + 1] = x;
+    }
+  }
+}
+
+__device__ __forceinline__ int32_t tour_find(const int64_t* __restrict__ tptr, const int32_t* __restrict__ tadj,
+                                            int32_t row, int32_t x) {
+  int64_t lo = tptr[row], hi = tptr[row + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (tadj[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return (int32_t)lo;
+}
+
+// reverse arcs and the u->v arc of every tree edge, after the rows were sorted
+__global__ void k_tour_fix_rev(const int64_t* __restrict__ tptr, const int32_t* __restrict__ tadj, int64_t n,
+                               int32_t* __restrict__ rev) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t p = tptr[x]; p < tptr[x + 1]; p++) rev[p] = tour_find(tptr, tadj, tadj[p], (int32_t)x);
+}
+
+__global__ void k_tour_fix_arcs(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                                const uint8_t* __restrict__ tflag, int64_t m, const int64_t* __restrict__ tptr,
+                                const int32_t* __restrict__ tadj, int32_t* __restrict__ arc_uv) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    if (tflag[e]) arc_uv[e] = tour_find(tptr, tadj, eu[e], ev[e]);
+}
+
+}  // namespace
+
+}  // namespace pdg

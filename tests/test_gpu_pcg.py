@@ -58,6 +58,17 @@ def test_exact_preconditioner_and_degenerate_rhs(B):
     assert it == 0 and rel == 0.0
 
 
+def test_deterministic(B):
+    """Every sum runs in a fixed order (the Euler tour of a canonical adjacency): repeated calls agree exactly."""
+    g = W.grid_graph(100)
+    b = np.random.default_rng(0).standard_normal(g.n)
+    ids = O.recover(g, 0.02, c=2)[1]
+    first = B.pcg_quality(g, ids, b)
+    for _ in range(3):
+        assert B.pcg_quality(g, ids, b) == first
+    assert B.pcg_quality(g, ids[:0], b) == B.pcg_quality(g, ids[:0], b)
+
+
 def test_rejects_bad_edge_lists(B):
     g = W.grid_graph(20)
     off = O.offtree_scores(g, c=0)["id"]
