@@ -34,6 +34,10 @@
  *      spanning tree T (Def. "BFS step size").  Stop after alpha*|V| edges
  *      (Sec. 2.2 budget).
  *
+ * Also here: spanning-tree generation, the step before recovery (Sec. 2.2;
+ * Kruskal for the maximum-weight and the effective-weight trees of Eq. weff,
+ * orc_spanning_tree at the end of this file).
+ *
  * Readings of the paper taken here (each is listed with its reason in the
  * design notes of the repository):
  *   - R_T is the exact real path sum, rounded once (the paper gives no
