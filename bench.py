@@ -237,6 +237,23 @@ def ncu_traffic(kernel: str, workload: str):
         return None
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (all ranks call this; one all-reduce)."""
+    if world <= 1:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, units_per_rank: int, t_max_ms: float) -> float:
+    """Replicas: every rank recovers its own copy of the workload, so the job processes world x the units in the
+    slowest rank's time (weak scaling)."""
+    return world * units_per_rank / (t_max_ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None):
     import torch
 
@@ -300,12 +317,8 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
         if i >= args.warmup:
             step_ms.append(sp.last_timings())
     mean_ms = float(np.mean(times))
-    t_max = mean_ms
-    if world > 1:
-        tt = torch.tensor([mean_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * info["n_offtree"] / (t_max / 1e3)
+    t_max = max_over_ranks(mean_ms, world, dev)
+    value = whole_job_value(world, info["n_offtree"], t_max)
     # per-step breakdown and the roofline of the dominant kernel
     names = ["classify", "tree", "score", "select", "sort", "accept", "budget"]
     avg = {nm: float(np.mean([s[nm] for s in step_ms])) for nm in names}
