@@ -93,3 +93,33 @@ def test_options_layout_matches_header(tmp_path):
     assert int(out["size"]) == ctypes.sizeof(binding.Options)
     for f in fields:
         assert int(out[f]) == getattr(binding.Options, f).offset, f
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_device(lib):
+    """pdg_spanning_tree and pdg_pcg_quality check their arguments before any CUDA call."""
+    from paper_2508_20403_gb300 import binding
+
+    L = binding.load()
+    rp = (ctypes.c_int64 * 3)(0, 1, 2)
+    col = (ctypes.c_int32 * 2)(1, 0)
+    w = (ctypes.c_double * 2)(1.0, 1.0)
+    par = (ctypes.c_int32 * 2)(-1, 0)
+    out = (ctypes.c_int32 * 2)()
+    E = binding.PDG_E_INVALID_ARG
+    assert L.pdg_spanning_tree(0, rp, col, w, 0, 0, out, 0, None) == E  # n < 1
+    assert L.pdg_spanning_tree(2, rp, col, w, 0, 7, out, 0, None) == E  # unknown tree kind
+    assert L.pdg_spanning_tree(2, None, col, w, 0, 0, out, 0, None) == E
+    assert L.pdg_spanning_tree(2, rp, col, w, 5, 0, out, 0, None) == E  # memory kind
+    b = (ctypes.c_double * 2)(1.0, -1.0)
+    ids = (ctypes.c_int32 * 1)(0)
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    args = lambda **kw: dict(dict(n=2, rp=rp, col=col, w=w, par=par, ids=ids, k=1, b=b, tol=1e-3, mi=10, kind=0), **kw)
+    call = lambda a: L.pdg_pcg_quality(a["n"], a["rp"], a["col"], a["w"], a["par"], a["ids"], a["k"], a["b"],
+                                       a["tol"], a["mi"], a["kind"], ctypes.byref(it), ctypes.byref(rel), None)
+    assert call(args(tol=0.0)) == E
+    assert call(args(mi=0)) == E
+    assert call(args(k=8193)) == E  # dense capacitance bound
+    assert call(args(k=-1)) == E
+    assert call(args(n=1)) == E
+    assert call(args(b=None)) == E
