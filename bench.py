@@ -119,7 +119,9 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.nvml = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(), f"pdgrass_clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
