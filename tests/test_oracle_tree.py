@@ -170,3 +170,25 @@ def test_tree_invariants_and_disconnected():
     assert (p < 0).sum() == 2
     with pytest.raises(ValueError):
         O.spanning_tree(two, O.TREE_FEGRASS)
+
+
+@pytest.mark.parametrize("n", [5, 6, 7, 8, 11, 12])
+def test_fegrass_cycle_closed_form(n):
+    """Cycle C_n with unit weights: every degree is 2 (L = log 2), the root is vertex 0 (ties: smaller id) and
+    d(i) = min(i, n - i), so W_eff(i, i+1) = log 2 / (d(i) + d(i+1)) is smallest on the edges farthest from 0; the
+    tree drops the one of those with the largest canonical id (ties go to the smaller id) and hangs the two arcs
+    of the cycle from vertex 0."""
+    eu = np.array([min(i, (i + 1) % n) for i in range(n)], dtype=np.int32)
+    ev = np.array([max(i, (i + 1) % n) for i in range(n)], dtype=np.int32)
+    rp, col, w = W.csr_from_edges(n, eu, ev, np.ones(n))
+    g = W.Graph(n=n, row_ptr=rp, col=col, w=w, parent=-np.ones(n, dtype=np.int32), name=f"cycle{n}")
+    d = [min(i, n - i) for i in range(n)]
+    # canonical ids: edges sorted by (u, v)
+    edges = sorted(zip(eu.tolist(), ev.tolist()))
+    sums = [d[a] + d[b] for a, b in edges]
+    far = max(sums)
+    dropped = max(i for i, s in enumerate(sums) if s == far)
+    keep = [e for i, e in enumerate(edges) if i != dropped]
+    want = _rooted_parent(g, n, keep)
+    assert want[0] == -1
+    assert np.array_equal(O.spanning_tree(g, O.TREE_FEGRASS), want)
