@@ -81,3 +81,14 @@ def test_recovered_edges_precondition_better_than_random():
         it_rnd, _ = PC.pcg_quality(g, rnd, b)
         assert its[alpha] < it_rnd
     assert its[0.10] <= its[0.02]
+
+
+def test_rank_k_update_terminates_in_k_plus_one_iterations():
+    """L_G = L_P + (the k edges the preconditioner leaves out): the generalised spectrum is 1 plus at most k other
+    values, so exact-arithmetic CG stops after at most k + 1 iterations (checked with k = 1, 2, 3 missing edges)."""
+    g = W.grid_graph(12, seed=6)
+    off = O.offtree_scores(g, c=0)["id"]
+    b = _rhs(g.n, 7)
+    for missing in (1, 2, 3):
+        it, rel = PC.pcg_quality(g, off[missing:], b, tol=1e-10, max_iter=50)
+        assert it <= missing + 1 and rel <= 1e-10, (missing, it, rel)
