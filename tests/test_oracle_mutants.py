@@ -119,3 +119,69 @@ def test_planted_mistake_is_caught(tmp_path, name):
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="no gcc")
 def test_unmutated_copy_passes(tmp_path):
     assert not _caught(_build(tmp_path, "none", []))
+
+
+PCG_MUTANTS = {
+    "beta inverted": ("p = z + (rz_new / rz) * p", "p = z + (rz / rz_new) * p"),
+    "step length from r.r": ("a = rz / (p @ Ap)", "a = (r @ r) / (p @ Ap)"),
+    "stopping on the squared residual": ("rel = np.linalg.norm(r) / nb", "rel = (np.linalg.norm(r) / nb) ** 2"),
+    "preconditioner ignores the recovered edges": ("LP = sparsifier_laplacian(g, edge_ids)",
+                                                   "LP = sparsifier_laplacian(g, edge_ids[:0])"),
+}
+
+
+def _pcg_module(edit):
+    import importlib.util
+    import sys
+    import types
+
+    src = open(os.path.join(ROOT, "oracle", "pcg.py")).read()
+    if edit:
+        assert edit[0] in src, edit
+        src = src.replace(edit[0], edit[1])
+    mod = types.ModuleType("pcg_mutant")
+    exec(compile(src, "pcg_mutant", "exec"), mod.__dict__)
+    return mod
+
+
+def _pcg_caught(PCm):
+    """The pins' statements: scipy's own CG with the same exact preconditioner, and one iteration for L_P = L_G."""
+    import scipy.sparse.linalg as spla
+
+    from oracle import oracle as O
+
+    g = W.grid_graph(30, seed=4)
+    _, ids, _, _ = O.recover(g, 0.05, c=2)
+    b = np.random.default_rng(1).standard_normal(g.n)
+    it, _ = PCm.pcg_quality(g, ids, b, tol=1e-6)
+    LG = PCm.laplacian_from_csr(g.n, g.row_ptr, g.col, g.w)
+    from oracle import pcg as PC
+
+    LP = PC.sparsifier_laplacian(g, ids)
+    root = int(np.flatnonzero(g.parent < 0)[0])
+    keep = np.flatnonzero(np.arange(g.n) != root)
+    lu = spla.splu(LP[keep][:, keep].tocsc())
+
+    def apply(r):
+        z = np.zeros(g.n)
+        z[keep] = lu.solve(np.asarray(r).ravel()[keep])
+        return z - z.mean()
+
+    count = [0]
+    bc = b - b.mean()
+    spla.cg(LG, bc, rtol=1e-6, atol=0.0, M=spla.LinearOperator((g.n, g.n), matvec=apply), maxiter=2000,
+            callback=lambda xk: count.__setitem__(0, count[0] + 1))
+    if abs(count[0] - it) > 1:
+        return True
+    off = O.offtree_scores(g, c=0)["id"]
+    it_exact, _ = PCm.pcg_quality(g, off, b, tol=1e-8)
+    return it_exact != 1
+
+
+@pytest.mark.parametrize("name", sorted(PCG_MUTANTS))
+def test_planted_pcg_mistake_is_caught(name):
+    assert _pcg_caught(_pcg_module(PCG_MUTANTS[name])), name
+
+
+def test_unmutated_pcg_passes():
+    assert not _pcg_caught(_pcg_module(None))
