@@ -668,8 +668,9 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
+    # the batch and serving legs are reported by rank 0 only (the headline is the replicated recovery)
     batch_graphs = None
-    if not args.no_batch:
+    if not args.no_batch and rank == 0:
         # generated in a spawn pool before any CUDA call in this process
         from paper_2508_20403_gb300 import workloads as W
 
@@ -678,7 +679,7 @@ def main():
                                       workers=min(16, os.cpu_count() or 1))
         log(f"[rank {rank}] generated {len(batch_graphs)} batch graphs in {time.time() - t0:.1f}s")
     serve_graphs = None
-    if not args.no_serve:
+    if not args.no_serve and rank == 0:
         t0 = time.time()
         serve_graphs = serve_pool(args, workers=min(16, os.cpu_count() or 1))
         log(f"[rank {rank}] generated {len(serve_graphs)} serving-pool graphs in {time.time() - t0:.1f}s")
