@@ -62,3 +62,19 @@ def test_tune_small_graph_is_exact(tmp_path):
     with B.Sparsifier.from_graph(g, options=opt) as sp:
         st, ids, sc, _ = sp.recover(0.1, 2, capacity=g.m)
     assert np.array(ids).tolist() == oids.tolist() and np.array_equal(np.array(sc), osc)
+
+
+def test_committed_cache_is_valid():
+    """The cache shipped with the package parses, and every entry holds settings the library accepts."""
+    cache = AT.load_cache(AT.DEFAULT_CACHE)
+    assert cache, "the package ships a tuned cache"
+    for dev, classes in cache.items():
+        assert "|sm" in dev
+        for cls, entry in classes.items():
+            assert cls.startswith("n2^") and "-g2^" in cls
+            o = entry["options"]
+            assert set(o) == set(AT.SPACE)
+            assert 1 <= o["warp_tier_max"] <= 32
+            assert 0 <= o["block_tier_max"] <= 896
+            assert o["sort_tile_keys"] in (2048, 3072, 4096)
+            assert entry["ms"] <= entry["default_ms"] * 1.0001  # never worse than the defaults it was timed against
