@@ -18,6 +18,9 @@
 //   * The device address of the array is looked up once per device, on the
 //     first call made with that device current (cudaGetSymbolAddress).  Make
 //     that first call before any stream capture begins.
+//   * The call waits for its stream on the host (it reads the error word
+//     back), and clears a launch error left by earlier unrelated work before
+//     it checks its own launches.
 #include <mutex>
 
 #include "pdg_internal.cuh"
@@ -145,6 +148,7 @@ extern "C" int pdg_edge_endpoints_noalloc(int64_t n, const int64_t* row_ptr, con
     scratch = g_na_addr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();  // an earlier, unrelated launch error must not be reported as ours
   int num_sms = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kNaBlocks, (n + kBlock - 1) / kBlock));

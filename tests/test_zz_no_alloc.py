@@ -64,3 +64,27 @@ def test_noalloc_rejects_out_of_range(B):
     # a valid call afterwards still succeeds (the error word is cleared per call)
     ids = _device(np.array([0, g.m - 1], dtype=np.int32), torch.int32)
     assert B.edge_endpoints_noalloc(g.n, rp, col, ids, u, v) == B.PDG_OK
+
+
+def test_noalloc_at_the_size_limit(B):
+    """n = PDG_NOALLOC_MAX_N exactly (the 128^3 mesh has 2^21 vertices): every scan block is used and the last
+    row prefix lands in the slot next to the block sums.  A strided set of ids that includes the last id m - 1,
+    twice in a row, must equal the handle path."""
+    import torch
+
+    g = W.mesh3d_graph(128)
+    assert g.n == B.NOALLOC_MAX_N
+    rp, col = _device(g.row_ptr, torch.int64), _device(g.col, torch.int32)
+    ids_np = np.unique(np.concatenate([np.arange(0, g.m, 9973), [g.m - 1, g.m - 2, 1]])).astype(np.int32)
+    eu, ev, _ = g.edges()
+    with B.Sparsifier.from_graph(g, device=True) as sp:
+        for ids_host in (ids_np, ids_np[::-1].copy()):
+            ids = _device(ids_host, torch.int32)
+            want_u, want_v = sp.endpoints(ids)
+            u = torch.full_like(ids, -5)
+            v = torch.full_like(ids, -5)
+            assert B.edge_endpoints_noalloc(g.n, rp, col, ids, u, v) == B.PDG_OK
+            torch.cuda.synchronize()
+            assert torch.equal(u, want_u) and torch.equal(v, want_v)
+            assert u.cpu().numpy().tolist() == eu[ids_host].tolist()
+            assert v.cpu().numpy().tolist() == ev[ids_host].tolist()
