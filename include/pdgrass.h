@@ -215,31 +215,6 @@ int pdg_last_stats(pdg_handle h, int64_t* stats);
 int pdg_last_timings(pdg_handle h, float* ms);
 
 /*
- * pdg_edge_endpoints_noalloc -- the mapping of pdg_edge_endpoints for callers
- * that must not allocate device memory (for example code that may only use a
- * caller-owned memory pool, or a serving loop that must not stall on
- * cudaMalloc/cudaFree).  The paper has no counterpart: this is a service of
- * the library, not a step of the method.
- *
- *   n        vertices of the caller's graph, 1 <= n <= PDG_NOALLOC_MAX_N.
- *   row_ptr  DEVICE int64[n+1], col DEVICE int32[row_ptr[n]]: the symmetric
- *            CSR with sorted rows (as for sparsify_init; not re-validated).
- *   ids      DEVICE int32[count], canonical edge ids; u, v DEVICE
- *            int32[count] receive the endpoints (u < v), or -1 for an id out
- *            of range (then PDG_E_INVALID_ARG is returned).
- *   stream   cudaStream_t for the work; the call returns after the stream
- *            has reached it.
- *
- * No device memory is allocated: the only scratch is a fixed array of about
- * 16 MB inside the library (PDG_NOALLOC_MAX_N + 1 row prefixes plus scan
- * block sums), present on every device that loads the library until the
- * process exits.  Calls share that array, so calls that overlap on one
- * device race and must be serialised by the caller.  The first call on each
- * device looks the array's address up (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.
- * Returns PDG_OK, PDG_E_INVALID_ARG (bad size or id) or PDG_E_CUDA.
- */
-/*
  * pdg_spanning_tree -- generate the spanning tree that recovery starts from
  * (Sec. 2.2: feGRASS's first step builds the tree from the effective weight,
  * Eq. weff; the plain maximum-weight tree is the other common choice).
@@ -296,6 +271,48 @@ int pdg_pcg_quality(int64_t n, const int64_t* row_ptr, const int32_t* col, const
                     const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
                     int mem_kind, int32_t* out_iters, double* out_relres, void* stream);
 
+/*
+ * pdg_pcg_trace -- pdg_pcg_quality with the run's intermediate results, so
+ * that the iteration can be checked step by step (Sec. 5 measure).
+ *
+ *   out_history    host float64[max_iter]: entry i - 1 receives ||r_i|| / ||b'||
+ *                  after iteration i, for i = 1 .. *out_iters.
+ *   out_precond_b  host float64[n]: the preconditioner applied to b', i.e. the
+ *                  solution z of L_P z = b' grounded at the tree root, then
+ *                  centred (the first z of the iteration).
+ *   every other argument and every status as in pdg_pcg_quality; both
+ *   outputs must be non-NULL (else PDG_E_INVALID_ARG).
+ */
+int pdg_pcg_trace(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
+                  const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
+                  int mem_kind, int32_t* out_iters, double* out_relres, double* out_history, double* out_precond_b,
+                  void* stream);
+
+/*
+ * pdg_edge_endpoints_noalloc -- the mapping of pdg_edge_endpoints for callers
+ * that must not allocate device memory (for example code that may only use a
+ * caller-owned memory pool, or a serving loop that must not stall on
+ * cudaMalloc/cudaFree).  The paper has no counterpart: this is a service of
+ * the library, not a step of the method.
+ *
+ *   n        vertices of the caller's graph, 1 <= n <= PDG_NOALLOC_MAX_N.
+ *   row_ptr  DEVICE int64[n+1], col DEVICE int32[row_ptr[n]]: the symmetric
+ *            CSR with sorted rows (as for sparsify_init; not re-validated).
+ *   ids      DEVICE int32[count], canonical edge ids; u, v DEVICE
+ *            int32[count] receive the endpoints (u < v), or -1 for an id out
+ *            of range (then PDG_E_INVALID_ARG is returned).
+ *   stream   cudaStream_t for the work; the call waits on the host until
+ *            the stream has finished it (it synchronises that stream).
+ *
+ * No device memory is allocated: the only scratch is a fixed array of about
+ * 16 MB inside the library (PDG_NOALLOC_MAX_N + 1 row prefixes plus scan
+ * block sums), present on every device that loads the library until the
+ * process exits.  Calls share that array, so calls that overlap on one
+ * device race and must be serialised by the caller.  The first call on each
+ * device looks the array's address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.
+ * Returns PDG_OK, PDG_E_INVALID_ARG (bad size or id) or PDG_E_CUDA.
+ */
 #define PDG_NOALLOC_MAX_N (1 << 21)
 int pdg_edge_endpoints_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* ids,
                                int64_t count, int32_t* u, int32_t* v, void* stream);

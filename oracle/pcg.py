@@ -59,6 +59,12 @@ def sparsifier_laplacian(g, edge_ids) -> sp.csr_matrix:
 
 def pcg_quality(g, edge_ids, b, tol: float = 1e-3, max_iter: int = 1000):
     """Returns (iterations, final relative residual)."""
+    it, rel, _, _ = pcg_trace(g, edge_ids, b, tol, max_iter)
+    return it, rel
+
+
+def pcg_trace(g, edge_ids, b, tol: float = 1e-3, max_iter: int = 1000):
+    """Returns (iterations, final relative residual, the relative residual after each iteration, M(b'))."""
     n = g.n
     LG = laplacian_from_csr(n, g.row_ptr, g.col, g.w)
     LP = sparsifier_laplacian(g, edge_ids)
@@ -77,18 +83,21 @@ def pcg_quality(g, edge_ids, b, tol: float = 1e-3, max_iter: int = 1000):
     x = np.zeros(n)
     r = bb.copy()
     z = M(r)
+    z0 = z.copy()
     p = z.copy()
     rz = r @ z
+    hist = []
     for it in range(1, max_iter + 1):
         Ap = LG @ p
         a = rz / (p @ Ap)
         x += a * p
         r -= a * Ap
         rel = np.linalg.norm(r) / nb
+        hist.append(rel)
         if rel <= tol:
-            return it, rel
+            return it, rel, np.array(hist), z0
         z = M(r)
         rz_new = r @ z
         p = z + (rz_new / rz) * p
         rz = rz_new
-    return max_iter, np.linalg.norm(r) / nb
+    return max_iter, np.linalg.norm(r) / nb, np.array(hist), z0

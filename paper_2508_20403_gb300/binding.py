@@ -37,7 +37,8 @@ TREE_FEGRASS = 1
 
 EXPORTS = ("pdg_default_options", "pdg_status_string", "sparsify_init", "recover_offtree", "sparsifier_free",
            "pdg_edge_endpoints", "sparsify_batch_init", "recover_offtree_batch", "pdg_handle_info",
-           "pdg_last_stats", "pdg_last_timings", "pdg_spanning_tree", "pdg_pcg_quality")
+           "pdg_last_stats", "pdg_last_timings", "pdg_spanning_tree", "pdg_pcg_quality", "pdg_pcg_trace",
+           "pdg_edge_endpoints_noalloc")
 STEP_NAMES = ("classify", "tree", "score", "select", "sort", "accept", "budget", "total")
 
 
@@ -95,6 +96,8 @@ def load(path: Optional[str] = None):
     L.pdg_spanning_tree.restype = c_int
     L.pdg_pcg_quality.argtypes = [i64, P, P, P, P, P, i64, P, f64, i32, c_int, P, P, P]
     L.pdg_pcg_quality.restype = c_int
+    L.pdg_pcg_trace.argtypes = [i64, P, P, P, P, P, i64, P, f64, i32, c_int, P, P, P, P, P]
+    L.pdg_pcg_trace.restype = c_int
     if path is None:
         _lib = L
     return L
@@ -134,6 +137,28 @@ def pcg_quality(g, edge_ids, b, tol: float = 1e-3, max_iter: int = 1000, stream=
     if st != PDG_OK:
         raise PdgError(st, "pdg_pcg_quality")
     return int(it.value), float(rel.value)
+
+
+def pcg_trace(g, edge_ids, b, tol: float = 1e-3, max_iter: int = 1000, stream=None):
+    """pdg_pcg_trace on a workloads.Graph (host arrays): (iterations, final relative residual, the relative
+    residual after each iteration, the preconditioner applied to the centred right-hand side)."""
+    L = load()
+    rp = _host_arr(g.row_ptr, np.int64)
+    col = _host_arr(g.col, np.int32)
+    w = _host_arr(g.w, np.float64)
+    par = _host_arr(g.parent, np.int32)
+    ids = _host_arr(edge_ids, np.int32)
+    bb = _host_arr(b, np.float64)
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    hist = np.zeros(int(max_iter), dtype=np.float64)
+    z0 = np.zeros(int(g.n), dtype=np.float64)
+    st = L.pdg_pcg_trace(int(g.n), _ptr(rp), _ptr(col), _ptr(w), _ptr(par), _ptr(ids) if ids.size else None,
+                         int(ids.size), _ptr(bb), float(tol), int(max_iter), MEM_HOST, ctypes.byref(it),
+                         ctypes.byref(rel), _ptr(hist), _ptr(z0), _stream_ptr(stream))
+    if st != PDG_OK:
+        raise PdgError(st, "pdg_pcg_trace")
+    return int(it.value), float(rel.value), hist[:int(it.value)].copy(), z0
 
 
 def status_string(status: int) -> str:

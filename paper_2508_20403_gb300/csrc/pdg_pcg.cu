@@ -383,7 +383,7 @@ __global__ void k_pc_sub(double* __restrict__ z, const double* __restrict__ t, c
   } while (0)
 
 int pcg_quality(Handle& h, const int32_t* ids, int64_t k, const double* b, double tol, int32_t max_iter,
-                int32_t* iters, double* relres) {
+                int32_t* iters, double* relres, double* hist, double* z0) {
   const int64_t n = h.n, m = h.m;
   cudaStream_t s = h.stream;
   const int gn = grid_for(h, n), gm = grid_for(h, std::max<int64_t>(m, 1)), gk = grid_for(h, std::max<int64_t>(k, 1));
@@ -567,6 +567,10 @@ int pcg_quality(Handle& h, const int32_t* ids, int64_t k, const double* b, doubl
     return PDG_OK;
   }
   if (!precond(r, z)) return fail(PDG_E_CUDA);
+  if (z0) {  // the preconditioner applied to b' (host copy for the caller)
+    PC_CK(cudaMemcpyAsync(z0, z, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    PC_CK(cudaStreamSynchronize(s));
+  }
   PC_CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (!dot(r, z, &rz)) return fail(PDG_E_CUDA);
   double rel = 1.0;
@@ -579,6 +583,7 @@ int pcg_quality(Handle& h, const int32_t* ids, int64_t k, const double* b, doubl
     k_pc_axpy<<<gn, kBlock, 0, s>>>(r, Ap, -a, n);
     if (!dot(r, r, &rr)) return fail(PDG_E_CUDA);
     rel = std::sqrt(rr) / nb;
+    if (hist) hist[it - 1] = rel;
     if (rel <= tol) break;
     if (!precond(r, z)) return fail(PDG_E_CUDA);
     double rz_new = 0;

@@ -92,3 +92,28 @@ def test_rank_k_update_terminates_in_k_plus_one_iterations():
     for missing in (1, 2, 3):
         it, rel = PC.pcg_quality(g, off[missing:], b, tol=1e-10, max_iter=50)
         assert it <= missing + 1 and rel <= 1e-10, (missing, it, rel)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.05])
+def test_trace_preconditioner_solves_the_sparsifier_system(alpha):
+    """The z that pcg_trace reports is a solution of L_P z = b' with mean zero (the preconditioner's definition):
+    checked by a product with a Laplacian assembled independently from the CSR and the parent array, and the
+    residual history ends with the returned residual."""
+    g = W.grid_graph(40, seed=5)
+    ids = O.recover(g, alpha, c=2)[1] if alpha > 0 else np.zeros(0, dtype=np.int32)
+    b = _rhs(g.n, 3)
+    it, rel, hist, z0 = PC.pcg_trace(g, ids, b, tol=1e-3)
+    bb = b - b.mean()
+    # L_P from an edge list: the tree edges (v, parent v) plus the listed off-tree edges
+    eu, ev, ew = g.edges()
+    wmap = {(int(a), int(c)): float(x) for a, c, x in zip(eu, ev, ew)}
+    LPz = np.zeros(g.n)
+    pairs = [(min(v, int(g.parent[v])), max(v, int(g.parent[v]))) for v in range(g.n) if g.parent[v] >= 0]
+    pairs += [(int(eu[i]), int(ev[i])) for i in ids]
+    for a, c in pairs:
+        f = wmap[(a, c)] * (z0[a] - z0[c])
+        LPz[a] += f
+        LPz[c] -= f
+    assert np.abs(LPz - bb).max() <= 1e-9 * np.abs(bb).max()
+    assert abs(z0.mean()) <= 1e-12 * np.abs(z0).max()
+    assert len(hist) == it and hist[-1] == rel
