@@ -105,52 +105,39 @@ __device__ __forceinline__ bool strictly_similar(const int32_t (&Up)[kA], const 
   return (in_ball(Up, U, b) && in_ball(Vp, V, b)) || (in_ball(Up, V, b) && in_ball(Vp, U, b));
 }
 
-__device__ __forceinline__ int32_t anc_step(const int32_t* __restrict__ parent, const int32_t* __restrict__ up1,
-                                            int32_t x, int j) {
-  // j-th ancestor for j <= 3 from level 0 (parent) and level 1 (anc_2)
-  if (x < 0 || j == 0) return x;
-  if (j == 1) return parent[x];
-  if (up1 == nullptr) {  // tree of depth <= 1 has no level 1: anc_2 is above the root
-    return -1;
-  }
-  int32_t y = up1[x];
-  if (j == 2) return y;
-  return y < 0 ? -1 : parent[y];
-}
-
-// Records in (LCA, rank) order.  Each record is oriented so that the child
-// of the LCA above the first endpoint has the smaller id ("side" order; an
-// endpoint equal to the LCA is its own side).  A marker with beta* >= 1 has
-// both endpoints strictly inside the two child subtrees, so it can only mark
-// an edge whose endpoints sit in the same two subtrees in the same order:
-// one probe orientation suffices unless the prober has an endpoint on the LCA.
+// Records in (LCA, rank) order.  Each record is oriented by preorder label
+// (first endpoint = the smaller label): the subtrees of the LCA's children
+// are disjoint label ranges, so this orders the two children below the
+// endpoints the same way for every edge of the subtask (an endpoint equal to
+// the LCA is its own side and has the smaller label).  A marker with
+// beta* >= 1 has both endpoints strictly inside the two child subtrees, so it
+// can only mark an edge whose endpoints sit in the same two subtrees in the
+// same order: one probe orientation suffices unless the prober has an
+// endpoint on the LCA.  Ancestors anc_1..c come from the parent array.
 __global__ void __launch_bounds__(kBlock) k_build_records(
     const int32_t* __restrict__ lsort_rank, const int32_t* __restrict__ rank_cand, const int32_t* __restrict__ cand_idx,
     const int32_t* __restrict__ ou, const int32_t* __restrict__ ov, const int32_t* __restrict__ lca,
-    const uint8_t* __restrict__ side, const u128* __restrict__ P, const int32_t* __restrict__ parent,
-    const int32_t* __restrict__ up,
+    const u128* __restrict__ P, const int32_t* __restrict__ parent,
     int c, const DevScalars* __restrict__ dsc, int64_t cap, int32_t* __restrict__ rec_u, int32_t* __restrict__ rec_v,
     int32_t* __restrict__ rec_anc, int32_t* __restrict__ rec_du, int32_t* __restrict__ rec_dv,
     uint8_t* __restrict__ rec_b, int32_t* __restrict__ rec_rank, int32_t* __restrict__ rec_lca) {
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
-  const int32_t* up1 = up;  // level 1 (anc_2), nullptr for trees of depth <= 1
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = lsort_rank[s];
     const int32_t i = cand_idx[rank_cand[r]];
-    int32_t u = ou[i], v = ov[i];
+    const int32_t u = ou[i], v = ov[i];  // u < v
     const int32_t l = lca[i];
     const int32_t dl = (int32_t)(uint32_t)P[l];
-    int32_t du = (int32_t)(uint32_t)P[u] - dl, dv = (int32_t)(uint32_t)P[v] - dl;
-    if (side[i]) {  // oriented by the step that found the LCA
-      int32_t t = u; u = v; v = t;
-      t = du; du = dv; dv = t;
-    }
+    const int32_t du = (int32_t)(uint32_t)P[u] - dl, dv = (int32_t)(uint32_t)P[v] - dl;
     rec_u[s] = u;
     rec_v[s] = v;
+    int32_t au = u, av = v;
     for (int j = 1; j <= c; j++) {
-      rec_anc[(int64_t)(j - 1) * cap + s] = anc_step(parent, up1, u, j);
-      rec_anc[(int64_t)(c + j - 1) * cap + s] = anc_step(parent, up1, v, j);
+      au = au < 0 ? -1 : parent[au];
+      av = av < 0 ? -1 : parent[av];
+      rec_anc[(int64_t)(j - 1) * cap + s] = au;
+      rec_anc[(int64_t)(c + j - 1) * cap + s] = av;
     }
     rec_du[s] = du;
     rec_dv[s] = dv;
@@ -1069,13 +1056,11 @@ static int accept_coop(Handle& h, int c, int grid, const RecArrays& ra);
 int step_accept(Handle& h, int c) {
   const int grid = h.num_sms * 8;
   const int64_t cap = h.Rcap;
-  const int32_t* up1 = (h.J >= 2) ? h.up : nullptr;
   int st;
   ++h.launches;
   k_build_records<<<grid, kBlock, 0, h.stream>>>(h.lsort_rank, h.rank_cand, h.cand_idx, h.off_u, h.off_v, h.lca,
-                                                  h.side, h.P[h.p_final], h.parent, up1, c, h.dsc, cap, h.rec_u,
-                                                  h.rec_v, h.rec_anc, h.rec_du, h.rec_dv, h.rec_b, h.rec_rank,
-                                                  h.rec_lca);
+                                                  h.P, h.parent, c, h.dsc, cap, h.rec_u, h.rec_v, h.rec_anc,
+                                                  h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.rec_lca);
   // subtask boundaries, tier lists, per-position tiers
   const int64_t lb_tiles = (cap + kLbTile - 1) / kLbTile;
   if (lb_tiles > h.scan_tiles_cap || lb_tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized with the buffers

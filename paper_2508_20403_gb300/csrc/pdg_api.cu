@@ -123,7 +123,7 @@ __global__ void k_reset_recover(DevScalars* dsc) {
 }
 
 __global__ void k_reset_attempt(DevScalars* dsc) {
-  dsc->err &= ERR_RANGE;
+  dsc->err &= ERR_RANGE | ERR_TIMEOUT | ERR_BOUNDS;  // errors of steps A1-A3 end the recovery
   dsc->bounds_site = 0;
   dsc->rounds_used = 0;
   dsc->n_cand = 0;
@@ -145,9 +145,11 @@ __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->n_big_chunk = 0;
 }
 
+// endpoints of canonical ids in the caller's vertex ids (u < v): the edge
+// list holds preorder labels, vtx_of_pre maps them back
 __global__ void k_endpoints(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, int64_t m,
-                            const int32_t* __restrict__ ids, int64_t count, int32_t* __restrict__ ou,
-                            int32_t* __restrict__ ov, DevScalars* dsc) {
+                            const int32_t* __restrict__ vtx_of_pre, const int32_t* __restrict__ ids, int64_t count,
+                            int32_t* __restrict__ ou, int32_t* __restrict__ ov, DevScalars* dsc) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t id = ids[i];
     if (id < 0 || id >= m) {
@@ -155,8 +157,9 @@ __global__ void k_endpoints(const int32_t* __restrict__ eu, const int32_t* __res
       ou[i] = ov[i] = -1;
       continue;
     }
-    ou[i] = eu[id];
-    ov[i] = ev[id];
+    const int32_t a = vtx_of_pre[eu[id]], b = vtx_of_pre[ev[id]];
+    ou[i] = min(a, b);
+    ov[i] = max(a, b);
   }
 }
 
@@ -448,15 +451,12 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
     h.off_ptr_h[g + 1] = h.off_ptr_h[g] + (mg - ng + 1);
   }
   h.E_off = h.off_ptr_h[num_graphs];
-  h.J = 0;
-  while ((1ll << h.J) <= h.max_depth) h.J++;
   // workspace
   const int64_t E = std::max<int64_t>(h.E_off, 1);
   if ((st = alloc_n(h, &h.d_edge_ptr, num_graphs + 1)) || (st = alloc_n(h, &h.d_off_ptr, num_graphs + 1)) ||
       (st = alloc_n(h, &h.off_u, E)) || (st = alloc_n(h, &h.off_v, E)) || (st = alloc_n(h, &h.off_id, E)) ||
-      (st = alloc_n(h, &h.off_w, E)) || (st = alloc_n(h, &h.rtree, n)) || (st = alloc_n(h, &h.P[0], n)) ||
-      (st = alloc_n(h, &h.P[1], n)) || (st = alloc_n(h, &h.up, (int64_t)std::max(h.J - 1, 1) * n)) ||
-      (st = alloc_n(h, &h.key, E)) || (st = alloc_n(h, &h.lca, E)) || (st = alloc_n(h, &h.side, E)) ||
+      (st = alloc_n(h, &h.off_w, E)) || (st = alloc_n(h, &h.rtree, n)) ||
+      (st = alloc_n(h, &h.key, E)) || (st = alloc_n(h, &h.lca, E)) ||
       (st = alloc_n(h, &h.hist, (int64_t)num_graphs * kSelBins)) || (st = alloc_n(h, &h.sel, num_graphs)) ||
       (st = alloc_n(h, &h.d_cand_ptr, num_graphs + 1)) || (st = alloc_n(h, &h.d_graph_tmp, num_graphs + 1)) ||
       (st = alloc_n(h, &h.gstat, num_graphs)) || (st = alloc_n(h, &h.gcount, num_graphs)) ||
@@ -465,6 +465,8 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       (st = alloc_n(h, &h.radix_counters, 2 * kRadixPassesMax)) ||
       (st = ensure_scan_status(h, std::max<int64_t>(std::max<int64_t>(n, num_graphs), E) + 1)))
     return fail(st);
+  // the tree's layout: preorder labels, Euler tour, the relabelled edge list and parents
+  if ((st = build_tree_layout(h)) || (st = tree_scan_workspace(h))) return fail(st);
   HostStage& s = hp->stage;
   s.G = num_graphs;
   s.sel = static_cast<GraphSel*>(pinned_alloc(sizeof(GraphSel) * num_graphs));
@@ -552,9 +554,12 @@ int pdg_spanning_tree(int64_t n, const int64_t* row_ptr, const int32_t* col, con
   return PDG_OK;
 }
 
-int pdg_pcg_quality(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
-                    const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
-                    int mem_kind, int32_t* out_iters, double* out_relres, void* stream) {
+}  // extern "C"
+
+// pdg_pcg_quality and pdg_pcg_trace: hist and z0 are nullable host outputs
+static int pcg_entry(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
+                     const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
+                     int mem_kind, int32_t* out_iters, double* out_relres, double* hist, double* z0, void* stream) {
   if (n < 2 || n >= (1ll << 30) || !row_ptr || !parent || !b || !out_iters || !out_relres || n_edges < 0 ||
       n_edges > kPcgMaxEdges || (n_edges > 0 && !edge_ids) || !(tol > 0) || max_iter < 1 ||
       (mem_kind != PDG_MEM_HOST && mem_kind != PDG_MEM_DEVICE))
@@ -613,11 +618,29 @@ int pdg_pcg_quality(int64_t n, const int64_t* row_ptr, const int32_t* col, const
     return fail(st);
   int32_t it = 0;
   double rel = 0.0;
-  if ((st = pcg_quality(h, d_ids, n_edges, d_b, tol, max_iter, &it, &rel))) return fail(st);
+  if ((st = pcg_quality(h, d_ids, n_edges, d_b, tol, max_iter, &it, &rel, hist, z0))) return fail(st);
   *out_iters = it;
   *out_relres = rel;
   sparsifier_free(hp);
   return PDG_OK;
+}
+
+extern "C" {
+
+int pdg_pcg_quality(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
+                    const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
+                    int mem_kind, int32_t* out_iters, double* out_relres, void* stream) {
+  return pcg_entry(n, row_ptr, col, w, parent, edge_ids, n_edges, b, tol, max_iter, mem_kind, out_iters, out_relres,
+                   nullptr, nullptr, stream);
+}
+
+int pdg_pcg_trace(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w, const int32_t* parent,
+                  const int32_t* edge_ids, int64_t n_edges, const double* b, double tol, int32_t max_iter,
+                  int mem_kind, int32_t* out_iters, double* out_relres, double* out_history, double* out_precond_b,
+                  void* stream) {
+  if (!out_history || !out_precond_b) return PDG_E_INVALID_ARG;
+  return pcg_entry(n, row_ptr, col, w, parent, edge_ids, n_edges, b, tol, max_iter, mem_kind, out_iters, out_relres,
+                   out_history, out_precond_b, stream);
 }
 
 int sparsify_init(pdg_handle* out, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* w,
@@ -809,6 +832,11 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
         for (int i = 0; i < 3; i++) cudaEventElapsedTime(&acc_ms[i], h.ev[i], h.ev[i + 1]);
     }
     const int err = h.hsc->err;
+    if (getenv("PDG_DEBUG_ATTEMPTS"))
+      fprintf(stderr, "pdgrass: attempt %d err %d n_cand %lld n_big %lld n_big_seg %lld big_regs %lld table_cap %lld "
+                      "xcap %lld Rcap %lld\n", attempts, err, (long long)h.hsc->n_cand, (long long)h.hsc->n_big,
+              (long long)h.hsc->n_big_seg, (long long)h.hsc->big_regs, (long long)h.table_cap, (long long)h.xcap,
+              (long long)h.Rcap);
     if (err & ERR_RANGE) return PDG_E_RANGE;
     if (err & ERR_TIMEOUT) return PDG_E_TIMEOUT;
     if (err & ERR_TABLE) {
@@ -989,7 +1017,8 @@ int pdg_edge_endpoints(pdg_handle hp, const int32_t* ids, int64_t count, int32_t
   ++h.launches;
   k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
   ++h.launches;
-  k_endpoints<<<grid_for(h, count), kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.m, d_ids, count, d_u, d_v, h.dsc);
+  k_endpoints<<<grid_for(h, count), kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.m, h.vtx_of_pre, d_ids, count, d_u,
+                                                            d_v, h.dsc);
   if (mem_kind == PDG_MEM_HOST) {
     PDG_CUDA(cudaMemcpyAsync(u, d_u, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, h.stream));
     PDG_CUDA(cudaMemcpyAsync(v, d_v, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, h.stream));

@@ -4,12 +4,14 @@
 //
 // Canonical id of {u, v}, u < v: rank of the CSR entry (u, v) among all
 // entries with row < col in row-major order.  The handle keeps the graph as
-// its canonical edge list (u, v, w in id order; built once from the CSR by
-// build_edge_list at init), so every recovery classifies by streaming that
-// list: edge (u, v) is a tree edge iff parent[v] == u or parent[u] == v.  The
-// write pass also records, for every non-root vertex x, r(x) =
-// fl(1/w(x, parent x)) (the resistive weight W_re = 1/w of Eq. RT), and the
-// exponent range of these r that fixes the fixed-point scale of step A2.
+// its canonical edge list (id order; built once from the CSR by
+// build_edge_list at init, endpoints then relabelled in the tree's preorder
+// as (a, b), a < b), so every recovery classifies by streaming that list: a
+// parent's label is below its child's, so edge (a, b) is a tree edge iff
+// parent[b] == a.  The write pass also records, for every non-root vertex x,
+// r(x) = fl(1/w(x, parent x)) (the resistive weight W_re = 1/w of Eq. RT),
+// computed on the integer pipes (pdg_fp.cuh), and the exponent range of these
+// r that fixes the fixed-point scale of step A2.
 //
 // Layout: each block owns a contiguous chunk of edges (CSR entries for the
 // edge-list build), taken in tiles of kTile; each thread reads kItems
@@ -17,6 +19,7 @@
 // write pass that places each tile's output as one contiguous run.
 #include <climits>
 
+#include "pdg_fp.cuh"
 #include "pdg_internal.cuh"
 
 namespace pdg {
@@ -182,8 +185,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_list(const int64_t* __restrict_
 
 // Recovery-time classification of the canonical edge list.  Count pass:
 // off-tree edges per block.  Write pass: r(x) for the tree edges (queued per
-// warp so the FP64 reciprocals run densely -- a division per lane per item
-// would keep the slow double-precision pipe busy for every edge) and the
+// warp so the reciprocals run densely, every lane on a tree edge) and the
 // off-tree SoA, staged per tile and written as one coalesced run.
 template <bool WRITE>
 __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
@@ -215,22 +217,15 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__
       load_cols(eu, base, b1, a);
       load_cols(ev, base, b1, b);
       if (WRITE) load_weights(ew, base, b1, x);
-      int32_t pa[kItems], pb[kItems];
+      int32_t pb[kItems];
 #pragma unroll
-      for (int i = 0; i < kItems; i++) {
-        const bool ok = base + i < b1;
-        pa[i] = ok ? __ldg(parent + a[i]) : -1;
-        pb[i] = ok ? __ldg(parent + b[i]) : -1;
-      }
+      for (int i = 0; i < kItems; i++) pb[i] = (base + i < b1) ? __ldg(parent + b[i]) : -1;
 #pragma unroll
       for (int i = 0; i < kItems; i++) {
         if (base + i >= b1) continue;
         if (pb[i] == a[i]) {
           is_tree |= 1u << i;
           child[i] = b[i];
-        } else if (pa[i] == b[i]) {
-          is_tree |= 1u << i;
-          child[i] = a[i];
         } else {
           is_off |= 1u << i;
         }
@@ -257,7 +252,10 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__
       const int tot = __shfl_sync(0xffffffffu, incl, 31);
       for (int j = lane; j < tot; j += 32) {
         const int q = wid * (kTile / (kBlock / 32)) + j;
-        const double r = 1.0 / st_w[q];
+        const double wq = st_w[q];
+        bool ok;
+        const uint64_t rb = rcp_rn_bits((uint64_t)__double_as_longlong(wq), &ok);
+        const double r = ok ? __longlong_as_double((long long)rb) : __drcp_rn(wq);
         rtree[st_u[q]] = r;
         const int e = (int)(((uint64_t)__double_as_longlong(r) >> 52) & 0x7ff) - 1023;
         e_lo = min(e_lo, e);

@@ -27,6 +27,7 @@ constexpr int kBlockTierMax = 896;      // <= kBlockTierSlots / (2 * 9)
 constexpr int kBlockTierDefault = 0;  // off: on the mesh and R-MAT workloads the cooperative tier is faster
 constexpr int kRadixHistWords = 16 * 256 + 2 * kRadixPassesMax;  // + skip flags, buffer choices
 constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kRmqMaxLevels = 6;  // levels of the range-minimum structure (n < 2^30: 30 / 5)
 
 // error bits raised by validation kernels (mapped to a status on the host)
 enum : int {
@@ -138,17 +139,23 @@ struct Handle {
   // sizes
   int64_t n = 0, nnz = 0, m = 0, E_off = 0, max_depth = 0;
   int32_t G = 1;
-  int J = 0;  // pointer-jumping rounds = bit length of the max depth
   std::vector<int64_t> vtx_ptr_h, edge_ptr_h, off_ptr_h;  // G+1 each
 
   // resident graph
   int64_t* row_ptr = nullptr;  // input CSR: resident during init only
   int32_t* col = nullptr;
   double* w = nullptr;
-  int32_t* el_u = nullptr;  // canonical edge list (u < v, id order), resident
+  // canonical edge list in id order, resident; after the tree layout its
+  // endpoints are preorder labels, el_u < el_v
+  int32_t* el_u = nullptr;
   int32_t* el_v = nullptr;
   double* el_w = nullptr;
-  int32_t* parent = nullptr;
+  int32_t* parent = nullptr;  // in preorder labels once the tree layout is built
+  // tree layout (sparsify_init): Euler tour (A arcs: label entered, or ~label
+  // left), the caller's vertex id of every preorder label
+  int32_t* tour = nullptr;
+  int64_t A = 0;
+  int32_t* vtx_of_pre = nullptr;
   int64_t* d_vtx_ptr = nullptr;
   int64_t* d_edge_ptr = nullptr;
   int64_t* d_off_ptr = nullptr;
@@ -163,15 +170,20 @@ struct Handle {
   int64_t* blk_b = nullptr;
   int nblk = 0;
 
-  // tree: P(v) = D(v) * 2^32 + depth(v); D = exact root distance in units of 2^-S
-  u128* P[2] = {nullptr, nullptr};
-  int32_t* up = nullptr;  // levels 1..J-1 (level 0 is parent)
-  int p_final = 0;
+  // tree: P(x) = D(x) * 2^32 + depth(x); D = exact root distance in units of 2^-S
+  u128* P = nullptr;
+  // range-minimum structure over val0[x] = depth(x) * 2^32 + parent(x):
+  // level j + 1 holds the minima of the 32-entry groups of level j
+  int rmq_levels = 0;
+  int64_t rmq_size[kRmqMaxLevels] = {0};
+  uint64_t* rmq_val[kRmqMaxLevels] = {nullptr};
+  uint32_t* rmq_mask[kRmqMaxLevels] = {nullptr};
+  u128* ts_sum = nullptr;        // tree scan: tile sums, then their prefixes
+  uint32_t* ts_done = nullptr;   // blocks finished: [0] tree-scan tile sums, [1] range-minimum build
 
   // scores
   uint64_t* key = nullptr;  // FP64 score bits (positive -> order preserving)
-  int32_t* lca = nullptr;
-  uint8_t* side = nullptr;  // per off-tree edge: 1 iff the v-side child of the LCA has the smaller id
+  int32_t* lca = nullptr;   // preorder label of the LCA
 
   // selection
   uint32_t* hist = nullptr;  // G * kSelBins
@@ -433,6 +445,8 @@ int scan_excl_u8(Handle& h, const uint8_t* in, int64_t* out, const int64_t* n_de
 // steps
 int validate_graph(Handle& h);                  // sparsify_init checks + max depth
 int build_edge_list(Handle& h);                 // init: canonical edge list from the CSR
+int build_tree_layout(Handle& h);               // init: preorder labels, Euler tour, relabelled edges and parents
+int tree_scan_workspace(Handle& h);             // init: look-back space of the tree scan
 int step_classify(Handle& h);                   // A1
 int step_tree(Handle& h);                       // A2
 int step_score(Handle& h, int score_mode);      // A3
@@ -443,8 +457,10 @@ int coop_rounds(const Handle& h, int c);        // cooperative-tier rounds the n
 int validate_csr(Handle& h);                    // CSR shape, symmetry and weights only
 int spanning_tree(Handle& h, int tree_kind, int32_t* parent);  // parent array of the generated tree (device)
 constexpr int64_t kPcgMaxEdges = 8192;  // recovered edges of the PCG quality measure (dense k x k capacitance)
+// device ids and b; host results (hist: nullable, the relative residual after each iteration;
+// z0: nullable, the preconditioner applied to the centred right-hand side, n values)
 int pcg_quality(Handle& h, const int32_t* ids, int64_t k, const double* b, double tol, int32_t max_iter,
-                int32_t* iters, double* relres);  // device ids and b; host results
+                int32_t* iters, double* relres, double* hist = nullptr, double* z0 = nullptr);
 int step_sort(Handle& h);                       // A4b: (graph, score desc, id asc) then (lca, rank)
 int step_accept(Handle& h, int c);              // A5 + A6
 int step_budget(Handle& h, int32_t* out_ids, double* out_scores);  // A7

@@ -1,21 +1,28 @@
-// Step A2: tree preprocessing of Algorithm 1 (root distances "dists" and the
-// skip table for LCA queries, Algorithm 1 step 1; Sec. 4.2 work/span analysis).
+// Step A2: tree preprocessing of Algorithm 1 step 1 -- the root distances
+// ("dists") and the structure that answers LCA queries (the skip table's
+// role), recomputed by every recovery from the tree layout built at init.
 //
 // Root distances are EXACT: every r(v) = fl(1/w(v, parent v)) is a multiple
 // of 2^-S with S = 52 - min_v exponent(r(v)), so D(v) = sum of r on the root
-// path is an integer in units of 2^-S.  Integer addition is associative, so
-// pointer jumping produces the same bits as any sequential walk, and
-// R_T(u, v) = D(u) + D(v) - 2 D(LCA) is exact before its single rounding.
+// path is an integer in units of 2^-S, and R_T(u, v) = D(u) + D(v) - 2 D(LCA)
+// (Eq. RT) is exact before its single rounding.  Each vertex carries one
+// 128-bit word P(v) = D(v) * 2^32 + depth(v); D < 2^96 is checked from the
+// exponent range and the maximum depth (PDG_E_RANGE otherwise).
 //
-// Each vertex carries one 128-bit word P(v) = D(v) * 2^32 + hops(v): one
-// 16-byte gather moves both the distance and the hop depth, and one 128-bit
-// add advances both during pointer jumping (depth < 2^30 never carries into
-// D).  D must stay below 2^96; this is checked from the exponent range and
-// the maximum depth before jumping (PDG_E_RANGE otherwise).
+// k_tree_sum + k_tree_scan: one prefix sum over the Euler tour.  A down arc
+// into v adds word(v) = fixed(r(v)) * 2^32 + 1, an up arc out of v subtracts
+// it, so the running sum at v's down arc is P(v).  Integer addition is
+// associative: the tiled scan gives the same bits as a sequential walk.  The
+// same pass writes, per vertex (preorder label x), the range-minimum key
+// val0[x] = depth(x) * 2^32 + parent(x).
 //
-// Pointer jumping: after round j, jump(v) = anc_{2^(j+1)}(v) and P(v) sums
-// the path from v up to (not including) jump(v), or to the root.  The jump
-// pointers of the rounds are the binary-lifting table (level j = anc_{2^j}).
+// k_rmq_levels: the range-minimum structure over val0.  Level j + 1 holds the
+// minima of the 32-entry groups of level j, up to a single group.  Inside a
+// group, mask[k] has bit i set when entry i (i <= k) has a smaller depth than
+// every later entry up to k (a suffix minimum); the minimum depth over [i, k]
+// in one group is then found at the lowest set bit of mask[k] at or above i.
+// A query (step A3) combines at most two partial groups per level.
+#include <algorithm>
 #include <climits>
 
 #include "pdg_internal.cuh"
@@ -24,8 +31,8 @@ namespace pdg {
 
 namespace {
 
-// P(v) of the bare edge to the parent: fixed(r(v)) * 2^32 + 1 (0 at a root).
-// fixed(r) = mant * 2^(e - 52 + S) with S = 52 - e_min.
+// word(v) of the edge to the parent: fixed(r(v)) * 2^32 + 1, with
+// fixed(r) = mant * 2^(e - 52 + S) and S = 52 - e_min
 __device__ __forceinline__ u128 edge_word(double r, int e_min, bool range_ok) {
   const uint64_t b = (uint64_t)__double_as_longlong(r);
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
@@ -42,80 +49,285 @@ __device__ __forceinline__ bool range_fits(DevScalars* dsc, int dep_bits) {
   return ok;
 }
 
-// The edge words alone (a forest of single vertices has no jumping round).
-__global__ void k_tree_init(const int32_t* __restrict__ parent, const double* __restrict__ rtree, int64_t n,
-                            int dep_bits, DevScalars* dsc, u128* __restrict__ P0) {
-  const bool range_ok = range_fits(dsc, dep_bits);
-  const int e_min = dsc->e_min;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    P0[v] = parent[v] >= 0 ? edge_word(rtree[v], e_min, range_ok) : (u128)0;
+__device__ __forceinline__ u128 shfl_up_u128(u128 x, int d) {
+  const uint64_t lo = __shfl_up_sync(0xffffffffu, (unsigned long long)(uint64_t)x, d);
+  const uint64_t hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(uint64_t)(x >> 64), d);
+  return ((u128)hi << 64) | lo;
 }
 
-// Round 0 of the pointer jumping with the edge words built on the fly:
-// P(v) = word(v) + word(parent v), jump(v) = parent(parent v).
-__global__ void __launch_bounds__(kBlock) k_tree_first(const int32_t* __restrict__ parent,
-                                                       const double* __restrict__ rtree, int64_t n, int dep_bits,
-                                                       DevScalars* dsc, u128* __restrict__ Pout,
-                                                       int32_t* __restrict__ jout) {
-  const bool range_ok = range_fits(dsc, dep_bits);
-  const int e_min = dsc->e_min;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t a = parent[v];
-    u128 p = 0;
-    int32_t na = -1;
-    if (a >= 0) {
-      p = edge_word(rtree[v], e_min, range_ok);
-      na = parent[a];
-      if (na >= 0) p += edge_word(rtree[a], e_min, range_ok);
-    }
-    Pout[v] = p;
-    if (jout) jout[v] = na;
+__device__ __forceinline__ u128 shfl_xor_u128(u128 x, int d) {
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)x, d);
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)(x >> 64), d);
+  return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 warp_incl_scan_u128(u128 x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const u128 y = shfl_up_u128(x, d);
+    if (lane >= d) x += y;
+  }
+  return x;
+}
+
+// The tour is scanned in tiles of 256 threads x 8 arcs, reduce-then-scan:
+// k_tree_sum adds each tile's arcs (the last block to finish turns the tile
+// sums into exclusive prefixes), k_tree_scan rescans every tile from its
+// prefix and writes the vertices.  No tile waits on another (a chained scan
+// would have to pass the running prefix through every tile in order).
+constexpr int kTsThreads = 256;
+constexpr int kTsItems = 8;
+constexpr int kTsTile = kTsThreads * kTsItems;
+
+struct TreeScanArgs {
+  const int32_t* tour;
+  int64_t A;
+  const double* rtree;
+  const int32_t* parent;
+  int dep_bits;
+  DevScalars* dsc;
+  u128* P;
+  uint64_t* val0;
+  u128* tsum;     // [tiles] tile sums, then their exclusive prefixes
+  uint32_t* done;  // blocks of k_tree_sum finished (the last one resets it)
+};
+
+// the tile's arcs of this thread (INT_MIN past the end) and the r of their vertices
+__device__ __forceinline__ void load_arcs(const TreeScanArgs& a, int64_t base, int32_t (&arc)[kTsItems],
+                                          double (&r)[kTsItems]) {
+  if (base + kTsItems <= a.A) {
+    const int4* p4 = reinterpret_cast<const int4*>(a.tour + base);
+    const int4 x = __ldg(p4), y = __ldg(p4 + 1);
+    arc[0] = x.x; arc[1] = x.y; arc[2] = x.z; arc[3] = x.w;
+    arc[4] = y.x; arc[5] = y.y; arc[6] = y.z; arc[7] = y.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < kTsItems; i++) arc[i] = (base + i < a.A) ? __ldg(a.tour + base + i) : INT_MIN;
+  }
+#pragma unroll
+  for (int i = 0; i < kTsItems; i++) {
+    const int32_t x = arc[i] >= 0 ? arc[i] : ~arc[i];
+    r[i] = (arc[i] != INT_MIN) ? __ldg(a.rtree + x) : 0.0;
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_tree_jump(const u128* __restrict__ Pin, u128* __restrict__ Pout,
-                                                      const int32_t* __restrict__ jin,
-                                                      int32_t* __restrict__ jout, int64_t n) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t a = jin[v];
-    u128 p = Pin[v];
-    int32_t na = -1;
-    if (a >= 0) {
-      p += Pin[a];
-      na = jin[a];
-    }
-    Pout[v] = p;
-    if (jout) jout[v] = na;
+// +word(x) for the down arc into x, -word(x) for the up arc out of x
+__device__ __forceinline__ u128 arc_word(int32_t arc, double r, int e_min, bool range_ok) {
+  if (arc == INT_MIN) return 0;
+  const u128 w = edge_word(r, e_min, range_ok);
+  return arc >= 0 ? w : (u128)0 - w;
+}
+
+__device__ __forceinline__ u128 block_sum_u128(u128 x, u128* s_warp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d; d >>= 1) x += shfl_xor_u128(x, d);
+  if (lane == 0) s_warp[wid] = x;
+  __syncthreads();
+  u128 t = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_warp[w];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kTsThreads) k_tree_sum(TreeScanArgs a) {
+  __shared__ u128 s_warp[kTsThreads / 32];
+  __shared__ int s_last;
+  const bool range_ok = range_fits(a.dsc, a.dep_bits);
+  const int e_min = a.dsc->e_min;
+  const int64_t t = blockIdx.x;
+  int32_t arc[kTsItems];
+  double r[kTsItems];
+  load_arcs(a, t * kTsTile + (int64_t)threadIdx.x * kTsItems, arc, r);
+  u128 s = 0;
+#pragma unroll
+  for (int i = 0; i < kTsItems; i++) s += arc_word(arc[i], r[i], e_min, range_ok);
+  const u128 tot = block_sum_u128(s, s_warp);
+  if (threadIdx.x == 0) {
+    a.tsum[t] = tot;
+    __threadfence();
+    s_last = (atomicAdd(a.done, 1u) == gridDim.x - 1) ? 1 : 0;
   }
+  __syncthreads();
+  if (!s_last) return;
+  // the last block: exclusive prefixes of the tile sums, in chunks of one value per thread
+  __threadfence();
+  const int64_t tiles = gridDim.x;
+  u128 run = 0;
+  for (int64_t c0 = 0; c0 < tiles; c0 += kTsThreads) {
+    const int64_t i = c0 + threadIdx.x;
+    u128 v = 0;
+    if (i < tiles) {
+      const ulonglong2 q = __ldcg(reinterpret_cast<const ulonglong2*>(a.tsum + i));
+      v = ((u128)q.y << 64) | q.x;
+    }
+    const u128 incl = warp_incl_scan_u128(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    u128 before = run;
+    for (int w = 0; w < wid; w++) before += s_warp[w];
+    u128 chunk = 0;
+    for (int w = 0; w < kTsThreads / 32; w++) chunk += s_warp[w];
+    if (i < tiles) a.tsum[i] = before + incl - v;
+    run += chunk;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.done = 0;
+}
+
+__global__ void __launch_bounds__(kTsThreads) k_tree_scan(TreeScanArgs a) {
+  __shared__ u128 s_warp[kTsThreads / 32];
+  const bool range_ok = range_fits(a.dsc, a.dep_bits);
+  const int e_min = a.dsc->e_min;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t t = blockIdx.x;
+  int32_t arc[kTsItems];
+  double r[kTsItems];
+  load_arcs(a, t * kTsTile + (int64_t)threadIdx.x * kTsItems, arc, r);
+  u128 s = 0;
+#pragma unroll
+  for (int i = 0; i < kTsItems; i++) s += arc_word(arc[i], r[i], e_min, range_ok);
+  const u128 incl = warp_incl_scan_u128(s);
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  const ulonglong2 q = __ldcg(reinterpret_cast<const ulonglong2*>(a.tsum + t));  // the tile's prefix
+  u128 p = ((u128)q.y << 64) | q.x;
+  for (int w = 0; w < wid; w++) p += s_warp[w];
+  p += incl - s;  // prefix of every arc before this thread's first
+#pragma unroll
+  for (int i = 0; i < kTsItems; i++) {
+    if (arc[i] == INT_MIN) continue;
+    p += arc_word(arc[i], r[i], e_min, range_ok);
+    if (arc[i] >= 0) {  // the down arc into x: P(x) and the range-minimum key
+      const int32_t x = arc[i];
+      a.P[x] = p;
+      a.val0[x] = ((uint64_t)(uint32_t)p << 32) | (uint32_t)__ldg(a.parent + x);
+    }
+  }
+}
+
+// The range-minimum structure in one launch.  Each block takes 8192 entries
+// of level 0 (256 groups) and then the 256 group minima it produced (8 groups
+// of level 1); the last block to finish builds the remaining, small levels.
+// A group's masks come from one thread walking its 32 entries in order with
+// a stack of suffix minima kept as a bit set: an entry pops the stacked
+// entries whose depth is not below its own, then pushes itself, and the
+// stack after entry k is mask[k].  Entries are staged in shared memory with
+// a padded row per group, so loads, walks and stores are conflict-free.
+constexpr int kRmqThreads = 256;
+constexpr int kRmqChunk = kRmqThreads * 32;  // entries per block and pass
+
+struct RmqArgs {
+  uint64_t* val[kRmqMaxLevels];
+  uint32_t* mask[kRmqMaxLevels];
+  int64_t size[kRmqMaxLevels];
+  int levels;
+  uint32_t* done;  // blocks finished (the last one resets it)
+};
+
+// entries [base, base + len) of one level (len <= kRmqChunk, base a multiple
+// of 32): their masks, and the minimum of every group to val_next[entry / 32]
+// when val_next is given
+__device__ void rmq_chunk(const uint64_t* __restrict__ val, int64_t size, int64_t base, int len,
+                          uint32_t* __restrict__ mask, uint64_t* __restrict__ val_next, uint32_t (*s_d)[33]) {
+  const int t = threadIdx.x;
+  const int ngroups = (len + 31) / 32;
+  for (int i = t; i < ngroups * 32; i += kRmqThreads) {
+    const int64_t idx = base + i;
+    s_d[i >> 5][i & 31] = (i < len && idx < size) ? (uint32_t)(__ldcg(val + idx) >> 32) : 0xffffffffu;
+  }
+  __syncthreads();
+  const bool walk = t < ngroups && base + 32 * t < size;
+  uint32_t m[32];
+  if (walk) {
+    uint32_t stack = 0;
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+      const uint32_t d = s_d[t][k];
+      while (stack) {  // pop the entries whose depth is not below d
+        const int top = 31 - __clz(stack);
+        if (s_d[t][top] < d) break;
+        stack &= ~(1u << top);
+      }
+      stack |= 1u << k;
+      m[k] = stack;
+    }
+    if (val_next) val_next[(base >> 5) + t] = __ldcg(val + base + 32 * t + (__ffs(stack) - 1));
+  }
+  __syncthreads();  // every walk is done: the rows now take the masks
+  if (walk) {
+#pragma unroll
+    for (int k = 0; k < 32; k++) s_d[t][k] = m[k];
+  }
+  __syncthreads();
+  for (int i = t; i < len; i += kRmqThreads) {
+    const int64_t idx = base + i;
+    if (idx < size) mask[idx] = s_d[i >> 5][i & 31];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kRmqThreads) k_rmq_build(RmqArgs a) {
+  __shared__ uint32_t s_d[kRmqThreads][33];
+  __shared__ int s_last;
+  const int64_t b0 = (int64_t)blockIdx.x * kRmqChunk;
+  rmq_chunk(a.val[0], a.size[0], b0, kRmqChunk, a.mask[0], a.levels > 1 ? a.val[1] : nullptr, s_d);
+  if (a.levels > 1)
+    rmq_chunk(a.val[1], a.size[1], b0 / 32, kRmqThreads, a.mask[1], a.levels > 2 ? a.val[2] : nullptr, s_d);
+  if (a.levels <= 2) return;  // uniform
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(a.done, 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int j = 2; j < a.levels; j++)
+    for (int64_t base = 0; base < a.size[j]; base += kRmqChunk)
+      rmq_chunk(a.val[j], a.size[j], base, (int)min((int64_t)kRmqChunk, a.size[j] - base), a.mask[j],
+                j + 1 < a.levels ? a.val[j + 1] : nullptr, s_d);
+  if (threadIdx.x == 0) *a.done = 0;
 }
 
 }  // namespace
 
 int step_tree(Handle& h) {
-  const int64_t n = h.n;
-  const int grid = grid_for(h, n);
   int dep_bits = 0;
   while ((1ll << dep_bits) <= h.max_depth) dep_bits++;
-  int cur = 0;
-  if (h.J == 0) {  // no vertex has a parent
+  if (h.A > 0) {
+    const int64_t tiles = (h.A + kTsTile - 1) / kTsTile;
+    TreeScanArgs a{h.tour, h.A, h.rtree, h.parent, dep_bits, h.dsc, h.P, h.rmq_val[0], h.ts_sum, h.ts_done};
     ++h.launches;
-    k_tree_init<<<grid, kBlock, 0, h.stream>>>(h.parent, h.rtree, n, dep_bits, h.dsc, h.P[0]);
-  } else {
+    k_tree_sum<<<(int)tiles, kTsThreads, 0, h.stream>>>(a);
     ++h.launches;
-    k_tree_first<<<grid, kBlock, 0, h.stream>>>(h.parent, h.rtree, n, dep_bits, h.dsc, h.P[1],
-                                                 h.J > 1 ? h.up : nullptr);
-    cur = 1;
+    k_tree_scan<<<(int)tiles, kTsThreads, 0, h.stream>>>(a);
+    PDG_CUDA(cudaGetLastError());
   }
-  PDG_CUDA(cudaGetLastError());
-  for (int j = 1; j < h.J; j++) {
-    const int32_t* jin = h.up + (int64_t)(j - 1) * n;
-    int32_t* jout = (j + 1 < h.J) ? h.up + (int64_t)j * n : nullptr;
-    ++h.launches;
-    k_tree_jump<<<grid, kBlock, 0, h.stream>>>(h.P[cur], h.P[cur ^ 1], jin, jout, n);
-    cur ^= 1;
+  // the range-minimum structure over val0
+  RmqArgs r{};
+  for (int j = 0; j < h.rmq_levels; j++) {
+    r.val[j] = h.rmq_val[j];
+    r.mask[j] = h.rmq_mask[j];
+    r.size[j] = h.rmq_size[j];
   }
+  r.levels = h.rmq_levels;
+  r.done = h.ts_done + 1;
+  ++h.launches;
+  k_rmq_build<<<(int)((h.rmq_size[0] + kRmqChunk - 1) / kRmqChunk), kRmqThreads, 0, h.stream>>>(r);
   PDG_CUDA(cudaGetLastError());
-  h.p_final = cur;
+  return PDG_OK;
+}
+
+// the tree-scan work space for a tour of A arcs (tile sums, two block counters)
+int tree_scan_workspace(Handle& h) {
+  const int64_t tiles = std::max<int64_t>((h.A + kTsTile - 1) / kTsTile, 1);
+  int st;
+  if ((st = device_alloc(h, (void**)&h.ts_sum, sizeof(u128) * (size_t)tiles)) ||
+      (st = device_alloc(h, (void**)&h.ts_done, sizeof(uint32_t) * 2)))
+    return st;
+  PDG_CUDA(cudaMemsetAsync(h.ts_done, 0, sizeof(uint32_t) * 2, h.stream));
   return PDG_OK;
 }
 
