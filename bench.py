@@ -28,6 +28,37 @@ sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "Off-tree edges/s in recovery"
+# The oracle's bounded sample of the headline workload: the same mesh 128^3 inputs and c, with the budget cut to
+# k = floor(0.02 n) -- exactly the first 41,943 edges of the alpha = 0.10 output, since the greedy decides every
+# edge from earlier edges only.  The oracle still scores, orders and groups all off-tree edges; only the greedy
+# stops earlier (a full alpha = 0.10 run takes 30-40 s on one core, too long for K timed steps).
+ORACLE_SAMPLE_ALPHA = 0.02
+
+
+def host_cpu() -> dict:
+    """Model name and logical core count of the host (read-only)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    import platform
+
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
 
 
 def log(*a):
@@ -184,14 +215,16 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- algorithmic bytes
 
-def step_bytes(n, nnz, E, J, R, k):
+def step_bytes(n, nnz, E, G, R, k):
     """Compulsory DRAM bytes of each step of the GPU pipeline (each stream
     once, gathers at element size), per recovery."""
+    A = 2 * (n - G)  # Euler-tour arcs
     return {
-        # stream the canonical edge list (u, v: 4 B, w: 8 B), read parent, write r(v) and the off-tree SoA
+        # stream the canonical edge list (u, v: 4 B, w: 8 B), gather parent, write r(v) and the off-tree SoA
         "classify": 16 * (nnz // 2) + 4 * n + 8 * n + 20 * E,
-        # read parent + r; per pointer-jumping round read P,jump (20 B), gather P,jump (20 B), write (20 B)
-        "tree": 12 * n + 16 * n + J * 60 * n,
+        # two passes over the tour (arc 4 B + r gather 8 B); write P (16 B) and the range-minimum key (8 B),
+        # read parent (4 B); the range-minimum build reads the keys (8 B) and writes the masks (4 B)
+        "tree": 2 * 12 * A + 28 * n + 12 * n,
         # read (u, v, w) 16 B, gather P(u), P(v), P(LCA) 48 B, write key + lca 12 B
         "score": 76 * E,
         # two histogram passes + one compaction pass over the keys, write candidates (idx, key, val)
@@ -239,6 +272,38 @@ def ncu_traffic(kernel: str, workload: str):
         return None
 
 
+def sources_digest() -> str:
+    """sha256 over the CUDA sources of the library (file names and contents, sorted)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2508_20403_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_recovery_traffic(workload: str):
+    """DRAM bytes (read + write) of all kernels of one recovery, from the committed ncu summary, if it was
+    taken on the CUDA sources as they are now (else None)."""
+    path = os.path.join(ROOT, "profiles", f"recovery_traffic_{workload}.md")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("- ") and ": " in line:
+                    key, val = line[2:].split(": ", 1)
+                    fields[key.strip()] = val.strip().strip("`")
+        if fields.get("sources sha256") != sources_digest():
+            return None
+        return float(fields["dram bytes per recovery"])
+    except Exception:
+        return None
+
+
 def max_over_ranks(ms: float, world: int, device=None) -> float:
     """The slowest rank's time (all ranks call this; one all-reduce)."""
     if world <= 1:
@@ -256,7 +321,63 @@ def whole_job_value(world: int, units_per_rank: int, t_max_ms: float) -> float:
     return world * units_per_rank / (t_max_ms / 1e3)
 
 
-def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None):
+def time_recoveries(sp, alpha, c, steps, warmup, flush, stream, out_ids, out_sc):
+    """CUDA-event times (ms) of `steps` recoveries after `warmup` untimed ones; L2 is flushed before each."""
+    import torch
+
+    for _ in range(warmup):
+        sp.recover(alpha, c, out_ids=out_ids, out_scores=out_sc)
+    torch.cuda.synchronize()
+    times, launches = [], []
+    for i in range(steps):
+        flush.fill_(i & 0xff)  # evict L2 between steps (outside the timed interval)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sp.recover(alpha, c, out_ids=out_ids, out_scores=out_sc)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        launches.append(sp.last_stats()["launches"])
+    return times, launches
+
+
+def step_list(avg, bytes_, peak):
+    """Per-step rows {step, ms, model bytes, GB/s, fraction of the peak}, in pipeline order."""
+    rows = []
+    for nm in ("classify", "tree", "score", "select", "sort", "accept", "budget"):
+        gbs = bytes_[nm] / (avg[nm] / 1e3) / 1e9 if avg[nm] > 0 else None
+        rows.append({"step": nm, "ms": round(avg[nm], 4), "model_bytes": int(bytes_[nm]),
+                     "gbs": None if gbs is None else round(gbs, 1),
+                     "frac": None if gbs is None else round(gbs / peak, 4)})
+    return rows
+
+
+def config_leg(args, g, dev, B, AT, torch, flush, stream, alphas, steps, label):
+    """Extra configurations: min and median ms per recovery, edges/s and the path roofline fraction."""
+    peak, _ = measured_peaks()
+    opt = AT.options_for(g, use_graph=1)
+    rows = []
+    with B.Sparsifier.from_graph(g, device=True, options=opt, stream=stream) as sp:
+        info = sp.info()
+        for alpha in alphas:
+            k = int(math.floor(alpha * g.n))
+            out_ids = torch.zeros(max(k, 1), dtype=torch.int32, device=dev)
+            out_sc = torch.zeros(max(k, 1), dtype=torch.float64, device=dev)
+            times, _ = time_recoveries(sp, alpha, args.c, steps, 3, flush, stream, out_ids, out_sc)
+            st = sp.last_stats()
+            b_alg = path_bytes(info["n"], info["m"], info["n_offtree"], k)
+            t_med = float(np.median(times))
+            rows.append({"workload": label, "n": info["n"], "m": info["m"], "n_offtree": info["n_offtree"],
+                         "alpha": alpha, "c": args.c, "k": k, "steps": steps, "min_ms": float(np.min(times)),
+                         "median_ms": t_med, "edges_per_s": info["n_offtree"] / (t_med / 1e3),
+                         "path_frac": b_alg / (t_med / 1e3) / 1e9 / peak, "algorithmic_bytes": b_alg,
+                         "candidates": st["candidates"], "max_subtask": st["max_subtask"],
+                         "launch_shape": {kk: getattr(opt, kk) for kk in AT.SPACE}})
+    return rows
+
+
+def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None, extra_graphs=None):
     import torch
 
     from paper_2508_20403_gb300 import binding as B, build as BLD, workloads as W
@@ -270,7 +391,7 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     t0 = time.time()
-    g = W.mesh3d_graph(128)
+    g = W.mesh3d_graph(MESH_SIDE)
     log(f"[rank {rank}] generated {g.name} n={g.n} m={g.m} E_off={g.n_offtree} in {time.time() - t0:.1f}s")
     k = int(math.floor(args.alpha * g.n))
     # timed handle: the recovery is captured once and replayed as a CUDA graph
@@ -278,84 +399,100 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
     from paper_2508_20403_gb300 import autotune as AT
 
     opt = AT.options_for(g, use_graph=0 if args.no_graph else 1)
-    tuned = {k: getattr(opt, k) for k in AT.SPACE}
-    sp = B.Sparsifier.from_graph(g, device=True, options=opt, stream=stream)
+    tuned = {kk: getattr(opt, kk) for kk in AT.SPACE}
+    dev_inputs = [torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+                  for a, dt in ((g.row_ptr, torch.int64), (g.col, torch.int32), (g.w, torch.float64),
+                                (g.parent, torch.int32))]
+    # sparsify_init from device-resident inputs (upload of the graph excluded): validation, the resident
+    # canonical edge list and the tree layout
+    init_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t_init = time.perf_counter()
+        sp = B.Sparsifier(g.n, *dev_inputs, options=opt, stream=stream)
+        torch.cuda.synchronize()
+        init_ms.append((time.perf_counter() - t_init) * 1e3)
+        sp.close()
+    sp = B.Sparsifier(g.n, *dev_inputs, options=opt, stream=stream)
     info = sp.info()
     out_ids = torch.zeros(max(k, 1), dtype=torch.int32, device=dev)
     out_sc = torch.zeros(max(k, 1), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    def one():
-        return sp.recover(args.alpha, args.c, out_ids=out_ids, out_scores=out_sc)
-
-    for _ in range(args.warmup):
-        one()
-    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    times, step_ms, launches = [], [], []
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
-        for i in range(args.steps):
-            flush.fill_(i & 0xff)  # evict L2 between steps (outside the timed interval)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st, ids, sc, cnt = one()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            launches.append(sp.last_stats()["launches"])
+        times, launches = time_recoveries(sp, args.alpha, args.c, args.steps, args.warmup, flush, stream, out_ids,
+                                          out_sc)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     stats = sp.last_stats()
     sp.close()
     # per-step breakdown: a second handle, launched step by step with CUDA events
-    sp = B.Sparsifier.from_graph(g, device=True, options=AT.options_for(g, profile=1), stream=stream)
+    step_ms = []
+    sp = B.Sparsifier(g.n, *dev_inputs, options=AT.options_for(g, profile=1), stream=stream)
     for i in range(args.warmup + args.steps):
         flush.fill_(i & 0xff)
-        one()
+        sp.recover(args.alpha, args.c, out_ids=out_ids, out_scores=out_sc)
         if i >= args.warmup:
             step_ms.append(sp.last_timings())
+    sp.close()
     mean_ms = float(np.mean(times))
     t_max = max_over_ranks(mean_ms, world, dev)
     value = whole_job_value(world, info["n_offtree"], t_max)
-    # per-step breakdown and the roofline of the dominant kernel
     names = ["classify", "tree", "score", "select", "sort", "accept", "budget"]
-    avg = {nm: float(np.mean([s[nm] for s in step_ms])) for nm in names}
-    J = 0
-    while (1 << J) <= info["max_depth"]:
-        J += 1
+    avg = {nm: float(np.mean([s_[nm] for s_ in step_ms])) for nm in names}
     nnz = 2 * info["m"]
-    bytes_ = step_bytes(info["n"], nnz, info["n_offtree"], J, stats["candidates"], k)
+    bytes_ = step_bytes(info["n"], nnz, info["n_offtree"], info["num_graphs"], stats["candidates"], k)
     peak, peak_kind = measured_peaks()
+    b_alg = path_bytes(info["n"], info["m"], info["n_offtree"], k)
+    achieved = b_alg / (t_max / 1e3) / 1e9
+    steps_rows = step_list(avg, bytes_, peak)
+    top = max(steps_rows, key=lambda r: r["ms"])
     dom_bytes = SCORE_BYTES_PER_EDGE * info["n_offtree"]
     dom_ms = avg["score"]  # the events around step A3 bracket exactly one launch of k_score
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    traffic = ncu_traffic(DOMINANT_KERNEL, "mesh128_a010")
-    b_alg = path_bytes(info["n"], info["m"], info["n_offtree"], k)
     result = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": headline_config(args, world, info["n"], info["m"], info["n_offtree"], info["max_depth"]),
+        "config": headline_config(args, world),
         "min_ms": float(np.min(times)), "median_ms": float(np.median(times)),
+        "init_ms": {"median": float(np.median(init_ms)), "runs": [round(x, 3) for x in init_ms],
+                    "includes": "sparsify_init from device-resident CSR and parent: validation, canonical edge "
+                                "list, tree layout (Euler tour, preorder labels)"},
+        "tree_max_depth": info["max_depth"],
         "step_ms": {nm: round(avg[nm], 4) for nm in names},
         "recovery_stats": stats,
         "launch_shape": dict(tuned, source="autotune cache" if AT.lookup(AT.load_cache(), AT.device_key(),
                                                                           AT.class_of(g)) else "defaults"),
-        "roofline": {"bound": "hbm", "kernel": DOMINANT_KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "algorithmic_bytes": dom_bytes, "duration_ms": dom_ms},
-        "path_roofline": {"algorithmic_bytes": b_alg, "achieved_gbs": b_alg / (t_max / 1e3) / 1e9,
-                          "frac": b_alg / (t_max / 1e3) / 1e9 / peak,
-                          "step_bytes": bytes_, "step_gbs": {nm: round(bytes_[nm] / (avg[nm] / 1e3) / 1e9, 1)
-                                                             for nm in names}},
+        # The roofline of the whole recovery (steps A1-A7 in one CUDA-graph replay) against the method's
+        # compulsory traffic; the per-step rows and the longest single kernel explain it.
+        "roofline": {"bound": "hbm", "kernel": "recovery A1-A7 (one CUDA-graph replay)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_recovery_traffic("mesh128_a010"), "peak_source": peak_kind,
+                     "algorithmic_bytes": b_alg, "duration_ms": t_max,
+                     "steps": steps_rows, "top_step": top["step"],
+                     "longest_kernel": {"kernel": DOMINANT_KERNEL, "algorithmic_bytes": dom_bytes,
+                                        "duration_ms": dom_ms,
+                                        "achieved": dom_bytes / (dom_ms / 1e3) / 1e9,
+                                        "frac": dom_bytes / (dom_ms / 1e3) / 1e9 / peak,
+                                        "traffic": ncu_traffic(DOMINANT_KERNEL, "mesh128_a010")}},
         "gpu_launches": int(np.sum(launches)),
         "gpu_launches_per_step": int(np.mean(launches)),
     }
-    sp.close()
+    if rank == 0 and not args.no_configs:
+        t0 = time.time()
+        rows = config_leg(args, g, dev, B, AT, torch, flush, stream, (0.02, 0.05), min(args.steps, 10),
+                          WORKLOAD)
+        rows += config_leg(args, W.grid_graph(100), dev, B, AT, torch, flush, stream, (0.02,), min(args.steps, 10),
+                           "grid100 (2D grid 100x100, w U[1,10], max-weight spanning tree)")
+        if extra_graphs is not None and "rmat22" in extra_graphs:
+            rows += config_leg(args, extra_graphs["rmat22"], dev, B, AT, torch, flush, stream, (0.02, 0.05, 0.10),
+                               min(args.steps, 10),
+                               "rmat22 (R-MAT scale 22, a=.57 b=c=.19, ef 16, LCC, w U(0,1], max-weight tree)")
+        result["configs"] = rows
+        log(f"[rank {rank}] config leg {time.time() - t0:.1f}s")
     del flush
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e_leg(args, g, dev, B, torch)
@@ -372,7 +509,7 @@ def run_ours(args, rank, world, local_rank, batch_graphs=None, serve_graphs=None
         result["serve"] = serve_leg(args, serve_graphs, dev, torch)
         log(f"[rank {rank}] serve leg {time.time() - t0:.1f}s")
     if rank == 0 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_leg(args)
+        result["cpu_baseline"] = cpu_leg(args, g)
     result["clocks"] = clk.summary()
     return result
 
@@ -504,16 +641,10 @@ def e2e_leg(args, g, dev, B, torch):
             "includes": "sparsify_init (upload + validation) + recover_offtree + D2H + sparsifier_free"}
 
 
-def cpu_sample_graph():
-    from paper_2508_20403_gb300 import workloads as W
-
-    return W.mesh3d_graph(64, seed=W.SEED_BASE + 1)
-
-
 def tree_leg(args, g, dev, B, torch):
     """Spanning-tree generation (pdg_spanning_tree) on the headline mesh, device CSR in and device parent out,
     both trees; the maximum-weight tree must equal the workload's own (scipy) tree.  The oracle's Kruskal is
-    timed on the 64^3 sample."""
+    timed on the same mesh."""
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     rp, col, w = t(g.row_ptr, torch.int64), t(g.col, torch.int32), t(g.w, torch.float64)
     out = torch.zeros(g.n, dtype=torch.int32, device=dev)
@@ -536,13 +667,13 @@ def tree_leg(args, g, dev, B, torch):
     if not args.no_cpu:
         from oracle import oracle as O
 
-        gs = cpu_sample_graph()
         for name, kind in (("max_weight", O.TREE_MAX_WEIGHT), ("fegrass_weff", O.TREE_FEGRASS)):
             t0 = time.perf_counter()
-            O.spanning_tree(gs, kind)
+            O.spanning_tree(g, kind)
             dt = time.perf_counter() - t0
-            res[name]["cpu_oracle"] = {"value": gs.m / dt, "unit": "edges/s", "cores": 1,
-                                       "sample": f"mesh 64^3 (m={gs.m}), single-threaded C Kruskal, {dt:.2f} s"}
+            res[name]["cpu_oracle"] = {"value": g.m / dt, "unit": "edges/s", "cores": 1,
+                                       "sample": f"the same mesh {MESH_SIDE}^3 (m={g.m}), single-threaded C "
+                                                 f"Kruskal, {dt:.2f} s"}
     return res
 
 
@@ -575,55 +706,59 @@ def pcg_leg(args, B):
             "tol": 1e-3, "rows": rows}
 
 
-def cpu_leg(args, g=None, repeats=1):
-    """The oracle as it stands, single thread, on a bounded sample of the same
-    workload family: the 64^3 mesh with the same weight law, alpha and c."""
+def oracle_sample_recovery(g, args):
+    """One step of the oracle's bounded sample (see ORACLE_SAMPLE_ALPHA); returns seconds."""
+    from oracle import oracle as O
+
+    t0 = time.perf_counter()
+    O.recover(g, ORACLE_SAMPLE_ALPHA, c=args.c)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_text(g, args) -> str:
+    ks = int(math.floor(ORACLE_SAMPLE_ALPHA * g.n))
+    return (f"one oracle recovery per step on the same mesh {MESH_SIDE}^3 inputs (E_off={g.n_offtree}) and c={args.c} "
+            f"with the budget cut to k={ks} (alpha={ORACLE_SAMPLE_ALPHA}): the first {ks} edges of the "
+            f"alpha={args.alpha} output (the greedy decides each edge from earlier edges only); all off-tree edges "
+            f"are still scored, ordered and grouped; value = E_off / seconds; single-threaded C oracle")
+
+
+def cpu_leg(args, g):
+    """The oracle as it stands, single thread, on the bounded sample of the headline workload."""
     from oracle import oracle as O
 
     O.build()
-    g = g or cpu_sample_graph()
-    ts = []
-    for _ in range(repeats):
-        t0 = time.perf_counter()
-        O.recover(g, args.alpha, c=args.c)
-        ts.append(time.perf_counter() - t0)
-    t = float(np.mean(ts))
-    return {"value": g.n_offtree / t, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"mesh 64^3 (n={g.n}, E_off={g.n_offtree}), same weight law, alpha={args.alpha}, c={args.c}; "
-                      f"single-threaded C oracle, {t:.2f} s per recovery"}
+    t = oracle_sample_recovery(g, args)
+    return {"value": g.n_offtree / t, "unit": "edges/s", "cores": 1, "kind": "oracle", "seconds": t,
+            "sample": oracle_sample_text(g, args), "host": host_cpu()}
 
 
 MESH_SIDE = 128
 WORKLOAD = "mesh128 (3D 7-point mesh 128^3, w log-uniform [1e-3,1e3], max-weight spanning tree)"
 
 
-def headline_config(args, world, n=None, m=None, n_off=None, max_depth=None):
-    s = MESH_SIDE
-    n = s ** 3 if n is None else n
-    m = 3 * s * s * (s - 1) if m is None else m
-    n_off = m - n + 1 if n_off is None else n_off
-    cfg = {"workload": WORKLOAD, "n": n, "m": m, "n_offtree": n_off, "alpha": args.alpha, "c": args.c,
-           "k": int(math.floor(args.alpha * n)), "parallelism": "replicas" if world > 1 else "1 GPU",
-           "l2": "256 MB buffer written between timed steps; inputs (175 MB) exceed L2"}
-    if max_depth is not None:
-        cfg["max_depth"] = max_depth
-    return cfg
+def headline_config(args, world):
+    s_ = MESH_SIDE
+    n = s_ ** 3
+    m = 3 * s_ * s_ * (s_ - 1)
+    return {"workload": WORKLOAD, "n": n, "m": m, "n_offtree": m - n + 1, "alpha": args.alpha, "c": args.c,
+            "k": int(math.floor(args.alpha * n)), "parallelism": "replicas" if world > 1 else "1 GPU",
+            "l2": "256 MB buffer written between timed steps; inputs (175 MB) exceed L2"}
 
 
 def run_reference(args, rank, world):
+    """The oracle on the headline inputs (mesh 128^3), each step the bounded sample described by
+    oracle_sample_text; rank 0 only."""
     if rank != 0:
         return None
-    g = cpu_sample_graph()
     from oracle import oracle as O
+    from paper_2508_20403_gb300 import workloads as W
 
+    g = W.mesh3d_graph(MESH_SIDE)
     O.build()
     for _ in range(args.warmup):
-        O.recover(g, args.alpha, c=args.c)
-    ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        O.recover(g, args.alpha, c=args.c)
-        ts.append(time.perf_counter() - t0)
+        oracle_sample_recovery(g, args)
+    ts = [oracle_sample_recovery(g, args) for _ in range(args.steps)]
     t = float(np.mean(ts))
     v = g.n_offtree / t
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": world,
@@ -631,8 +766,7 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": headline_config(args, world),
             "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step one recovery of mesh 64^3 (same weight law and tree rule, "
-                                       f"E_off={g.n_offtree}), single-threaded C oracle"},
+                             "sample": oracle_sample_text(g, args), "host": host_cpu()},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -649,6 +783,9 @@ def main():
     ap.add_argument("--no-tree", action="store_true", help="skip the spanning-tree generation leg")
     ap.add_argument("--no-pcg", action="store_true", help="skip the PCG sparsifier-quality leg")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the extra configurations (mesh alpha .02/.05, grid 100^2, R-MAT scale 22)")
+    ap.add_argument("--no-rmat", action="store_true", help="skip R-MAT scale 22 in the extra configurations")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=2000)
     ap.add_argument("--batch-alpha", type=float, default=0.05)
@@ -683,11 +820,18 @@ def main():
         t0 = time.time()
         serve_graphs = serve_pool(args, workers=min(16, os.cpu_count() or 1))
         log(f"[rank {rank}] generated {len(serve_graphs)} serving-pool graphs in {time.time() - t0:.1f}s")
+    extra_graphs = None
+    if not args.no_configs and not args.no_rmat and rank == 0:
+        from paper_2508_20403_gb300 import workloads as W
+
+        t0 = time.time()
+        extra_graphs = {"rmat22": W.rmat_graph(22, workers=min(16, os.cpu_count() or 1))}
+        log(f"[rank {rank}] generated R-MAT scale 22 in {time.time() - t0:.1f}s")
     if world > 1:
         import torch
 
         torch.distributed.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank, batch_graphs, serve_graphs)
+    res = run_ours(args, rank, world, local_rank, batch_graphs, serve_graphs, extra_graphs)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
