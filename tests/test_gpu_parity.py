@@ -289,15 +289,44 @@ def mesh128():
     return W.mesh3d_graph(128)
 
 
-def _compare_bench_path(B, g, alpha, c=2):
+def _stored_expectation(name, g, alpha):
+    """The oracle's stored result for a full-size benchmark graph (tests/golden/full_size_expect.json, written by
+    tests/golden/make_full_size_expect.py from the oracle), if the generator produced the same arrays here."""
+    import json
+    import os
+
+    from tests.golden.make_full_size_expect import OUT, graph_digest
+
+    if not name or not os.path.exists(OUT):
+        return None
+    with open(OUT) as f:
+        rec = json.load(f).get(name)
+    if not rec or repr(alpha) not in rec["alphas"] or rec["graph_sha256"] != graph_digest(g):
+        return None
+    return rec["alphas"][repr(alpha)]
+
+
+def _compare_bench_path(B, g, alpha, c=2, stored=None):
     """The benchmark's launch path: inputs resident in device memory, outputs
     written to device buffers, the recovery captured into a CUDA graph on the
-    first call and replayed on the second; both calls must equal the oracle."""
+    first call and replayed on the second; both calls must equal the oracle.
+    `stored` names a graph of the stored oracle results: when the arrays match,
+    the ids and scores are compared by their digests (the oracle's greedy takes
+    tens of minutes on R-MAT scale 22), else the oracle runs here."""
+    import hashlib
+
     import torch
 
+    from paper_2508_20403_gb300 import autotune as AT
+
     k = int(np.floor(alpha * g.n))
-    ost, oids, osc, _ = O.recover(g, alpha, c=c)
-    opt = B.default_options(use_graph=1)
+    exp = _stored_expectation(stored, g, alpha)
+    if exp is None:
+        ost, oids, osc, _ = O.recover(g, alpha, c=c)
+        under = ost == O.UNDER_BUDGET
+    else:
+        under = exp["status"] == O.UNDER_BUDGET
+    opt = AT.options_for(g, use_graph=1)  # the launch shape the benchmark uses for this graph class
     out_ids = torch.zeros(max(k, 1), dtype=torch.int32, device="cuda")
     out_sc = torch.zeros(max(k, 1), dtype=torch.float64, device="cuda")
     with B.Sparsifier.from_graph(g, device=True, options=opt) as sp:
@@ -305,18 +334,25 @@ def _compare_bench_path(B, g, alpha, c=2):
             out_ids.fill_(-1)
             out_sc.fill_(0.0)
             st, ids, sc, cnt = sp.recover(alpha, c, out_ids=out_ids, out_scores=out_sc)
-            assert (st == B.PDG_UNDER_BUDGET) == (ost == O.UNDER_BUDGET)
-            assert ids.cpu().numpy().tolist() == oids.tolist(), (g.name, alpha, c, sp.last_stats())
-            got = sc.cpu().numpy()
-            assert np.array_equal(got, osc)
-            np.testing.assert_allclose(got, osc, rtol=SCORE_RTOL, atol=0)
+            assert (st == B.PDG_UNDER_BUDGET) == under
+            got_ids = ids.cpu().numpy().astype("<i4")
+            got = sc.cpu().numpy().astype("<f8")
+            if exp is None:
+                assert got_ids.tolist() == oids.tolist(), (g.name, alpha, c, sp.last_stats())
+                assert np.array_equal(got, osc)
+                np.testing.assert_allclose(got, osc, rtol=SCORE_RTOL, atol=0)
+            else:
+                assert got_ids.size == exp["count"], (g.name, alpha, got_ids.size, exp["count"])
+                assert got_ids[:8].tolist() == exp["head"] and got_ids[-8:].tolist() == exp["tail"]
+                assert hashlib.sha256(got_ids.tobytes()).hexdigest() == exp["ids_sha256"], (g.name, alpha)
+                assert hashlib.sha256(got.tobytes()).hexdigest() == exp["scores_sha256"], (g.name, alpha)
         return sp.last_stats()
 
 
-@pytest.mark.parametrize("alpha", [0.02, 0.10])
+@pytest.mark.parametrize("alpha", [0.02, 0.05, 0.10])
 def test_mesh128_full_size(B, mesh128, alpha):
     """The benchmark's workload in the benchmark's launch configuration."""
-    stats = _compare_bench_path(B, mesh128, alpha)
+    stats = _compare_bench_path(B, mesh128, alpha, stored="mesh128")
     assert stats["coop_candidates"] > 0 and stats["max_subtask"] > 1000
 
 
@@ -327,11 +363,52 @@ def rmat22():
     return W.rmat_graph(22, workers=min(16, os.cpu_count() or 1))
 
 
-def test_rmat22_full_size(B, rmat22):
+@pytest.mark.parametrize("alpha", [0.02, 0.05, 0.10])
+def test_rmat22_full_size(B, rmat22, alpha):
     """R-MAT scale 22 (about 2.4M vertices, 64M edges after deduplication, one
     giant subtask at the hub root) at full size, bench launch path."""
-    stats = _compare_bench_path(B, rmat22, 0.02)
+    stats = _compare_bench_path(B, rmat22, alpha, stored="rmat22")
     assert stats["max_subtask"] > 10000
+
+
+@pytest.mark.parametrize("n,alpha", [(100_000, 0.05), (1_000_000, 0.10), (1_000_000, 0.02)])
+def test_delaunay_serving_graphs(B, n, alpha):
+    """The serving mix's Delaunay triangulations (n uniform points, weights U[1,10], maximum-weight tree) near
+    both ends of its size range, bench launch path."""
+    g = W.delaunay_graph(n, np.random.default_rng([W.SEED_BASE + 4, n]))
+    _compare_bench_path(B, g, alpha)
+
+
+def test_full_batch_sampled_against_oracle(B):
+    """The 2,000-graph batch of the batching benchmark, recovered in one call on the benchmark's launch path
+    (device buffers, CUDA-graph capture and replay); every 40th graph and the ten largest are checked against
+    the oracle one by one (ids in order and scores bit for bit), on both calls."""
+    import os
+    import torch
+
+    graphs = W.batch_graphs(2000, seed=W.SEED_BASE + 3, workers=min(16, os.cpu_count() or 1))
+    pk = W.pack_graphs(graphs)
+    alphas = np.full(len(graphs), 0.05)
+    largest = np.argsort([-g.n for g in graphs], kind="stable")[:10]
+    sample = sorted(set(range(0, len(graphs), 40)) | set(int(i) for i in largest))
+    expect = {i: O.recover(graphs[i], 0.05, c=2) for i in sample}
+    from paper_2508_20403_gb300 import autotune as AT
+
+    with B.BatchSparsifier.from_packed(pk, device=True, options=AT.options_for(pk, use_graph=1)) as bs:
+        op = bs.out_ptr_for(alphas)
+        out = torch.zeros(max(int(op[-1]), 1), dtype=torch.int32, device="cuda")
+        outs = torch.zeros(max(int(op[-1]), 1), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            out.fill_(-1)
+            st, _, ids, sc, counts, gst = bs.recover_batch(alphas, c=2, out_ptr=op, out_ids=out, out_scores=outs)
+            ids = ids.cpu().numpy() if hasattr(ids, "cpu") else np.asarray(ids)
+            sc = sc.cpu().numpy() if hasattr(sc, "cpu") else np.asarray(sc)
+            for i in sample:
+                ost, oids, osc, _ = expect[i]
+                got = ids[op[i]:op[i] + counts[i]]
+                assert got.tolist() == oids.tolist(), (i, graphs[i].name)
+                assert np.array_equal(sc[op[i]:op[i] + counts[i]], osc), i
+                assert (gst[i] == B.PDG_UNDER_BUDGET) == (ost == O.UNDER_BUDGET)
 
 
 def test_mesh48_cooperative_tier_only(B):
