@@ -71,7 +71,8 @@ typedef struct pdg_options {
   int32_t block_tier_max;   /* subtasks with warp_tier_max+1..block_tier_max candidates get one block each
                                (shared-memory marker table); 0 turns the block tier off; at most 896 */
   int32_t sort_tile_keys;   /* keys per tile of the radix-sort scatter: 2048, 3072 or 4096 (0: 3072) */
-  int32_t reserved;
+  int32_t sort_one_launch;  /* 1 (default): the ordering step runs as one cooperative launch whenever every
+                               tile of the candidates fits in one resident block; 0: one kernel per pass */
 } pdg_options;
 
 typedef struct pdg_sparsifier* pdg_handle; /* opaque, owned by the library */

@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
     _fields_ = [("score_mode", ctypes.c_int32), ("warp_tier_max", ctypes.c_int32), ("k_override", ctypes.c_int64),
                 ("candidate_factor", ctypes.c_double), ("max_rounds", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("profile", ctypes.c_int32), ("block_tier_max", ctypes.c_int32),
-                ("sort_tile_keys", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sort_tile_keys", ctypes.c_int32), ("sort_one_launch", ctypes.c_int32)]
 
 
 _lib = None

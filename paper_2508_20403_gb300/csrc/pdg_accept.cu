@@ -531,7 +531,14 @@ __global__ void __launch_bounds__(32) k_accept_block(const int32_t* __restrict__
 
 
 
-__device__ __forceinline__ uint64_t und_tag(int round) { return (uint64_t)(0xffffffffu - (uint32_t)round) << 32; }
+// Undecided entries carry a tag of (attempt, round) in their high word; later
+// attempts and rounds have smaller tags, so an atomicMin registration always
+// replaces an entry left by an earlier attempt, and a probe ignores entries
+// whose tag is not its own round's.  The buffers are filled with all-ones
+// when allocated and never need clearing.
+__device__ __forceinline__ uint64_t und_tag(uint32_t epoch, int round) {
+  return (uint64_t)(0xffffffffu - (epoch * 128u + (uint32_t)round)) << 32;
+}
 
 struct CoopArgs {
   RecArrays ra;
@@ -541,7 +548,8 @@ struct CoopArgs {
   int32_t* reg_slot;   // per position: pair slot of each registered (j, j'), 16 per position
   int32_t* pslot;      // per position: pair slot of each flagged probe (o, i, i'), 32 per position
   PairSlot* ptab;
-  ExactEnt* xtab;      // 16 entries (j * 4 + j') per flagged pair
+  ExactEnt* xtab;      // 16 entries (j * 4 + j') per flagged pair; their und field serves the even rounds
+  unsigned long long* xund1;  // the undecided ranks of the odd rounds, one per entry of xtab
   const uint64_t* cap;  // effective pair-table capacity (device)
   int64_t* n_flag;     // flagged pairs (exact blocks handed out)
   int64_t xcap;        // exact blocks available
@@ -754,10 +762,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_probe(CoopArgs a, DevScalars
       }
       if (atomicCAS(&a.ptab[slt].xidx, kNone, (uint32_t)xi) == kNone) {
         ExactEnt* e = a.xtab + xi * 16;
-        for (int w = 0; w < 16; w++) {
-          e[w].acc = kNone;
-          e[w].und = ~0ull;
-        }
+        for (int w = 0; w < 16; w++) e[w].acc = kNone;  // undecided entries need no clearing (tags)
         atomicOr(&a.flagbits[slt >> 5], 1u << (slt & 31));
       }
       xi++;
@@ -788,7 +793,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_probe(CoopArgs a, DevScalars
 // rounds and the finisher read directly.
 template <int C, bool FIRST>
 __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int b, int32_t rank, bool accepted,
-                                               uint64_t und_val, uint64_t cap) {
+                                               uint64_t und_val, uint64_t cap, int buf) {
   if (b == 0) return;  // never registered (matches only itself)
   constexpr int NP = (C + 1) * (C + 1);
   int32_t sl[NP];
@@ -827,9 +832,9 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
       continue;
     }
     const int j = t / (C + 1), jp = t % (C + 1);
-    ExactEnt* e = a.xtab + (int64_t)xi[t] * 16 + j * 4 + jp;
-    if (accepted) atomicMin(&e->acc, (uint32_t)rank);
-    else atomicMin(&e->und, (unsigned long long)und_val);
+    const int64_t ei = (int64_t)xi[t] * 16 + j * 4 + jp;
+    if (accepted) atomicMin(&a.xtab[ei].acc, (uint32_t)rank);
+    else atomicMin(buf ? &a.xund1[ei] : &a.xtab[ei].und, (unsigned long long)und_val);
   }
   if (bad) bounds_fail(a.dsc, (bad & 1u) ? 2 : (FIRST ? 3 : 4), 0, s);
 }
@@ -840,7 +845,7 @@ __device__ __forceinline__ void exact_register(const CoopArgs& a, int32_t s, int
 // flagged probe may read are loaded together.
 template <int C, bool WITH_UND, bool FIRST>
 __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const Rec& r, uint32_t pm, uint64_t tag,
-                                           int where, uint64_t cap) {
+                                           int where, uint64_t cap, int buf) {
   int res = 0;
   uint32_t xis[2][C + 1][C + 1];
   uint32_t bad = 0;  // failed range checks (1: pair slot, 2: exact block), reported once below
@@ -891,9 +896,10 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
 #pragma unroll
           for (int jp = 0; jp + ip <= C; jp++) {
             const int bb = min(min(j + h1, jp + h2), C);
-            ent[j][jp] = (i + j <= bb && ip + jp <= bb)
-                             ? __ldcg(reinterpret_cast<const ulonglong2*>(a.xtab + (int64_t)xi * 16 + j * 4 + jp))
-                             : make_ulonglong2(~0ull, ~0ull);
+            const int64_t ei = (int64_t)xi * 16 + j * 4 + jp;
+            ent[j][jp] = (i + j <= bb && ip + jp <= bb) ? __ldcg(reinterpret_cast<const ulonglong2*>(a.xtab + ei))
+                                                        : make_ulonglong2(~0ull, ~0ull);
+            if (WITH_UND && buf && i + j <= bb && ip + jp <= bb) ent[j][jp].y = __ldcg(a.xund1 + ei);
           }
 #pragma unroll
         for (int j = 0; j + i <= C; j++)
@@ -909,48 +915,45 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
   return res;
 }
 
+// Round 1 registrations: every cooperative candidate (the ones phase A
+// accepted as accepted markers, the undecided ones as undecided, in the odd
+// rounds' buffer); round 1 also replaces the saved pair slots by exact-block
+// indices.
 template <int C>
-__global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalars* dsc, int round) {
+__global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalars* dsc) {
   if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0) return;
-  if (round > 1 && a.und_count[round - 1] == 0) return;
-  // round 1 also registers the candidates phase A accepted; later rounds only
-  // touch the positions phase A left undecided
-  const int64_t nb = (round == 1) ? dsc->n_big : *a.n_und;
-  const int32_t* pos = (round == 1) ? a.big_pos : a.und_list;
+  const int64_t nb = dsc->n_big;
   const uint64_t cap = *a.cap;
-  const uint64_t tag = und_tag(round);
+  const uint64_t tag = und_tag(dsc->epoch, 1);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t s = pos[q];
+    const int32_t s = a.big_pos[q];
     const uint8_t st = a.state[s];
     if (st != ST_UNDECIDED && st != ST_ACCEPTED_NEW) continue;
     const int b = a.ra.b[s];
     const int32_t rank = a.ra.rank[s];
-    if (round == 1) {
-      if (st == ST_UNDECIDED) {
-        exact_register<C, true>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank, cap);
-      } else {
-        exact_register<C, true>(a, s, b, rank, true, 0, cap);
-        a.state[s] = ST_ACCEPTED;
-      }
+    if (st == ST_UNDECIDED) {
+      exact_register<C, true>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank, cap, 1);
     } else {
-      if (st == ST_UNDECIDED) {
-        exact_register<C, false>(a, s, b, rank, false, tag | (uint64_t)(uint32_t)rank, cap);
-      } else {
-        exact_register<C, false>(a, s, b, rank, true, 0, cap);
-        a.state[s] = ST_ACCEPTED;
-      }
+      exact_register<C, true>(a, s, b, rank, true, 0, cap, 1);
+      a.state[s] = ST_ACCEPTED;
     }
   }
 }
 
+// Round r (one launch): every undecided candidate probes the round-r entries
+// (undecided ranks in buffer r & 1) and then registers for round r + 1 at
+// once -- accepted ranks as final markers, still-undecided ranks in buffer
+// (r + 1) & 1, which no probe of round r reads.  A probe of round r may
+// already see markers accepted during round r; acceptance is final, so that
+// only settles the prober earlier.
 template <int C>
-__global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* dsc, int round) {
+__global__ void __launch_bounds__(kBlock) k_exact_round(CoopArgs a, DevScalars* dsc, int round) {
   if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
   const int64_t nb = *a.n_und;
-  const uint64_t tag = und_tag(round);
+  const uint64_t tag = und_tag(dsc->epoch, round), next_tag = und_tag(dsc->epoch, round + 1);
   const uint64_t cap = *a.cap;
   unsigned long long waiting = 0;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
@@ -958,11 +961,17 @@ __global__ void __launch_bounds__(kBlock) k_exact_probe(CoopArgs a, DevScalars* 
     if (a.state[s] != ST_UNDECIDED) continue;
     Rec r;
     load_rec(a.ra, s, C, r);
-    const int res = (round == 1) ? exact_probe<C, true, true>(a, s, r, a.pmask[s], tag, round, cap)
-                                 : exact_probe<C, true, false>(a, s, r, a.pmask[s], tag, round, cap);
-    if (res == 2) a.state[s] = ST_REJECTED;
-    else if (res == 0) a.state[s] = ST_ACCEPTED_NEW;
-    else waiting++;
+    const int res = (round == 1) ? exact_probe<C, true, true>(a, s, r, a.pmask[s], tag, round, cap, round & 1)
+                                 : exact_probe<C, true, false>(a, s, r, a.pmask[s], tag, round, cap, round & 1);
+    if (res == 2) {
+      a.state[s] = ST_REJECTED;
+    } else if (res == 0) {
+      exact_register<C, false>(a, s, r.b, r.rank, true, 0, cap, 0);
+      a.state[s] = ST_ACCEPTED;
+    } else {
+      waiting++;
+      exact_register<C, false>(a, s, r.b, r.rank, false, next_tag | (uint64_t)(uint32_t)r.rank, cap, (round + 1) & 1);
+    }
   }
   for (int o = 16; o; o >>= 1) waiting += __shfl_down_sync(0xffffffffu, waiting, o);
   if ((threadIdx.x & 31) == 0 && waiting) atomicAdd((unsigned long long*)&a.und_count[round], waiting);
@@ -984,11 +993,11 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
       if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
       Rec r;
       load_rec(a.ra, s, C, r);
-      if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0, 99, cap) == 2) {
+      if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0, 99, cap, 0) == 2) {
         a.state[s] = ST_REJECTED;
         continue;
       }
-      exact_register<C, false>(a, s, r.b, r.rank, true, 0, cap);
+      exact_register<C, false>(a, s, r.b, r.rank, true, 0, cap, 0);
       a.state[s] = ST_ACCEPTED;
     }
   }
@@ -1015,11 +1024,11 @@ int run_coop(Handle& h, const CoopArgs& a, int grid, int rounds) {
   // round 1 registers every cooperative candidate; the rest of the rounds only
   // walk the (shorter) list of candidates phase A left undecided
   const int grid_und = std::max(1, h.num_sms * 2);
+  ++h.launches;
+  k_exact_register<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
   for (int r = 1; r <= rounds; r++) {
     ++h.launches;
-    k_exact_register<C><<<r == 1 ? grid : grid_und, kBlock, 0, h.stream>>>(a, h.dsc, r);
-    ++h.launches;
-    k_exact_probe<C><<<grid_und, kBlock, 0, h.stream>>>(a, h.dsc, r);
+    k_exact_round<C><<<grid_und, kBlock, 0, h.stream>>>(a, h.dsc, r);
   }
   ++h.launches;
   k_exact_finish<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.big_seg, h.seg_begin, rounds);
@@ -1128,7 +1137,7 @@ static int accept_coop(Handle& h, int c, int grid, const RecArrays& ra) {
   ++h.launches;
   k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.flagbits, h.dsc, h.table_cap, d_cap, n_flag, n_und,
                                               h.seg_pref);
-  const CoopArgs a{ra,        h.big_pos, h.state,   h.pmask,    h.reg_slot, h.pslot, h.ptab, h.xtab,
+  const CoopArgs a{ra,        h.big_pos, h.state,   h.pmask,    h.reg_slot, h.pslot, h.ptab, h.xtab, h.xund1,
                    d_cap,     n_flag,    h.xcap,    und_count,  h.flagbits, h.und_list, n_und, h.pos_x,
                    h.seg_pref, h.dsc};
   switch (c) {

@@ -124,6 +124,7 @@ __global__ void k_reset_recover(DevScalars* dsc) {
 
 __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->err &= ERR_RANGE | ERR_TIMEOUT | ERR_BOUNDS;  // errors of steps A1-A3 end the recovery
+  dsc->epoch++;
   dsc->bounds_site = 0;
   dsc->rounds_used = 0;
   dsc->n_cand = 0;
@@ -237,11 +238,16 @@ int grow_tables(Handle& h, int64_t slots, int64_t xblocks) {
   xblocks = std::max<int64_t>(xblocks, std::max<int64_t>(64, h.table_cap / 16));
   if (xblocks > h.xcap) {
     device_release(h, h.xtab);
+    device_release(h, h.xund1);
     h.xtab = nullptr;
-    if ((st = alloc_n(h, &h.xtab, 16 * xblocks))) {
+    h.xund1 = nullptr;
+    if ((st = alloc_n(h, &h.xtab, 16 * xblocks)) || (st = alloc_n(h, &h.xund1, 16 * xblocks))) {
       h.xcap = 0;
       return st;
     }
+    // all-ones undecided entries: any registration replaces them (their tags stay above every real one)
+    PDG_CUDA(cudaMemsetAsync(h.xtab, 0xff, sizeof(ExactEnt) * 16 * (size_t)xblocks, h.stream));
+    PDG_CUDA(cudaMemsetAsync(h.xund1, 0xff, sizeof(unsigned long long) * 16 * (size_t)xblocks, h.stream));
     h.xcap = xblocks;
   }
   return PDG_OK;
@@ -281,7 +287,7 @@ void pdg_default_options(pdg_options* opt) {
   opt->profile = 0;
   opt->block_tier_max = kBlockTierDefault;
   opt->sort_tile_keys = 3072;
-  opt->reserved = 0;
+  opt->sort_one_launch = 1;
 }
 
 const char* pdg_status_string(int status) {
@@ -404,6 +410,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
   if (h.m >= (1ll << 31)) return fail(PDG_E_INVALID_ARG);
   if (!(h.hsc = static_cast<DevScalars*>(pinned_alloc(sizeof(DevScalars))))) return fail(PDG_E_OOM);
   if ((st = alloc_n(h, &h.dsc, 1))) return fail(st);
+  if (cudaMemsetAsync(h.dsc, 0, sizeof(DevScalars), h.stream) != cudaSuccess) return fail(PDG_E_CUDA);
   if ((st = alloc_n(h, &h.row_ptr, n + 1)) || (st = alloc_n(h, &h.col, h.nnz)) || (st = alloc_n(h, &h.w, h.nnz)) ||
       (st = alloc_n(h, &h.parent, n)) || (st = alloc_n(h, &h.d_vtx_ptr, num_graphs + 1)) ||
       (st = alloc_n(h, &h.blk_a, 10240)) || (st = alloc_n(h, &h.blk_b, 2048)))
@@ -759,8 +766,11 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
   float acc_ms[8] = {0};
   // Enqueue one attempt on h.stream: steps A1-A3 (first attempt only; they
   // do not depend on the prefix), then A4-A7 and the read-back of the status.
+  bool any_select_cur = false;
   auto enqueue = [&](bool first) -> int {
     int e;
+    // a single graph's first selection histogram is taken by the scoring kernel itself
+    h.fuse_hist = first && G == 1 && any_select_cur;
     if (first) {
       PDG_CUDA(cudaMemcpyAsync(h.d_k, s.k, sizeof(int64_t) * G, cudaMemcpyHostToDevice, h.stream));
       PDG_CUDA(cudaMemcpyAsync(h.d_out_ptr, s.out_ptr, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, h.stream));
@@ -795,6 +805,16 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
   bool first = true;
   for (;;) {
     if (++attempts > 40) return PDG_E_CUDA;
+    // every attempt advances the device epoch that tags the cooperative tier's undecided entries; long before
+    // the tags would wrap, the entries are refilled and the epoch restarts
+    if (++h.epochs >= (1u << 24)) {
+      if (h.xtab) {
+        PDG_CUDA(cudaMemsetAsync(h.xtab, 0xff, sizeof(ExactEnt) * 16 * (size_t)h.xcap, h.stream));
+        PDG_CUDA(cudaMemsetAsync(h.xund1, 0xff, sizeof(unsigned long long) * 16 * (size_t)h.xcap, h.stream));
+      }
+      PDG_CUDA(cudaMemsetAsync(&h.dsc->epoch, 0, sizeof(uint32_t), h.stream));
+      h.epochs = 1;
+    }
     int64_t need = 0;
     bool any_select = false;
     for (int32_t g = 0; g < G; g++) {
@@ -805,6 +825,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
       need += gs.take_all ? eoff[g] : h.want_h[g];
       if (!gs.take_all) any_select = true;
     }
+    any_select_cur = any_select;
     if ((st = ensure_candidates(h, std::max<int64_t>(h.Rcap, need + need / 4 + 4096), c))) return st;
     // the launch sequence a CUDA graph bakes in
     const GraphKey key{c, h.opt.score_mode, any_select ? 1 : 0, coop_rounds(h, c), h.Rcap, h.table_cap, h.xcap,

@@ -25,7 +25,8 @@ constexpr int kRadixPassesMax = 16; // 8 score digits + <= 4 graph digits + <= 4
 constexpr int kBlockTierSlots = 16384;
 constexpr int kBlockTierMax = 896;      // <= kBlockTierSlots / (2 * 9)
 constexpr int kBlockTierDefault = 0;  // off: on the mesh and R-MAT workloads the cooperative tier is faster
-constexpr int kRadixHistWords = 16 * 256 + 2 * kRadixPassesMax;  // + skip flags, buffer choices
+constexpr int kRadixHistOnesweep = 16 * 256 + 2 * kRadixPassesMax;  // per-pass sort: histograms, skip flags, buffers
+constexpr int kRadixHistWords = kRadixHistOnesweep + 3 * 8 * 256;     // + the one-launch sort's key-set histograms
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kRmqMaxLevels = 6;  // levels of the range-minimum structure (n < 2^30: 30 / 5)
 
@@ -82,6 +83,7 @@ struct DevScalars {
   int64_t n_constrained;  // cooperative tier: candidates with a possible earlier marker
   int64_t n_big_chunk;    // cooperative tier: chunks of at most kBigChunk positions
   unsigned long long score_ticket;  // step A3: next tile of off-tree edges to score
+  uint32_t epoch;       // attempts so far (tags the cooperative tier's undecided entries)
   int32_t bounds_site;  // first failed bounds check (see ERR_BOUNDS)
   int32_t bounds_where;  // its round (99: serial finisher)
   int64_t bounds_pos, bounds_val;  // its position and offending value
@@ -178,6 +180,8 @@ struct Handle {
   int64_t rmq_size[kRmqMaxLevels] = {0};
   uint64_t* rmq_val[kRmqMaxLevels] = {nullptr};
   uint32_t* rmq_mask[kRmqMaxLevels] = {nullptr};
+  uint64_t* rmq_pmin[kRmqMaxLevels] = {nullptr};  // per entry: minimum from its group's start (null: top level)
+  uint64_t* rmq_smin[kRmqMaxLevels] = {nullptr};  // per entry: minimum to its group's end
   u128* ts_sum = nullptr;        // tree scan: tile sums, then their prefixes
   uint32_t* ts_done = nullptr;   // blocks finished: [0] tree-scan tile sums, [1] range-minimum build
 
@@ -187,6 +191,7 @@ struct Handle {
 
   // selection
   uint32_t* hist = nullptr;  // G * kSelBins
+  bool fuse_hist = false;    // this attempt's first histogram level comes from step A3
   GraphSel* sel = nullptr;   // G
   std::vector<int64_t> want_h;  // requested prefix per graph
   // prefix that sufficed per graph in the last call, for the budget k_mem and
@@ -241,6 +246,8 @@ struct Handle {
   int64_t xcap = 0;
   PairSlot* ptab = nullptr;
   ExactEnt* xtab = nullptr;
+  unsigned long long* xund1 = nullptr;  // odd rounds' undecided ranks, one per exact entry
+  uint32_t epochs = 0;                  // attempts since the epoch last restarted (host count)
   uint32_t* pmask = nullptr;
   int32_t* reg_slot = nullptr;
   int32_t* pslot = nullptr;

@@ -181,6 +181,10 @@ int build_tree_layout(Handle& h) {
     if ((st = device_alloc(h, (void**)&h.rmq_val[h.rmq_levels], sizeof(uint64_t) * (size_t)sz)) ||
         (st = device_alloc(h, (void**)&h.rmq_mask[h.rmq_levels], sizeof(uint32_t) * (size_t)sz)))
       return st;
+    if (sz > 32 &&  // below the top level, queries read partial groups from these
+        ((st = device_alloc(h, (void**)&h.rmq_pmin[h.rmq_levels], sizeof(uint64_t) * (size_t)sz)) ||
+         (st = device_alloc(h, (void**)&h.rmq_smin[h.rmq_levels], sizeof(uint64_t) * (size_t)sz))))
+      return st;
     h.rmq_levels++;
     if (sz <= 32) break;
   }

@@ -35,59 +35,56 @@ struct ScoreArgs {
   const u128* P;
   const uint64_t* val[kRmqMaxLevels];
   const uint32_t* mask[kRmqMaxLevels];
+  const uint64_t* pmin[kRmqMaxLevels];
+  const uint64_t* smin[kRmqMaxLevels];
   int S;
   int score_mode;
   uint32_t n;
   int* err;
   uint64_t* key;
   int32_t* lca;
+  uint32_t* hist;  // nullable: the first-level selection histogram (key >> 52) of a single graph
 };
 
 // minimum of val0 over the labels [lo, hi] (lo <= hi), by depth.  Level j
-// holds the query range [a_j, b_j]; it is answered there if both ends share a
-// group, else the tail of a_j's group and the head of b_j's group are read and
-// the groups strictly between become the range of level j + 1.
+// holds the query range [a_j, b_j].  If both ends share a group the range is
+// answered there by its mask and one key; otherwise the tail of a_j's group
+// (smin) and the head of b_j's group (pmin) are single loads, and the groups
+// strictly between become the range of level j + 1.  Every address depends
+// only on (lo, hi), so all loads but the last key are issued together.
 __device__ __forceinline__ uint64_t range_min(const ScoreArgs& A, uint32_t lo, uint32_t hi) {
-  uint32_t a[kRmqMaxLevels], b[kRmqMaxLevels];
-  int nlev = kRmqMaxLevels;  // levels holding a query
-  bool single = false;       // the last of them is one group
+  uint64_t best = ~0ull;
+  bool done = false;
+  uint32_t fa = 0, fb = 0;  // the single-group range of the last level, if any
+  int fj = -1;
 #pragma unroll
   for (int j = 0; j < kRmqMaxLevels; j++) {
-    a[j] = lo;
-    b[j] = hi;
-    if (j < nlev) {
+    if (!done) {
       if ((lo >> 5) == (hi >> 5)) {
-        nlev = j + 1;
-        single = true;
+        fa = lo;
+        fb = hi;
+        fj = j;
+        done = true;
       } else {
+        best = min(best, min(__ldg(A.smin[j] + lo), __ldg(A.pmin[j] + hi)));
         lo = (lo >> 5) + 1;
         hi = (hi >> 5) - 1;
-        if (lo > hi) nlev = j + 1;
+        done = lo > hi;
       }
     }
   }
-  uint32_t m0[kRmqMaxLevels], m1[kRmqMaxLevels];
 #pragma unroll
   for (int j = 0; j < kRmqMaxLevels; j++) {
-    const bool one = single && j == nlev - 1;
-    m0[j] = (j < nlev) ? __ldg(A.mask[j] + (one ? b[j] : (a[j] | 31u))) : 0u;
-    m1[j] = (j < nlev && !one) ? __ldg(A.mask[j] + b[j]) : 0u;
-  }
-  uint64_t best = ~0ull;
-#pragma unroll
-  for (int j = 0; j < kRmqMaxLevels; j++) {
-    if (j < nlev) {
-      const bool one = single && j == nlev - 1;
-      const uint32_t o = a[j] & 31u;
-      const uint32_t g0 = (one ? b[j] : a[j]) & ~31u;
-      best = min(best, __ldg(A.val[j] + (g0 | (o + __ffs(m0[j] >> o) - 1))));
-      if (!one) best = min(best, __ldg(A.val[j] + ((b[j] & ~31u) | (__ffs(m1[j]) - 1))));
+    if (j == fj) {
+      const uint32_t m = __ldg(A.mask[j] + fb);
+      const uint32_t o = fa & 31u;
+      best = min(best, __ldg(A.val[j] + ((fb & ~31u) | (o + __ffs(m >> o) - 1))));
     }
   }
   return best;
 }
 
-__device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i) {
+__device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i, uint32_t* s_hist) {
   const int32_t u = A.ou[i], v = A.ov[i];  // preorder labels, u < v
   const u128 Pu = A.P[u], Pv = A.P[v];
   const uint64_t mn = range_min(A, (uint32_t)u + 1, (uint32_t)v);
@@ -108,6 +105,7 @@ __device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i) {
   }
   A.key[i] = sb;
   A.lca[i] = l;
+  if (s_hist) atomicAdd(&s_hist[sb >> 52], 1u);
 }
 
 // Long edge lists (a big packed batch) are scored in tiles of kScoreTile
@@ -118,21 +116,32 @@ __device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i) {
 constexpr int64_t kTicketMinEdges = 1ll << 24;
 
 __global__ void __launch_bounds__(kBlock) k_score(ScoreArgs A, int64_t E, DevScalars* __restrict__ dsc) {
+  __shared__ uint32_t s_hist[kSelBins];
+  uint32_t* sh = A.hist ? s_hist : nullptr;  // uniform over the grid
+  if (sh) {
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+  }
   A.S = 52 - dsc->e_min;
   if (E < kTicketMinEdges) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x)
-      score_edge(A, i);
-    return;
+      score_edge(A, i, sh);
+  } else {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      unsigned long long tk = 0;
+      if (lane == 0) tk = atomicAdd(&dsc->score_ticket, 1ull);
+      tk = __shfl_sync(0xffffffffu, tk, 0);
+      const int64_t i0 = (int64_t)tk * kScoreTile;
+      if (i0 >= E) break;
+      const int64_t i1 = min(E, i0 + kScoreTile);
+      for (int64_t i = i0 + lane; i < i1; i += 32) score_edge(A, i, sh);
+    }
   }
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long tk = 0;
-    if (lane == 0) tk = atomicAdd(&dsc->score_ticket, 1ull);
-    tk = __shfl_sync(0xffffffffu, tk, 0);
-    const int64_t i0 = (int64_t)tk * kScoreTile;
-    if (i0 >= E) break;
-    const int64_t i1 = min(E, i0 + kScoreTile);
-    for (int64_t i = i0 + lane; i < i1; i += 32) score_edge(A, i);
+  if (sh) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x)
+      if (sh[i]) atomicAdd(&A.hist[i], sh[i]);
   }
 }
 
@@ -147,14 +156,18 @@ int step_score(Handle& h, int score_mode) {
   A.ow = h.off_w;
   A.P = h.P;
   for (int j = 0; j < kRmqMaxLevels; j++) {
-    A.val[j] = h.rmq_val[j < h.rmq_levels ? j : h.rmq_levels - 1];
-    A.mask[j] = h.rmq_mask[j < h.rmq_levels ? j : h.rmq_levels - 1];
+    const int jj = j < h.rmq_levels ? j : h.rmq_levels - 1;
+    A.val[j] = h.rmq_val[jj];
+    A.mask[j] = h.rmq_mask[jj];
+    A.pmin[j] = h.rmq_pmin[jj];
+    A.smin[j] = h.rmq_smin[jj];
   }
   A.score_mode = score_mode;
   A.n = (uint32_t)h.n;
   A.err = &h.dsc->err;
   A.key = h.key;
   A.lca = h.lca;
+  A.hist = h.fuse_hist ? h.hist : nullptr;
   k_score<<<grid_for(h, h.E_off), kBlock, 0, h.stream>>>(A, h.E_off, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;

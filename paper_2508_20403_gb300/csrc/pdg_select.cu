@@ -254,7 +254,7 @@ int step_select(Handle& h) {
   for (int32_t g = 0; g < h.G; g++)
     if (h.want_h[g] < h.off_ptr_h[g + 1] - h.off_ptr_h[g]) any_select = true;
   for (int lvl = 0; lvl < 2; lvl++) {
-    if (any_select) {
+    if (any_select && !(lvl == 0 && h.fuse_hist)) {
       ++h.launches;
       k_sel_hist<<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, lvl, h.hist);
     }

@@ -21,6 +21,9 @@
 // recovery reports PDG_E_TIMEOUT instead of hanging.  A digit shared by all
 // keys is detected from the histogram and its pass moves nothing.  Sizes are
 // read on the device, so the sequence can be captured in a CUDA graph.
+#include <algorithm>
+#include <mutex>
+
 #include "pdg_internal.cuh"
 
 namespace pdg {
@@ -155,8 +158,8 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0
 #pragma unroll
       for (int i = 0; i < kOsItems; i++) {
         const int64_t idx = base + i * 32 + lane;
-        kk[i] = idx < N ? keys[idx] : 0;
-        vv[i] = idx < N ? vals[idx] : 0;
+        kk[i] = idx < N ? __ldcg(keys + idx) : 0;  // written by other blocks: bypass L1
+        vv[i] = idx < N ? __ldcg(vals + idx) : 0;
       }
 #pragma unroll
       for (int i = 0; i < kOsItems; i++) {
@@ -355,7 +358,342 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
   return PDG_OK;
 }
 
+namespace {
+
+// ---------------------------------------------------------------- one launch
+//
+// When every tile of the candidate keys fits in one co-resident block, the
+// whole of step A4b runs as ONE cooperative kernel: all passes of all three
+// key sets (score, graph index in a batch, LCA), the re-keying between them
+// and the final copy, with grid-wide barriers between the phases of a pass
+// instead of kernel boundaries and look-back chains.  A pass:
+//   rank   each block ranks its tile by the digit (stable: warp ballots and
+//          per-warp counters) and publishes the tile's 256 digit counts;
+//   scan   block b turns column b of the (tile x digit) count matrix into
+//          exclusive prefixes over the tiles;
+//   place  each block writes its keys to digit base + tile prefix + rank.
+// Digit bases and uniform (skipped) digits come from histograms of each key
+// set taken at its start.  Barriers count arrivals on one word (zeroed before
+// the launch); a wait that runs out sets ERR_TIMEOUT and the block goes on,
+// so the recovery reports the error instead of hanging.
+constexpr int kCoThreads = 512;
+constexpr int kCoItems = 6;
+constexpr int kCoTile = kCoThreads * kCoItems;
+constexpr int kCoWarps = kCoThreads / 32;
+constexpr int kCoKeySets = 3;
+
+struct CoopSortArgs {
+  uint64_t* k[2];
+  int32_t* v[2];
+  DevScalars* dsc;
+  const int32_t* cand_idx;
+  const int32_t* lca;
+  int32_t* rank_cand;
+  int32_t* lsort_rank;
+  const int64_t* cand_ptr;
+  int32_t G;
+  int nd_graph, nd_lca;
+  uint32_t* counts;  // [tiles][256]
+  uint32_t* totals;  // [kCoKeySets][kMaxDigits][256], zero at launch
+  uint32_t* bar;     // barrier arrivals, zero at launch
+  int64_t spin_limit;
+};
+
+struct CoopSmem {
+  uint64_t key[kCoTile];
+  int32_t val[kCoTile];
+  uint32_t wcnt[kCoWarps][kRdxBins];
+  uint32_t loff[kRdxBins];
+  uint32_t base[kRdxBins];
+  uint32_t wsum[32];
+  uint32_t bases[kMaxDigits][kRdxBins];  // exclusive digit bases of the current key set
+  int32_t uniform[kMaxDigits];
+};
+
+__device__ __forceinline__ void coop_barrier(const CoopSortArgs& a, uint32_t& target) {
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(a.bar, 1u);
+    volatile uint32_t* b = a.bar;
+    int64_t spins = 0;
+    while (*b < target && spins < a.spin_limit) spins++;
+    if (*b < target) atomicOr(&a.dsc->err, ERR_TIMEOUT);
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// one key set: histograms, then one rank / scan / place pass per non-uniform digit
+__device__ __forceinline__ void coop_keyset(const CoopSortArgs& a, CoopSmem& sm, int ks, int ndig, int& cur,
+                                            uint32_t& target,
+                            int64_t N, int64_t tiles) {
+  const int64_t t = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t t0 = t * kCoTile;
+  uint32_t* tot = a.totals + (int64_t)ks * kMaxDigits * kRdxBins;
+  // histograms of every digit of the key set (the order of the keys does not matter)
+  for (int i = threadIdx.x; i < ndig * kRdxBins; i += kCoThreads) (&sm.wcnt[0][0])[i] = 0;
+  __syncthreads();
+  if (t < tiles) {
+    const uint64_t* keys = a.k[cur];
+    for (int64_t i = t0 + threadIdx.x; i < N && i < t0 + kCoTile; i += kCoThreads) {
+      const uint64_t kk = __ldcg(keys + i);
+      for (int d = 0; d < ndig; d++) atomicAdd(&(&sm.wcnt[0][0])[d * kRdxBins + ((kk >> (8 * d)) & 0xff)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ndig * kRdxBins; i += kCoThreads) {
+      const uint32_t c = (&sm.wcnt[0][0])[i];
+      if (c) atomicAdd(&tot[i], c);
+    }
+  }
+  coop_barrier(a, target);
+  // digit bases (exclusive scans of the histograms) and uniform digits, in every block
+  for (int d = w; d < ndig; d += kCoWarps) {
+    uint32_t v[8], sum = 0;
+    bool uni = false;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      v[i] = __ldcg(&tot[d * kRdxBins + lane * 8 + i]);
+      sum += v[i];
+      if (v[i] == (uint32_t)N) uni = true;
+    }
+    const uint32_t incl = warp_incl_scan(sum);
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      sm.bases[d][lane * 8 + i] = run;
+      run += v[i];
+    }
+    uni = __any_sync(0xffffffffu, uni) || N == 0;
+    if (lane == 0) sm.uniform[d] = uni ? 1 : 0;
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1;
+  for (int d = 0; d < ndig; d++) {
+    if (sm.uniform[d]) continue;  // uniform over the grid: every block read the same totals
+    const int shift = 8 * d;
+    const uint64_t* keys = a.k[cur];
+    const int32_t* vals = a.v[cur];
+    uint64_t kk[kCoItems];
+    int32_t vv[kCoItems];
+    uint32_t rnk[kCoItems];
+    const int64_t base = t0 + (int64_t)w * (kCoTile / kCoWarps);
+    int tile_n = 0;
+    // rank: stable order inside the tile, digit counts of the tile
+    if (t < tiles) {
+      tile_n = (int)(N - t0 < kCoTile ? N - t0 : kCoTile);
+      for (int dd = lane; dd < kRdxBins; dd += 32) sm.wcnt[w][dd] = 0;
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < kCoItems; i++) {
+        const int64_t idx = base + i * 32 + lane;
+        kk[i] = idx < N ? __ldcg(keys + idx) : 0;  // written by other blocks: bypass L1
+        vv[i] = idx < N ? __ldcg(vals + idx) : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < kCoItems; i++) {
+        const bool valid = base + i * 32 + lane < N;
+        const int dig = (int)((kk[i] >> shift) & 0xff);
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+          const bool bit = (dig >> b) & 1;
+          const unsigned bb = __ballot_sync(0xffffffffu, bit);
+          peers &= bit ? bb : ~bb;
+        }
+        rnk[i] = valid ? sm.wcnt[w][dig] + __popc(peers & lt) : 0;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) sm.wcnt[w][dig] += __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      const int dg = threadIdx.x;
+      if (dg < kRdxBins) {
+        uint32_t run = 0;
+        for (int ww = 0; ww < kCoWarps; ww++) {
+          const uint32_t c = sm.wcnt[ww][dg];
+          sm.wcnt[ww][dg] = run;
+          run += c;
+        }
+        a.counts[t * kRdxBins + dg] = run;
+        const uint32_t incl = warp_incl_scan(run);
+        if (lane == 31) sm.wsum[w] = incl;
+        sm.base[dg] = run;  // the tile's count, kept for the local offsets below
+      }
+      __syncthreads();
+      if (dg < kRdxBins) {
+        uint32_t before = 0;
+        for (int ww = 0; ww < w; ww++) before += sm.wsum[ww];
+        const uint32_t incl = warp_incl_scan(sm.base[dg]);
+        sm.loff[dg] = before + incl - sm.base[dg];
+      }
+      __syncthreads();
+      // bucket the tile by digit in shared memory (stable: warp order, then rank)
+#pragma unroll
+      for (int i = 0; i < kCoItems; i++) {
+        if (base + i * 32 + lane < N) {
+          const int dig = (int)((kk[i] >> shift) & 0xff);
+          const uint32_t lp = sm.loff[dig] + sm.wcnt[w][dig] + rnk[i];
+          sm.key[lp] = kk[i];
+          sm.val[lp] = vv[i];
+        }
+      }
+    }
+    coop_barrier(a, target);
+    // the tile's prefix per digit: counts of the earlier tiles, summed by every block for itself
+    // (two threads per digit, each over half of the earlier tiles)
+    if (t < tiles) {
+      const int dg = threadIdx.x & (kRdxBins - 1), half = threadIdx.x >> 8;
+      const int64_t lo = half ? t / 2 : 0, hi = half ? t : t / 2;
+      uint32_t acc = 0;
+      int64_t tt = lo;
+      for (; tt + 4 <= hi; tt += 4) {
+        const uint32_t c0 = __ldcg(&a.counts[(tt + 0) * kRdxBins + dg]);
+        const uint32_t c1 = __ldcg(&a.counts[(tt + 1) * kRdxBins + dg]);
+        const uint32_t c2 = __ldcg(&a.counts[(tt + 2) * kRdxBins + dg]);
+        const uint32_t c3 = __ldcg(&a.counts[(tt + 3) * kRdxBins + dg]);
+        acc += c0 + c1 + c2 + c3;
+      }
+      for (; tt < hi; tt++) acc += __ldcg(&a.counts[tt * kRdxBins + dg]);
+      if (half) sm.base[dg] = acc;
+      __syncthreads();
+      if (!half) sm.base[dg] = sm.bases[d][dg] + acc + sm.base[dg] - sm.loff[dg];
+      __syncthreads();
+    }
+    // place: consecutive threads write consecutive slots of each digit's run
+    if (t < tiles) {
+      uint64_t* ko = a.k[cur ^ 1];
+      int32_t* vo = a.v[cur ^ 1];
+      for (int j = threadIdx.x; j < tile_n; j += kCoThreads) {
+        const uint64_t k = sm.key[j];
+        const uint32_t pos = sm.base[(k >> shift) & 0xff] + (uint32_t)j;
+        if (pos < (uint64_t)N) {
+          ko[pos] = k;
+          vo[pos] = sm.val[j];
+        }
+      }
+    }
+    cur ^= 1;
+    coop_barrier(a, target);
+  }
+}
+
+__global__ void __launch_bounds__(kCoThreads) k_sort_coop(CoopSortArgs a) {
+  extern __shared__ __align__(16) unsigned char co_smem[];
+  CoopSmem& sm = *reinterpret_cast<CoopSmem*>(co_smem);
+  if (attempt_aborted(a.dsc)) return;  // the attempt is void (uniform over the grid: set before the launch)
+  const int64_t N = a.dsc->n_cand;
+  const int64_t tiles = (N + kCoTile - 1) / kCoTile;
+  if (tiles > gridDim.x) {  // cannot happen: the host launches this path only when the capacity fits
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.dsc->err, ERR_CAPACITY);
+    return;
+  }
+  const int64_t t0 = (int64_t)blockIdx.x * kCoTile;
+  uint32_t target = 0;
+  int cur = a.dsc->radix_sel;
+  // 1. score descending (ties keep ascending id order)
+  coop_keyset(a, sm, 0, 8, cur, target, N, tiles);
+  // 2. in a batch, the graph index of each candidate (keeps graphs contiguous)
+  if (a.G > 1) {
+    if (blockIdx.x < tiles)
+      for (int64_t i = t0 + threadIdx.x; i < N && i < t0 + kCoTile; i += kCoThreads)
+        a.k[cur][i] = (uint64_t)part_of(a.cand_ptr, a.G, __ldcg(a.v[cur] + i));
+    __syncthreads();
+    coop_keyset(a, sm, 1, a.nd_graph, cur, target, N, tiles);
+  }
+  // 3. rank_cand[r] = candidate at rank r; keys := LCA, values := rank; group by LCA
+  if (blockIdx.x < tiles)
+    for (int64_t i = t0 + threadIdx.x; i < N && i < t0 + kCoTile; i += kCoThreads) {
+      const int32_t c = __ldcg(a.v[cur] + i);
+      a.rank_cand[i] = c;
+      a.k[cur][i] = (uint64_t)a.lca[a.cand_idx[c]];
+      a.v[cur][i] = (int32_t)i;
+    }
+  __syncthreads();
+  coop_keyset(a, sm, 2, a.nd_lca, cur, target, N, tiles);
+  if (blockIdx.x < tiles)
+    for (int64_t i = t0 + threadIdx.x; i < N && i < t0 + kCoTile; i += kCoThreads)
+      a.lsort_rank[i] = __ldcg(a.v[cur] + i);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.dsc->radix_sel = cur;
+}
+
+}  // namespace
+
+// blocks of the one-launch sort that fit on the device at once (0: not available)
+static int coop_sort_grid() {
+  static int grid = -1;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (grid >= 0) return grid;
+  grid = 0;
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return grid;
+  }
+  if (cudaFuncSetAttribute(k_sort_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CoopSmem)) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_coop, kCoThreads, sizeof(CoopSmem)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return grid;
+  }
+  grid = std::min(per_sm * sms, kCoThreads);  // the scan phase gives one thread to each tile
+  return grid;
+}
+
+static int step_sort_coop(Handle& h, int grid_max) {
+  // one block per tile of the candidate capacity: fewer arrivals per barrier than a full device
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_max, (h.Rcap + kCoTile - 1) / kCoTile));
+  // barrier word and the key-set histograms start at zero
+  PDG_CUDA(cudaMemsetAsync(h.radix_counters, 0, sizeof(uint32_t) * 2 * kRadixPassesMax, h.stream));
+  uint32_t* totals = h.radix_hist + kRadixHistOnesweep;  // beside the words the per-pass path keeps zero
+  PDG_CUDA(cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kCoKeySets * kMaxDigits * kRdxBins, h.stream));
+  CoopSortArgs a{};
+  a.k[0] = h.rk[0];
+  a.k[1] = h.rk[1];
+  a.v[0] = h.rv[0];
+  a.v[1] = h.rv[1];
+  a.dsc = h.dsc;
+  a.cand_idx = h.cand_idx;
+  a.lca = h.lca;
+  a.rank_cand = h.rank_cand;
+  a.lsort_rank = h.lsort_rank;
+  a.cand_ptr = h.d_cand_ptr;
+  a.G = h.G;
+  a.nd_graph = 0;
+  while ((1ll << (8 * a.nd_graph)) < h.G) a.nd_graph++;
+  a.nd_lca = 0;
+  while ((1ll << (8 * a.nd_lca)) < h.n) a.nd_lca++;
+  a.counts = h.radix_status;
+  a.totals = totals;
+  a.bar = h.radix_counters;
+  a.spin_limit = h.opt.spin_limit;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kCoThreads);
+  cfg.dynamicSmemBytes = sizeof(CoopSmem);
+  cfg.stream = h.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++h.launches;
+  PDG_CUDA(cudaLaunchKernelEx(&cfg, k_sort_coop, a));
+  return PDG_OK;
+}
+
 int step_sort(Handle& h) {
+  // one cooperative launch when every tile of the candidate capacity has its own resident block
+  const int cgrid = h.opt.sort_one_launch ? coop_sort_grid() : 0;
+  if (cgrid > 0 && (h.Rcap + kCoTile - 1) / kCoTile <= cgrid &&
+      kRadixHistOnesweep + (int64_t)kCoKeySets * kMaxDigits * kRdxBins <= kRadixHistWords &&
+      (int64_t)cgrid * kRdxBins <= (int64_t)kRadixPassesMax * 256 * ((h.Rcap + kTile - 1) / kTile))
+    return step_sort_coop(h, cgrid);
   const int grid = h.num_sms * 4;
   const int64_t tiles_max = sort_tiles(h);
   // look-back status and tile counters start clean for every pass

@@ -222,21 +222,34 @@ constexpr int kRmqChunk = kRmqThreads * 32;  // entries per block and pass
 struct RmqArgs {
   uint64_t* val[kRmqMaxLevels];
   uint32_t* mask[kRmqMaxLevels];
+  uint64_t* pmin[kRmqMaxLevels];
+  uint64_t* smin[kRmqMaxLevels];
   int64_t size[kRmqMaxLevels];
   int levels;
   uint32_t* done;  // blocks finished (the last one resets it)
 };
 
 // entries [base, base + len) of one level (len <= kRmqChunk, base a multiple
-// of 32): their masks, and the minimum of every group to val_next[entry / 32]
-// when val_next is given
+// of 32): their masks, the minima from the group start up to each entry
+// (pmin) and from each entry to the group end (smin), and the minimum of
+// every group to val_next[entry / 32] when val_next is given.  Both minima
+// come from the masks: the lowest set bit of mask[k] is the minimum of
+// [0, k], and the first set bit of mask[31] at or above k the minimum of
+// [k, 31] (padding past the level's end is deeper than any entry).
+// (FROM_PREV: the level was written by an earlier kernel, so its reads may use
+// the read-only cache; levels written by this kernel are read from L2)
+__device__ __forceinline__ uint64_t rmq_load(const uint64_t* p, bool from_prev) {
+  return from_prev ? __ldg(p) : __ldcg(p);
+}
+
 __device__ void rmq_chunk(const uint64_t* __restrict__ val, int64_t size, int64_t base, int len,
-                          uint32_t* __restrict__ mask, uint64_t* __restrict__ val_next, uint32_t (*s_d)[33]) {
+                          uint32_t* __restrict__ mask, uint64_t* __restrict__ pmin, uint64_t* __restrict__ smin,
+                          uint64_t* __restrict__ val_next, uint32_t (*s_d)[33], bool from_prev) {
   const int t = threadIdx.x;
   const int ngroups = (len + 31) / 32;
   for (int i = t; i < ngroups * 32; i += kRmqThreads) {
     const int64_t idx = base + i;
-    s_d[i >> 5][i & 31] = (i < len && idx < size) ? (uint32_t)(__ldcg(val + idx) >> 32) : 0xffffffffu;
+    s_d[i >> 5][i & 31] = (i < len && idx < size) ? (uint32_t)(rmq_load(val + idx, from_prev) >> 32) : 0xffffffffu;
   }
   __syncthreads();
   const bool walk = t < ngroups && base + 32 * t < size;
@@ -254,7 +267,7 @@ __device__ void rmq_chunk(const uint64_t* __restrict__ val, int64_t size, int64_
       stack |= 1u << k;
       m[k] = stack;
     }
-    if (val_next) val_next[(base >> 5) + t] = __ldcg(val + base + 32 * t + (__ffs(stack) - 1));
+    if (val_next) val_next[(base >> 5) + t] = rmq_load(val + base + 32 * t + (__ffs(stack) - 1), from_prev);
   }
   __syncthreads();  // every walk is done: the rows now take the masks
   if (walk) {
@@ -264,7 +277,15 @@ __device__ void rmq_chunk(const uint64_t* __restrict__ val, int64_t size, int64_
   __syncthreads();
   for (int i = t; i < len; i += kRmqThreads) {
     const int64_t idx = base + i;
-    if (idx < size) mask[idx] = s_d[i >> 5][i & 31];
+    if (idx >= size) continue;
+    const int g = i >> 5, k = i & 31;
+    const uint32_t mk = s_d[g][k];
+    mask[idx] = mk;
+    if (pmin) {
+      const int64_t g0 = base + 32 * g;
+      pmin[idx] = rmq_load(val + g0 + (__ffs(mk) - 1), from_prev);
+      smin[idx] = rmq_load(val + g0 + k + (__ffs(s_d[g][31] >> k) - 1), from_prev);
+    }
   }
   __syncthreads();
 }
@@ -273,9 +294,11 @@ __global__ void __launch_bounds__(kRmqThreads) k_rmq_build(RmqArgs a) {
   __shared__ uint32_t s_d[kRmqThreads][33];
   __shared__ int s_last;
   const int64_t b0 = (int64_t)blockIdx.x * kRmqChunk;
-  rmq_chunk(a.val[0], a.size[0], b0, kRmqChunk, a.mask[0], a.levels > 1 ? a.val[1] : nullptr, s_d);
+  rmq_chunk(a.val[0], a.size[0], b0, kRmqChunk, a.mask[0], a.pmin[0], a.smin[0], a.levels > 1 ? a.val[1] : nullptr,
+            s_d, true);
   if (a.levels > 1)
-    rmq_chunk(a.val[1], a.size[1], b0 / 32, kRmqThreads, a.mask[1], a.levels > 2 ? a.val[2] : nullptr, s_d);
+    rmq_chunk(a.val[1], a.size[1], b0 / 32, kRmqThreads, a.mask[1], a.pmin[1], a.smin[1],
+              a.levels > 2 ? a.val[2] : nullptr, s_d, false);
   if (a.levels <= 2) return;  // uniform
   if (threadIdx.x == 0) {
     __threadfence();
@@ -286,8 +309,8 @@ __global__ void __launch_bounds__(kRmqThreads) k_rmq_build(RmqArgs a) {
   __threadfence();
   for (int j = 2; j < a.levels; j++)
     for (int64_t base = 0; base < a.size[j]; base += kRmqChunk)
-      rmq_chunk(a.val[j], a.size[j], base, (int)min((int64_t)kRmqChunk, a.size[j] - base), a.mask[j],
-                j + 1 < a.levels ? a.val[j + 1] : nullptr, s_d);
+      rmq_chunk(a.val[j], a.size[j], base, (int)min((int64_t)kRmqChunk, a.size[j] - base), a.mask[j], a.pmin[j],
+                a.smin[j], j + 1 < a.levels ? a.val[j + 1] : nullptr, s_d, false);
   if (threadIdx.x == 0) *a.done = 0;
 }
 
@@ -310,6 +333,8 @@ int step_tree(Handle& h) {
   for (int j = 0; j < h.rmq_levels; j++) {
     r.val[j] = h.rmq_val[j];
     r.mask[j] = h.rmq_mask[j];
+    r.pmin[j] = h.rmq_pmin[j];
+    r.smin[j] = h.rmq_smin[j];
     r.size[j] = h.rmq_size[j];
   }
   r.levels = h.rmq_levels;
