@@ -592,9 +592,9 @@ def serve_pool(args, workers):
                         chunksize=1)
 
 
-def serve_leg(args, pool, dev, torch):
-    """Config 5: Poisson arrivals at --serve-rate for --serve-seconds into the
-    continuous-batching server; latency = completion - arrival."""
+def serve_point(args, pool, dev, rate, seconds, seed):
+    """One Poisson stream at `rate` requests/s for `seconds` into a fresh continuous-batching server; latency =
+    completion - arrival."""
     from paper_2508_20403_gb300 import serve as S
 
     srv = S.Server(mem_budget_bytes=args.serve_mem_gb << 30, slots=args.serve_slots, device=dev.index).start()
@@ -604,15 +604,26 @@ def serve_leg(args, pool, dev, torch):
     srv.batch_sizes.clear()
     srv.max_inflight = 0
     t0 = time.perf_counter()
-    reqs = S.run_stream(srv, pool, rate=args.serve_rate, duration=args.serve_seconds)
+    reqs = S.run_stream(srv, pool, rate=rate, duration=seconds, seed=seed)
     wall = time.perf_counter() - t0
     srv.stop()
     out = S.summarize(reqs, wall)
-    out.update({"rate_req_s": args.serve_rate, "seconds": args.serve_seconds, "pool_graphs": len(pool),
-                "slots": args.serve_slots, "mem_budget_gb": args.serve_mem_gb, "batches": len(srv.batch_sizes),
+    out.update({"rate_req_s": rate, "seconds": seconds, "pool_graphs": len(pool), "slots": args.serve_slots,
+                "mem_budget_gb": args.serve_mem_gb, "batches": len(srv.batch_sizes),
                 "mean_batch": float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0,
+                "max_batch": int(max(srv.batch_sizes)) if srv.batch_sizes else 0,
                 "max_batches_in_flight": srv.max_inflight, "errors": len(srv.errors),
                 "alphas": [0.02, 0.05, 0.10], "c": args.c})
+    return out
+
+
+def serve_leg(args, pool, dev, torch):
+    """Config 5: Poisson arrivals into the continuous-batching server, at the configured rate (200 requests/s for
+    60 s by default) and at a rate above what one request at a time can serve (--serve-high-rate), where the
+    queue builds up and requests are admitted into shared batches while others run."""
+    out = serve_point(args, pool, dev, args.serve_rate, args.serve_seconds, seed=20250833)
+    if args.serve_high_rate > 0:
+        out["high_rate"] = serve_point(args, pool, dev, args.serve_high_rate, args.serve_high_seconds, seed=20250834)
     return out
 
 
@@ -792,7 +803,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
-    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-pool", type=int, default=128)
+    ap.add_argument("--serve-high-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-high-seconds", type=float, default=15.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-mem-gb", type=int, default=32)
     args = ap.parse_args()

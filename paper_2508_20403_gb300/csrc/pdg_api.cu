@@ -473,7 +473,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
       (st = ensure_scan_status(h, std::max<int64_t>(std::max<int64_t>(n, num_graphs), E) + 1)))
     return fail(st);
   // the tree's layout: preorder labels, Euler tour, the relabelled edge list and parents
-  if ((st = build_tree_layout(h)) || (st = tree_scan_workspace(h))) return fail(st);
+  if ((st = build_tree_layout(h)) || (st = tree_scan_workspace(h)) || (st = classify_layout(h))) return fail(st);
   HostStage& s = hp->stage;
   s.G = num_graphs;
   s.sel = static_cast<GraphSel*>(pinned_alloc(sizeof(GraphSel) * num_graphs));

@@ -332,20 +332,29 @@ int build_edge_list(Handle& h) {
   return PDG_OK;
 }
 
-int step_classify(Handle& h) {
+// Init: the number of off-tree edges in each block's chunk of the edge list is
+// a fact of the fixed tree, so the write offsets of the recovery's compaction
+// are counted once here (a count pass and a scan) and kept.
+int classify_layout(Handle& h) {
   if (h.m == 0) return PDG_OK;
   const int nb = h.nblk;
+  int st;
+  if ((st = device_alloc(h, (void**)&h.cls_off, sizeof(int64_t) * (size_t)(nb + 1)))) return st;
   int64_t* cnt_off = h.blk_a;
-  int64_t* off_off = h.blk_a + 2560;
   ++h.launches;
   k_classify<false><<<nb, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, cnt_off, nullptr, nullptr,
                                                  nullptr, nullptr, nullptr, nullptr, h.dsc);
   PDG_CUDA(cudaGetLastError());
-  int st = scan_excl_i64(h, cnt_off, off_off, nb, nullptr, nb);
-  if (st) return st;
+  return scan_excl_i64(h, cnt_off, h.cls_off, nb, nullptr, nb);
+}
+
+// Recovery: one pass classifies every edge, writes r(x) of the tree edges
+// and the off-tree records at the offsets counted at init.
+int step_classify(Handle& h) {
+  if (h.m == 0) return PDG_OK;
   ++h.launches;
-  k_classify<true><<<nb, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, nullptr, off_off, h.rtree, h.off_u,
-                                                h.off_v, h.off_id, h.off_w, h.dsc);
+  k_classify<true><<<h.nblk, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, nullptr, h.cls_off,
+                                                    h.rtree, h.off_u, h.off_v, h.off_id, h.off_w, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

@@ -169,6 +169,7 @@ struct Handle {
   double* off_w = nullptr;
   double* rtree = nullptr;  // r(v) = fl(1/w(v, parent v))
   int64_t* blk_a = nullptr; // per-block counters (classification, scans)
+  int64_t* cls_off = nullptr;  // write offsets of the classification's block chunks (counted at init)
   int64_t* blk_b = nullptr;
   int nblk = 0;
 
@@ -454,6 +455,7 @@ int validate_graph(Handle& h);                  // sparsify_init checks + max de
 int build_edge_list(Handle& h);                 // init: canonical edge list from the CSR
 int build_tree_layout(Handle& h);               // init: preorder labels, Euler tour, relabelled edges and parents
 int tree_scan_workspace(Handle& h);             // init: look-back space of the tree scan
+int classify_layout(Handle& h);                 // init: off-tree edges per classification chunk
 int step_classify(Handle& h);                   // A1
 int step_tree(Handle& h);                       // A2
 int step_score(Handle& h, int score_mode);      // A3
