@@ -35,7 +35,7 @@ def device_bytes_estimate(g) -> int:
     n, m = g.n, g.m
     e_off = max(m - n + 1, 0)
     return int(8 * n + 24 * m + 4 * n  # CSR + parent
-               + 8 * n + 32 * n + 4 * n * 13  # r, P ping-pong, lifting table (<= 14 levels)
+               + 8 * n + 16 * n + 12 * n + 2 * 28 * n  # r, P, Euler tour + labels, range-minimum levels (x2 margin)
                + 36 * e_off  # off-tree SoA, keys, LCAs
                + 400 * max(int(0.2 * n), 1024)  # candidate buffers and tables
                + (1 << 20))
