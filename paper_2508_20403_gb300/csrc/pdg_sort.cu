@@ -542,24 +542,36 @@ __device__ __forceinline__ void coop_keyset(const CoopSortArgs& a, CoopSmem& sm,
       }
     }
     coop_barrier(a, target);
-    // the tile's prefix per digit: counts of the earlier tiles, summed by every block for itself
-    // (two threads per digit, each over half of the earlier tiles)
+    // the tile's prefix per digit: counts of the earlier tiles, summed by every block for itself.  The
+    // 256 counts of a tile are one 1 KB row: 64 threads read a row (16 bytes each), the eight row
+    // groups take every eighth earlier tile, four rows in flight per thread, then add up in shared memory.
     if (t < tiles) {
-      const int dg = threadIdx.x & (kRdxBins - 1), half = threadIdx.x >> 8;
-      const int64_t lo = half ? t / 2 : 0, hi = half ? t : t / 2;
-      uint32_t acc = 0;
-      int64_t tt = lo;
-      for (; tt + 4 <= hi; tt += 4) {
-        const uint32_t c0 = __ldcg(&a.counts[(tt + 0) * kRdxBins + dg]);
-        const uint32_t c1 = __ldcg(&a.counts[(tt + 1) * kRdxBins + dg]);
-        const uint32_t c2 = __ldcg(&a.counts[(tt + 2) * kRdxBins + dg]);
-        const uint32_t c3 = __ldcg(&a.counts[(tt + 3) * kRdxBins + dg]);
-        acc += c0 + c1 + c2 + c3;
+      const int q = threadIdx.x & 63, rg = threadIdx.x >> 6;
+      uint4 acc = make_uint4(0, 0, 0, 0);
+      for (int64_t r0 = rg; r0 < t; r0 += 32) {
+        uint4 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int64_t r = r0 + 8 * u;
+          x[u] = r < t ? __ldcg(reinterpret_cast<const uint4*>(a.counts + r * kRdxBins) + q) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          acc.x += x[u].x;
+          acc.y += x[u].y;
+          acc.z += x[u].z;
+          acc.w += x[u].w;
+        }
       }
-      for (; tt < hi; tt++) acc += __ldcg(&a.counts[tt * kRdxBins + dg]);
-      if (half) sm.base[dg] = acc;
+      reinterpret_cast<uint4*>(&sm.wcnt[rg][0])[q] = acc;  // the per-warp counters are free after bucketing
       __syncthreads();
-      if (!half) sm.base[dg] = sm.bases[d][dg] + acc + sm.base[dg] - sm.loff[dg];
+      const int dg = threadIdx.x;
+      if (dg < kRdxBins) {
+        uint32_t before = 0;
+#pragma unroll
+        for (int g = 0; g < kCoThreads / 64; g++) before += sm.wcnt[g][dg];
+        sm.base[dg] = sm.bases[d][dg] + before - sm.loff[dg];
+      }
       __syncthreads();
     }
     // place: consecutive threads write consecutive slots of each digit's run

@@ -433,16 +433,37 @@ def test_block_tier_bounds(B, wm, bm):
 @pytest.mark.parametrize("keys", [2048, 4096])
 def test_sort_tile_sizes(B, keys):
     """The radix-sort scatter tiles the autotuner may pick (2048 / 4096 keys; 3072 is the default everywhere
-    else) sort exactly: mesh and R-MAT against the oracle, and a packed batch against its graphs one by one."""
-    _compare(B, W.mesh3d_graph(48, seed=44), 0.1, sort_tile_keys=keys)
-    _compare(B, W.rmat_graph(13, seed=77), 0.5, sort_tile_keys=keys)
+    else) sort exactly on the one-kernel-per-pass path they shape: mesh and R-MAT against the oracle, and a
+    packed batch against its graphs one by one."""
+    _compare(B, W.mesh3d_graph(48, seed=44), 0.1, sort_tile_keys=keys, sort_one_launch=0)
+    _compare(B, W.rmat_graph(13, seed=77), 0.5, sort_tile_keys=keys, sort_one_launch=0)
     graphs = [W.batch_member(i, n_hi=3e4) for i in range(6)]
     pk = W.pack_graphs(graphs)
-    with B.BatchSparsifier.from_packed(pk, options=B.default_options(sort_tile_keys=keys)) as bs:
+    opt = B.default_options(sort_tile_keys=keys, sort_one_launch=0)
+    with B.BatchSparsifier.from_packed(pk, options=opt) as bs:
         st, op, ids, sc, counts, gst = bs.recover_batch(np.full(len(graphs), 0.1), c=2)
     for i, g in enumerate(graphs):
         _, oids, osc, _ = O.recover(g, 0.1, c=2)
         assert np.array(ids[op[i]:op[i] + counts[i]]).tolist() == oids.tolist()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sort_forms(B, mode):
+    """Both forms of the ordering step against the oracle: one kernel per radix pass (0) and the one cooperative
+    launch (1, default).  Mesh and R-MAT, grids (weights in a narrow range), a graph with fewer
+    candidates than one tile, and a packed batch (graph index passes) one by one."""
+    _compare(B, W.mesh3d_graph(48, seed=44), 0.1, sort_one_launch=mode)
+    _compare(B, W.rmat_graph(13, seed=77), 0.5, sort_one_launch=mode)
+    _compare(B, W.grid_graph(100), 0.05, sort_one_launch=mode)
+    _compare(B, W.grid_graph(12), 0.1, sort_one_launch=mode)
+    graphs = [W.batch_member(i, n_hi=3e4) for i in range(6)] + [W.grid_graph(30)]
+    pk = W.pack_graphs(graphs)
+    with B.BatchSparsifier.from_packed(pk, options=B.default_options(sort_one_launch=mode)) as bs:
+        st, op, ids, sc, counts, gst = bs.recover_batch(np.full(len(graphs), 0.1), c=2)
+    for i, g in enumerate(graphs):
+        _, oids, osc, _ = O.recover(g, 0.1, c=2)
+        assert np.array(ids[op[i]:op[i] + counts[i]]).tolist() == oids.tolist()
+        assert np.array_equal(np.array(sc[op[i]:op[i] + counts[i]]), osc)
 
 
 @pytest.mark.parametrize("alpha", [0.02, 0.10])
