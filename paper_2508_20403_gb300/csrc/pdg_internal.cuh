@@ -183,8 +183,8 @@ struct Handle {
   uint32_t* rmq_mask[kRmqMaxLevels] = {nullptr};
   uint64_t* rmq_pmin[kRmqMaxLevels] = {nullptr};  // per entry: minimum from its group's start (null: top level)
   uint64_t* rmq_smin[kRmqMaxLevels] = {nullptr};  // per entry: minimum to its group's end
-  u128* ts_sum = nullptr;        // tree scan: tile sums, then their prefixes
-  uint32_t* ts_done = nullptr;   // blocks finished: [0] tree-scan tile sums, [1] range-minimum build
+  u128* ts_sum = nullptr;        // tree scan: tile sums
+  uint32_t* ts_done = nullptr;   // range-minimum build: blocks finished
 
   // scores
   uint64_t* key = nullptr;  // FP64 score bits (positive -> order preserving)

@@ -16,7 +16,7 @@
 // same pass writes, per vertex (preorder label x), the range-minimum key
 // val0[x] = depth(x) * 2^32 + parent(x).
 //
-// k_rmq_levels: the range-minimum structure over val0.  Level j + 1 holds the
+// k_rmq_build: the range-minimum structure over val0.  Level j + 1 holds the
 // minima of the 32-entry groups of level j, up to a single group.  Inside a
 // group, mask[k] has bit i set when entry i (i <= k) has a smaller depth than
 // every later entry up to k (a suffix minimum); the minimum depth over [i, k]
@@ -72,10 +72,11 @@ __device__ __forceinline__ u128 warp_incl_scan_u128(u128 x) {
 }
 
 // The tour is scanned in tiles of 256 threads x 8 arcs, reduce-then-scan:
-// k_tree_sum adds each tile's arcs (the last block to finish turns the tile
-// sums into exclusive prefixes), k_tree_scan rescans every tile from its
-// prefix and writes the vertices.  No tile waits on another (a chained scan
-// would have to pass the running prefix through every tile in order).
+// k_tree_sum adds each tile's arcs, k_tree_scan adds up the sums of the
+// tiles before its own (every block for itself: a few loads per thread,
+// no serial pass over the tiles) and rescans its tile from that prefix,
+// writing the vertices.  No tile waits on another (a chained scan would
+// have to pass the running prefix through every tile in order).
 constexpr int kTsThreads = 256;
 constexpr int kTsItems = 8;
 constexpr int kTsTile = kTsThreads * kTsItems;
@@ -89,8 +90,7 @@ struct TreeScanArgs {
   DevScalars* dsc;
   u128* P;
   uint64_t* val0;
-  u128* tsum;     // [tiles] tile sums, then their exclusive prefixes
-  uint32_t* done;  // blocks of k_tree_sum finished (the last one resets it)
+  u128* tsum;  // [tiles] tile sums
 };
 
 // the tile's arcs of this thread (INT_MIN past the end) and the r of their vertices
@@ -133,7 +133,6 @@ __device__ __forceinline__ u128 block_sum_u128(u128 x, u128* s_warp) {
 
 __global__ void __launch_bounds__(kTsThreads) k_tree_sum(TreeScanArgs a) {
   __shared__ u128 s_warp[kTsThreads / 32];
-  __shared__ int s_last;
   const bool range_ok = range_fits(a.dsc, a.dep_bits);
   const int e_min = a.dsc->e_min;
   const int64_t t = blockIdx.x;
@@ -144,41 +143,12 @@ __global__ void __launch_bounds__(kTsThreads) k_tree_sum(TreeScanArgs a) {
 #pragma unroll
   for (int i = 0; i < kTsItems; i++) s += arc_word(arc[i], r[i], e_min, range_ok);
   const u128 tot = block_sum_u128(s, s_warp);
-  if (threadIdx.x == 0) {
-    a.tsum[t] = tot;
-    __threadfence();
-    s_last = (atomicAdd(a.done, 1u) == gridDim.x - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  // the last block: exclusive prefixes of the tile sums, in chunks of one value per thread
-  __threadfence();
-  const int64_t tiles = gridDim.x;
-  u128 run = 0;
-  for (int64_t c0 = 0; c0 < tiles; c0 += kTsThreads) {
-    const int64_t i = c0 + threadIdx.x;
-    u128 v = 0;
-    if (i < tiles) {
-      const ulonglong2 q = __ldcg(reinterpret_cast<const ulonglong2*>(a.tsum + i));
-      v = ((u128)q.y << 64) | q.x;
-    }
-    const u128 incl = warp_incl_scan_u128(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    u128 before = run;
-    for (int w = 0; w < wid; w++) before += s_warp[w];
-    u128 chunk = 0;
-    for (int w = 0; w < kTsThreads / 32; w++) chunk += s_warp[w];
-    if (i < tiles) a.tsum[i] = before + incl - v;
-    run += chunk;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *a.done = 0;
+  if (threadIdx.x == 0) a.tsum[t] = tot;
 }
 
-__global__ void __launch_bounds__(kTsThreads) k_tree_scan(TreeScanArgs a) {
+__global__ void __launch_bounds__(kTsThreads, 4) k_tree_scan(TreeScanArgs a) {
   __shared__ u128 s_warp[kTsThreads / 32];
+  __shared__ u128 s_pre[kTsThreads / 32];
   const bool range_ok = range_fits(a.dsc, a.dep_bits);
   const int e_min = a.dsc->e_min;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -192,8 +162,19 @@ __global__ void __launch_bounds__(kTsThreads) k_tree_scan(TreeScanArgs a) {
   const u128 incl = warp_incl_scan_u128(s);
   if (lane == 31) s_warp[wid] = incl;
   __syncthreads();
-  const ulonglong2 q = __ldcg(reinterpret_cast<const ulonglong2*>(a.tsum + t));  // the tile's prefix
-  u128 p = ((u128)q.y << 64) | q.x;
+  // the tile's prefix: the sums of all earlier tiles, added up by this block itself (loads four deep)
+  u128 pre[4] = {0, 0, 0, 0};
+  for (int64_t i = threadIdx.x; i < t; i += 4 * kTsThreads) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int64_t j = i + (int64_t)k * kTsThreads;
+      if (j < t) {
+        const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2*>(a.tsum + j));
+        pre[k] += ((u128)q.y << 64) | q.x;
+      }
+    }
+  }
+  u128 p = block_sum_u128(pre[0] + pre[1] + pre[2] + pre[3], s_pre);
   for (int w = 0; w < wid; w++) p += s_warp[w];
   p += incl - s;  // prefix of every arc before this thread's first
 #pragma unroll
@@ -211,11 +192,10 @@ __global__ void __launch_bounds__(kTsThreads) k_tree_scan(TreeScanArgs a) {
 // The range-minimum structure in one launch.  Each block takes 8192 entries
 // of level 0 (256 groups) and then the 256 group minima it produced (8 groups
 // of level 1); the last block to finish builds the remaining, small levels.
-// A group's masks come from one thread walking its 32 entries in order with
-// a stack of suffix minima kept as a bit set: an entry pops the stacked
-// entries whose depth is not below its own, then pushes itself, and the
-// stack after entry k is mask[k].  Entries are staged in shared memory with
-// a padded row per group, so loads, walks and stores are conflict-free.
+// A group's masks are the stacks of suffix minima, as a bit set, that a walk
+// over its 32 entries would hold: entry k pops the stacked entries whose
+// depth is not below its own, then pushes itself, and the stack after entry
+// k is mask[k] (built without the walk, see rmq_chunk).
 constexpr int kRmqThreads = 256;
 constexpr int kRmqChunk = kRmqThreads * 32;  // entries per block and pass
 
@@ -232,96 +212,159 @@ struct RmqArgs {
 // entries [base, base + len) of one level (len <= kRmqChunk, base a multiple
 // of 32): their masks, the minima from the group start up to each entry
 // (pmin) and from each entry to the group end (smin), and the minimum of
-// every group to val_next[entry / 32] when val_next is given.  Both minima
-// come from the masks: the lowest set bit of mask[k] is the minimum of
-// [0, k], and the first set bit of mask[31] at or above k the minimum of
-// [k, 31] (padding past the level's end is deeper than any entry).
+// every group to val_next[entry / 32] when val_next is given.
+// The chunk is staged in shared memory by coalesced loads; then one thread
+// takes one group into registers and builds it without a data-dependent
+// step: the stack after entry k keeps the earlier stack entries shallower
+// than entry k, so mask[k] = (mask[k-1] & {j < k : depth j < depth k}) | bit k,
+// where the set is 31 comparisons of registers; pmin and smin are running
+// minima of the 64-bit keys (a minimum-depth entry of the range; ties carry
+// the same parent inside any query range).  Padding past the level's end is
+// deeper than any entry.
 // (FROM_PREV: the level was written by an earlier kernel, so its reads may use
 // the read-only cache; levels written by this kernel are read from L2)
 __device__ __forceinline__ uint64_t rmq_load(const uint64_t* p, bool from_prev) {
   return from_prev ? __ldg(p) : __ldcg(p);
 }
 
+struct RmqSmem {
+  uint64_t v[kRmqChunk / 32][33];  // values, a padded row per group (then the minima being written out)
+  uint32_t m[kRmqChunk / 32][33];  // masks
+};
+
 __device__ void rmq_chunk(const uint64_t* __restrict__ val, int64_t size, int64_t base, int len,
                           uint32_t* __restrict__ mask, uint64_t* __restrict__ pmin, uint64_t* __restrict__ smin,
-                          uint64_t* __restrict__ val_next, uint32_t (*s_d)[33], bool from_prev) {
+                          uint64_t* __restrict__ val_next, RmqSmem& sm, bool from_prev) {
+  constexpr int kPer = kRmqChunk / kRmqThreads;
   const int t = threadIdx.x;
   const int ngroups = (len + 31) / 32;
-  for (int i = t; i < ngroups * 32; i += kRmqThreads) {
-    const int64_t idx = base + i;
-    s_d[i >> 5][i & 31] = (i < len && idx < size) ? (uint32_t)(rmq_load(val + idx, from_prev) >> 32) : 0xffffffffu;
+  {
+    uint64_t x[kPer];  // a thread's loads are independent and in flight together
+#pragma unroll
+    for (int i = 0; i < kPer; i++) {
+      const int li = i * kRmqThreads + t;
+      const int64_t idx = base + li;
+      x[i] = (li < ngroups * 32 && li < len && idx < size) ? rmq_load(val + idx, from_prev) : ~0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; i++) {
+      const int li = i * kRmqThreads + t;
+      if (li < ngroups * 32) sm.v[li >> 5][li & 31] = x[i];
+    }
   }
   __syncthreads();
-  const bool walk = t < ngroups && base + 32 * t < size;
-  uint32_t m[32];
-  if (walk) {
-    uint32_t stack = 0;
+  uint64_t v[32];
+  const bool own = t < ngroups;
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < 32; k++) v[k] = sm.v[t][k];
+    uint32_t mk = 0;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
-      const uint32_t d = s_d[t][k];
-      while (stack) {  // pop the entries whose depth is not below d
-        const int top = 31 - __clz(stack);
-        if (s_d[t][top] < d) break;
-        stack &= ~(1u << top);
-      }
-      stack |= 1u << k;
-      m[k] = stack;
-    }
-    if (val_next) val_next[(base >> 5) + t] = rmq_load(val + base + 32 * t + (__ffs(stack) - 1), from_prev);
-  }
-  __syncthreads();  // every walk is done: the rows now take the masks
-  if (walk) {
+      const uint32_t dk = (uint32_t)(v[k] >> 32);
+      uint32_t shallower = 0;
 #pragma unroll
-    for (int k = 0; k < 32; k++) s_d[t][k] = m[k];
+      for (int j = 0; j < k; j++) shallower |= ((uint32_t)(v[j] >> 32) < dk ? 1u : 0u) << j;
+      mk = (mk & shallower) | (1u << k);
+      sm.m[t][k] = mk;
+    }
+    uint64_t pm = ~0ull;
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+      pm = min(pm, v[k]);
+      sm.v[t][k] = pm;  // only this thread reads its row
+    }
+    if (val_next && base + 32 * t < size) val_next[(base >> 5) + t] = pm;
+    uint64_t sf = ~0ull;
+#pragma unroll
+    for (int k = 31; k >= 0; k--) {
+      sf = min(sf, v[k]);
+      v[k] = sf;
+    }
   }
   __syncthreads();
   for (int i = t; i < len; i += kRmqThreads) {
     const int64_t idx = base + i;
-    if (idx >= size) continue;
-    const int g = i >> 5, k = i & 31;
-    const uint32_t mk = s_d[g][k];
-    mask[idx] = mk;
-    if (pmin) {
-      const int64_t g0 = base + 32 * g;
-      pmin[idx] = rmq_load(val + g0 + (__ffs(mk) - 1), from_prev);
-      smin[idx] = rmq_load(val + g0 + k + (__ffs(s_d[g][31] >> k) - 1), from_prev);
+    if (idx >= size) break;  // idx grows with i
+    mask[idx] = sm.m[i >> 5][i & 31];
+    if (pmin) pmin[idx] = sm.v[i >> 5][i & 31];
+  }
+  if (pmin) {  // uniform
+    __syncthreads();
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < 32; k++) sm.v[t][k] = v[k];
+    }
+    __syncthreads();
+    for (int i = t; i < len; i += kRmqThreads) {
+      const int64_t idx = base + i;
+      if (idx >= size) break;
+      smin[idx] = sm.v[i >> 5][i & 31];
     }
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kRmqThreads) k_rmq_build(RmqArgs a) {
-  __shared__ uint32_t s_d[kRmqThreads][33];
+__global__ void __launch_bounds__(kRmqThreads, 2) k_rmq_build(RmqArgs a) {
+  extern __shared__ __align__(16) unsigned char rmq_smem[];
+  RmqSmem& sm = *reinterpret_cast<RmqSmem*>(rmq_smem);
   __shared__ int s_last;
   const int64_t b0 = (int64_t)blockIdx.x * kRmqChunk;
-  rmq_chunk(a.val[0], a.size[0], b0, kRmqChunk, a.mask[0], a.pmin[0], a.smin[0], a.levels > 1 ? a.val[1] : nullptr,
-            s_d, true);
-  if (a.levels > 1)
-    rmq_chunk(a.val[1], a.size[1], b0 / 32, kRmqThreads, a.mask[1], a.pmin[1], a.smin[1],
-              a.levels > 2 ? a.val[2] : nullptr, s_d, false);
-  if (a.levels <= 2) return;  // uniform
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(a.done, 1u) == gridDim.x - 1) ? 1 : 0;
+  // the chunks this block builds, in order (one call site keeps the register budget of one chunk):
+  // its 8192 entries of level 0, their 256 minima on level 1, and for the last block every chunk of level 2 up
+  int j = 0;
+  int64_t base = b0;
+  int len = kRmqChunk;
+  bool tail = false;
+  for (;;) {
+    rmq_chunk(a.val[j], a.size[j], base, len, a.mask[j], a.pmin[j], a.smin[j],
+              j + 1 < a.levels ? a.val[j + 1] : nullptr, sm, j == 0);
+    if (!tail) {
+      if (j == 0 && a.levels > 1) {
+        j = 1;
+        base = b0 / 32;
+        len = kRmqThreads;
+        continue;
+      }
+      if (a.levels <= 2) return;  // uniform
+      if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(a.done, 1u) == gridDim.x - 1) ? 1 : 0;
+      }
+      __syncthreads();
+      if (!s_last) return;
+      __threadfence();
+      tail = true;
+      j = 2;
+      base = 0;
+    } else {
+      base += kRmqChunk;
+      if (base >= a.size[j]) {
+        if (++j >= a.levels) break;
+        base = 0;
+      }
+    }
+    len = (int)min((int64_t)kRmqChunk, a.size[j] - base);
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int j = 2; j < a.levels; j++)
-    for (int64_t base = 0; base < a.size[j]; base += kRmqChunk)
-      rmq_chunk(a.val[j], a.size[j], base, (int)min((int64_t)kRmqChunk, a.size[j] - base), a.mask[j], a.pmin[j],
-                a.smin[j], j + 1 < a.levels ? a.val[j + 1] : nullptr, s_d, false);
   if (threadIdx.x == 0) *a.done = 0;
 }
 
 }  // namespace
+
+// the range-minimum build's shared memory, granted once per process (first asked at init, outside any
+// stream capture; thread-safe initialisation)
+static cudaError_t rmq_smem_attr() {
+  static const cudaError_t e =
+      cudaFuncSetAttribute(k_rmq_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RmqSmem));
+  return e;
+}
 
 int step_tree(Handle& h) {
   int dep_bits = 0;
   while ((1ll << dep_bits) <= h.max_depth) dep_bits++;
   if (h.A > 0) {
     const int64_t tiles = (h.A + kTsTile - 1) / kTsTile;
-    TreeScanArgs a{h.tour, h.A, h.rtree, h.parent, dep_bits, h.dsc, h.P, h.rmq_val[0], h.ts_sum, h.ts_done};
+    TreeScanArgs a{h.tour, h.A, h.rtree, h.parent, dep_bits, h.dsc, h.P, h.rmq_val[0], h.ts_sum};
     ++h.launches;
     k_tree_sum<<<(int)tiles, kTsThreads, 0, h.stream>>>(a);
     ++h.launches;
@@ -338,21 +381,23 @@ int step_tree(Handle& h) {
     r.size[j] = h.rmq_size[j];
   }
   r.levels = h.rmq_levels;
-  r.done = h.ts_done + 1;
+  r.done = h.ts_done;
+  PDG_CUDA(rmq_smem_attr());
   ++h.launches;
-  k_rmq_build<<<(int)((h.rmq_size[0] + kRmqChunk - 1) / kRmqChunk), kRmqThreads, 0, h.stream>>>(r);
+  k_rmq_build<<<(int)((h.rmq_size[0] + kRmqChunk - 1) / kRmqChunk), kRmqThreads, sizeof(RmqSmem), h.stream>>>(r);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
 
-// the tree-scan work space for a tour of A arcs (tile sums, two block counters)
+// the tree-scan work space for a tour of A arcs (tile sums) and the range-minimum build's block counter
 int tree_scan_workspace(Handle& h) {
+  PDG_CUDA(rmq_smem_attr());
   const int64_t tiles = std::max<int64_t>((h.A + kTsTile - 1) / kTsTile, 1);
   int st;
   if ((st = device_alloc(h, (void**)&h.ts_sum, sizeof(u128) * (size_t)tiles)) ||
-      (st = device_alloc(h, (void**)&h.ts_done, sizeof(uint32_t) * 2)))
+      (st = device_alloc(h, (void**)&h.ts_done, sizeof(uint32_t))))
     return st;
-  PDG_CUDA(cudaMemsetAsync(h.ts_done, 0, sizeof(uint32_t) * 2, h.stream));
+  PDG_CUDA(cudaMemsetAsync(h.ts_done, 0, sizeof(uint32_t), h.stream));
   return PDG_OK;
 }
 
