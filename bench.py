@@ -715,7 +715,35 @@ def pcg_leg(args, B):
                 row["iterations_oracle"] = PC.pcg_quality(g, ids, b, tol=1e-3)[0]
             rows.append(row)
     return {"workload": f"grid 100x100 (n={g.n}, m={g.m}), weights U[1,10], max-weight tree, c={args.c}",
-            "tol": 1e-3, "rows": rows}
+            "tol": 1e-3, "rows": rows, "mesh64": pcg_mesh64(args, B)}
+
+
+def pcg_mesh64(args, B):
+    """The same measure on the 3D mesh 64^3 (the headline family at 1/8 of its size) at alpha = .02: 5,242 extra
+    edges, inside the dense capacitance bound (8,192 edges; mesh 128^3 at .02 has 41,943).  The oracle's count
+    (and its range under rounding-level perturbations of b) is the stored one, written by an oracle-only script
+    (tests/golden/make_pcg_expect.py), valid when this run recovers the same edges."""
+    import hashlib
+
+    from paper_2508_20403_gb300 import workloads as W
+
+    with open(os.path.join(ROOT, "tests", "golden", "pcg_mesh64_expect.json")) as f:
+        e = json.load(f)
+    g = W.mesh3d_graph(64)
+    k = int(math.floor(e["alpha"] * g.n))
+    with B.Sparsifier.from_graph(g) as sp:
+        st, ids, _, _ = sp.recover(e["alpha"], e["c"], capacity=max(k, 1))
+    ids = np.ascontiguousarray(ids, dtype="<i4")
+    b = np.random.default_rng(e["b_seed"]).standard_normal(g.n)
+    t0 = time.perf_counter()
+    it, rel = B.pcg_quality(g, ids, b, tol=e["tol"])
+    row = {"workload": f"mesh 64^3 (n={g.n}, m={g.m}), w log-uniform [1e-3,1e3], max-weight tree, c={e['c']}",
+           "alpha": e["alpha"], "edges": int(ids.size), "iterations": it, "relres": rel,
+           "ms": (time.perf_counter() - t0) * 1e3, "tol": e["tol"]}
+    if hashlib.sha256(ids.tobytes()).hexdigest() == e["ids_sha256"]:
+        row.update(iterations_oracle=e["iterations"], oracle_count_range=e["count_range"],
+                   oracle_source="stored by tests/golden/make_pcg_expect.py (oracle only; same recovered edges)")
+    return row
 
 
 def oracle_sample_recovery(g, args):

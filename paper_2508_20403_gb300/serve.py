@@ -3,9 +3,10 @@
 Requests (a graph with its spanning tree, a ratio alpha, a cap c) arrive at
 any time.  Each of `slots` workers owns a CUDA stream; whenever a worker is
 free it takes every queued request that fits the device-memory budget (in
-arrival order), packs them into one CSR, uploads the batch
-(sparsify_batch_init: the graphs stay resident in device memory while the
-batch runs), runs ONE recover_offtree_batch and completes the requests.
+arrival order), packs them into one CSR in the worker's pinned staging
+buffers, uploads the batch (sparsify_batch_init: the graphs stay resident in
+device memory while the batch runs), runs ONE recover_offtree_batch and
+completes the requests.
 Requests that arrive while batches are on the GPU are admitted into the next
 batch as soon as a slot and memory free up, so the work of several batches
 overlaps on the device.  Each request's result is exactly what
@@ -131,6 +132,7 @@ class Server:
         torch = self.torch
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(device=self.device)
+        staging = _Staging(torch)
         while True:
             with self.cv:
                 while not self.stop_flag and not self.queue:
@@ -146,7 +148,7 @@ class Server:
                 self.inflight += 1
                 self.max_inflight = max(self.max_inflight, self.inflight)
             try:
-                self._run_batch(batch, bid, stream)
+                self._run_batch(batch, bid, stream, staging)
             except Exception as e:  # report, complete the requests with an error status
                 self.errors.append(repr(e))
                 for r in batch:
@@ -160,15 +162,18 @@ class Server:
                     self.batch_sizes.append(len(batch))
                     self.cv.notify_all()
 
-    def _run_batch(self, batch, bid, stream):
+    def _run_batch(self, batch, bid, stream, staging):
         t0 = time.perf_counter()
         for r in batch:
             r.t_start = t0
             r.batch = bid
-        pk = W.pack_graphs([r.graph for r in batch])
+        graphs = [r.graph for r in batch]
+        N, nnz = W.packed_sizes(graphs)
+        bufs = staging.get(N, nnz)  # the batch is packed straight into pinned memory (one copy, DMA upload)
+        pk = W.pack_graphs(graphs, out=tuple(b.numpy() for b in bufs))
         alphas = np.array([r.alpha for r in batch], dtype=np.float64)
         opt = B.default_options(use_graph=1 if self.use_graph else 0)
-        with B.BatchSparsifier(pk.vtx_ptr, pk.row_ptr, pk.col, pk.w, pk.parent, options=opt,
+        with B.BatchSparsifier(pk.vtx_ptr, bufs[0][:N + 1], bufs[1][:nnz], bufs[2][:nnz], bufs[3][:N], options=opt,
                                stream=stream.cuda_stream) as bs:
             st, op, ids, sc, counts, gst = bs.recover_batch(alphas, c=batch[0].c)
         t1 = time.perf_counter()
@@ -180,6 +185,26 @@ class Server:
                 r.t_done = t1
                 self.completed.append(r)
                 r.done.set()
+
+
+class _Staging:
+    """Pinned host buffers of one worker (row_ptr, col, w, parent of a packed batch), grown on demand."""
+
+    def __init__(self, torch):
+        self.torch = torch
+        self.cap = (0, 0)
+        self.bufs = None
+
+    def get(self, N: int, nnz: int):
+        if self.bufs is None or N + 1 > self.cap[0] or nnz > self.cap[1]:
+            torch = self.torch
+            cn, ce = max(N + 1, 2 * self.cap[0]), max(nnz, 2 * self.cap[1], 1)
+            self.bufs = (torch.empty(cn, dtype=torch.int64, pin_memory=True),
+                         torch.empty(ce, dtype=torch.int32, pin_memory=True),
+                         torch.empty(ce, dtype=torch.float64, pin_memory=True),
+                         torch.empty(cn, dtype=torch.int32, pin_memory=True))
+            self.cap = (cn, ce)
+        return self.bufs
 
 
 def poisson_arrivals(rate: float, duration: float, rng: np.random.Generator) -> np.ndarray:

@@ -345,7 +345,14 @@ class PackedGraphs:
         return int(self.vtx_ptr[-1])
 
 
-def pack_graphs(graphs: Sequence[Graph]) -> PackedGraphs:
+def packed_sizes(graphs: Sequence[Graph]):
+    """(vertices, CSR entries) of the disjoint union of `graphs`."""
+    return sum(g.n for g in graphs), sum(2 * g.m for g in graphs)
+
+
+def pack_graphs(graphs: Sequence[Graph], out=None) -> PackedGraphs:
+    """The disjoint union of `graphs`.  `out` may hold preallocated arrays (row_ptr int64[N+1], col int32[nnz],
+    w float64[nnz], parent int32[N], at least that long; e.g. views of pinned host memory) to write into."""
     G = len(graphs)
     vtx_ptr = np.zeros(G + 1, dtype=np.int64)
     edge_ptr = np.zeros(G + 1, dtype=np.int64)
@@ -355,21 +362,26 @@ def pack_graphs(graphs: Sequence[Graph]) -> PackedGraphs:
         edge_ptr[i + 1] = edge_ptr[i] + g.m
         nnz_ptr[i + 1] = nnz_ptr[i] + 2 * g.m
     N = int(vtx_ptr[-1])
-    if N >= 2 ** 31 - 1 or int(nnz_ptr[-1]) >= 2 ** 62:
+    nnz = int(nnz_ptr[-1])
+    if N >= 2 ** 31 - 1 or nnz >= 2 ** 62:
         raise ValueError("packed batch too large for int32 vertex ids")
-    row_ptr = np.empty(N + 1, dtype=np.int64)
-    col = np.empty(int(nnz_ptr[-1]), dtype=np.int32)
-    w = np.empty(int(nnz_ptr[-1]), dtype=np.float64)
-    parent = np.empty(N, dtype=np.int32)
+    if out is None:
+        row_ptr = np.empty(N + 1, dtype=np.int64)
+        col = np.empty(nnz, dtype=np.int32)
+        w = np.empty(nnz, dtype=np.float64)
+        parent = np.empty(N, dtype=np.int32)
+    else:
+        row_ptr, col, w, parent = out[0][:N + 1], out[1][:nnz], out[2][:nnz], out[3][:N]
     for i, g in enumerate(graphs):
         v0, v1 = int(vtx_ptr[i]), int(vtx_ptr[i + 1])
         e0, e1 = int(nnz_ptr[i]), int(nnz_ptr[i + 1])
-        row_ptr[v0:v1] = g.row_ptr[:-1] + e0
-        col[e0:e1] = g.col + v0
+        np.add(g.row_ptr[:-1], e0, out=row_ptr[v0:v1], casting="unsafe")
+        np.add(g.col, v0, out=col[e0:e1], casting="unsafe")
         w[e0:e1] = g.w
-        p = g.parent.astype(np.int64)
-        parent[v0:v1] = np.where(p >= 0, p + v0, -1)
-    row_ptr[N] = nnz_ptr[-1]
+        pv = parent[v0:v1]
+        np.add(g.parent, v0, out=pv, casting="unsafe")
+        pv[np.asarray(g.parent) < 0] = -1
+    row_ptr[N] = nnz
     return PackedGraphs(row_ptr=row_ptr, col=col, w=w, parent=parent, vtx_ptr=vtx_ptr, edge_ptr=edge_ptr)
 
 

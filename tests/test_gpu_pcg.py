@@ -18,6 +18,10 @@ The final residual must meet the tolerance.
 """
 from __future__ import annotations
 
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -117,3 +121,33 @@ def test_rejects_bad_edge_lists(B):
         with pytest.raises(B.PdgError) as e:
             B.pcg_quality(g, np.array(bad, dtype=np.int32), b)
         assert e.value.status == B.PDG_E_INVALID_ARG
+
+
+def test_mesh64_alpha02_against_stored_oracle(B):
+    """Mesh 64^3 at alpha = .02 with the oracle's recovery as the extra edges (5,242: inside the dense
+    capacitance bound of 8,192).  One oracle run there takes tens of seconds and the count range takes nine, so
+    they are stored (tests/golden/make_pcg_expect.py, oracle only); the same checks as above on the stored
+    values, with the preconditioner compared at 4,096 evenly spaced vertices.  If this host's generator or
+    oracle gives another graph or edge set, the oracle runs live instead."""
+    from tests.golden.make_full_size_expect import graph_digest
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pcg_mesh64_expect.json")) as f:
+        e = json.load(f)
+    g = W.mesh3d_graph(64)
+    ids = np.ascontiguousarray(O.recover(g, e["alpha"], c=e["c"])[1], dtype="<i4")
+    b = np.random.default_rng(e["b_seed"]).standard_normal(g.n)
+    it, rel, hist, z0 = B.pcg_trace(g, ids, b, tol=e["tol"])
+    if graph_digest(g) != e["graph_sha256"] or hashlib.sha256(ids.tobytes()).hexdigest() != e["ids_sha256"]:
+        _check(B, g, ids, b, tol=e["tol"])
+        return
+    idx = np.asarray(e["z0_sample_index"])
+    err = np.abs(z0[idx] - np.asarray(e["z0_sample"]))
+    assert err.max() <= PRECOND_TOL * e["z0_max_abs"], float(err.max())
+    assert abs(float(np.abs(z0).max()) - e["z0_max_abs"]) <= PRECOND_TOL * e["z0_max_abs"]
+    ohist = np.asarray(e["history"])
+    q = min(RESID_ITERS, len(hist), len(ohist))
+    rdiff = np.abs(hist[:q] - ohist[:q]) / ohist[:q]
+    assert rdiff.max(initial=0.0) <= RESID_RTOL, rdiff.tolist()
+    lo, hi = e["count_range"]
+    assert lo - ITER_SPREAD <= it <= hi + ITER_SPREAD, (it, e["iterations"], lo, hi)
+    assert rel <= e["tol"]
