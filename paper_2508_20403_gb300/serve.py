@@ -64,7 +64,7 @@ class Request:
 
 class Server:
     def __init__(self, mem_budget_bytes: int = 16 << 30, slots: int = 4, max_batch_graphs: int = 512,
-                 device: int = 0, use_graph: bool = False):
+                 device: int = 0, use_graph: bool = False, staging_hint=(0, 0)):
         import torch
 
         self.torch = torch
@@ -85,14 +85,20 @@ class Server:
         self.completed: List[Request] = []
         self.errors: List[str] = []
         self._rid = 0
+        # (vertices, CSR entries) every worker's pinned staging holds from the start (pinned allocations are
+        # slow: growing them under load stalls the worker)
+        self.staging_hint = staging_hint
 
     # ------------------------------------------------------------------ API
     def start(self):
         B.load()
+        self._ready = threading.Semaphore(0)
         for i in range(self.slots):
             t = threading.Thread(target=self._worker, args=(i,), daemon=True)
             t.start()
             self.workers.append(t)
+        for _ in range(self.slots):  # every worker has its stream and staging before requests are taken
+            self._ready.acquire()
         return self
 
     def submit(self, graph, alpha: float, c: int = 2) -> Request:
@@ -133,6 +139,11 @@ class Server:
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(device=self.device)
         staging = _Staging(torch)
+        try:
+            if self.staging_hint[0] > 0:
+                staging.get(*self.staging_hint)
+        finally:
+            self._ready.release()
         while True:
             with self.cv:
                 while not self.stop_flag and not self.queue:
