@@ -423,7 +423,7 @@ int sparsify_batch_init(pdg_handle* out, int32_t num_graphs, const int64_t* vtx_
           cudaSuccess)
     return fail(PDG_E_CUDA);
   h.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (h.m + kTile - 1) / kTile));
-  if ((st = validate_graph(h))) return fail(st);
+  if ((st = validate_graph(h, false))) return fail(st);  // acyclicity, depth and range: build_tree_layout
   // per-graph edge counts from the row offsets at the graph boundaries
   std::vector<int64_t> rp_at(num_graphs + 1);
   {
@@ -619,7 +619,7 @@ static int pcg_entry(int64_t n, const int64_t* row_ptr, const int32_t* col, cons
       cudaMemcpyAsync(d_b, b, sizeof(double) * n, kind, h.stream) != cudaSuccess ||
       cudaMemcpyAsync(h.d_vtx_ptr, vp, sizeof(vp), cudaMemcpyHostToDevice, h.stream) != cudaSuccess)
     return fail(PDG_E_CUDA);
-  if ((st = validate_graph(h))) return fail(st);
+  if ((st = validate_graph(h, true))) return fail(st);
   if ((st = alloc_n(h, &h.el_u, std::max<int64_t>(h.m, 1))) || (st = alloc_n(h, &h.el_v, std::max<int64_t>(h.m, 1))) ||
       (st = alloc_n(h, &h.el_w, std::max<int64_t>(h.m, 1))) || (st = build_edge_list(h)))
     return fail(st);

@@ -29,6 +29,7 @@ constexpr int kRadixHistOnesweep = 16 * 256 + 2 * kRadixPassesMax;  // per-pass 
 constexpr int kRadixHistWords = kRadixHistOnesweep + 3 * 8 * 256;     // + the one-launch sort's key-set histograms
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kRmqMaxLevels = 6;  // levels of the range-minimum structure (n < 2^30: 30 / 5)
+constexpr int kRmqStMax = 6144;   // level-2 entries up to which levels 2+ are one sparse table (n <= 6.29M)
 
 // error bits raised by validation kernels (mapped to a status on the host)
 enum : int {
@@ -183,6 +184,8 @@ struct Handle {
   uint32_t* rmq_mask[kRmqMaxLevels] = {nullptr};
   uint64_t* rmq_pmin[kRmqMaxLevels] = {nullptr};  // per entry: minimum from its group's start (null: top level)
   uint64_t* rmq_smin[kRmqMaxLevels] = {nullptr};  // per entry: minimum to its group's end
+  uint64_t* rmq_st = nullptr;  // sparse table over level 2 (row t: minima of 2^t entries; row 0 is level 2)
+  int rmq_st_rows = 0;
   u128* ts_sum = nullptr;        // tree scan: tile sums
   uint32_t* ts_done = nullptr;   // range-minimum build: blocks finished
 
@@ -451,7 +454,7 @@ int scan_excl_u32(Handle& h, const uint32_t* in, int64_t* out, const int64_t* n_
 int scan_excl_u8(Handle& h, const uint8_t* in, int64_t* out, const int64_t* n_dev, int64_t n_max);
 
 // steps
-int validate_graph(Handle& h);                  // sparsify_init checks + max depth
+int validate_graph(Handle& h, bool acyclic);    // input checks; acyclic: also acyclicity, max depth, range
 int build_edge_list(Handle& h);                 // init: canonical edge list from the CSR
 int build_tree_layout(Handle& h);               // init: preorder labels, Euler tour, relabelled edges and parents
 int tree_scan_workspace(Handle& h);             // init: look-back space of the tree scan

@@ -23,6 +23,7 @@
 // y's row), cut at each root, list ranking by pointer jumping, the preorder
 // rank of every down arc from a prefix count over the tour.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 #include <vector>
 
@@ -55,10 +56,14 @@ __global__ void k_lay_cut(const int32_t* __restrict__ parent, const int64_t* __r
 // Position of every arc in the concatenated tour (graph g's tour starts at
 // 2 (vtx_ptr[g] - g)), in original labels: y for x->y when x is y's parent
 // (down), ~x otherwise (up, leaving x); dflag marks the down arcs.
+// An arc whose list did not end after the ranking rounds lies on a tour that
+// no root cut: a cycle of parent links away from the root.  Such an arc, or a
+// position outside its graph's tour, marks the tree bad and is not written.
 __global__ void k_lay_arcs(const int32_t* __restrict__ tadj, const int64_t* __restrict__ tptr,
                            const int32_t* __restrict__ parent, const int32_t* __restrict__ rd,
-                           const int64_t* __restrict__ vtx_ptr, int32_t G, int64_t n, int32_t* __restrict__ tour,
-                           int32_t* __restrict__ dflag) {
+                           const int32_t* __restrict__ succ, const int64_t* __restrict__ vtx_ptr, int32_t G,
+                           int64_t n, int32_t* __restrict__ tour, int32_t* __restrict__ dflag,
+                           int32_t* __restrict__ bad) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = tptr[x], e = tptr[x + 1];
     if (b == e) continue;
@@ -67,6 +72,10 @@ __global__ void k_lay_arcs(const int32_t* __restrict__ tadj, const int64_t* __re
     const int64_t base = 2 * (vtx_ptr[g] - g);
     for (int64_t a = b; a < e; a++) {
       const int32_t y = tadj[a];
+      if (succ[a] != -1 || rd[a] < 0 || rd[a] >= len) {
+        *bad = 1;
+        continue;
+      }
       const int64_t pos = base + len - 1 - rd[a];
       const bool down = parent[y] == (int32_t)x;
       tour[pos] = down ? y : ~(int32_t)x;
@@ -87,6 +96,18 @@ __global__ void k_lay_pre(const int32_t* __restrict__ tour, const int64_t* __res
     const int32_t g = (G == 1) ? 0 : part_of(vtx_ptr, G, y);
     pre_of[y] = (int32_t)(dpre[p] + g + 1);
   }
+}
+
+// the largest hop depth: after the down arc at tour position p the depth is
+// (down arcs up to p) - (up arcs before p) = 2 dpre[p] + 1 - p (every graph's
+// tour starts after as many down arcs as its offset counts)
+__global__ void k_lay_depth(const int32_t* __restrict__ tour, const int64_t* __restrict__ dpre, int64_t A,
+                            DevScalars* dsc) {
+  long long mx = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A; p += (int64_t)gridDim.x * blockDim.x)
+    if (tour[p] >= 0) mx = max(mx, (long long)(2 * dpre[p] + 1 - p));
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax((long long*)&dsc->max_depth, mx);
 }
 
 __global__ void k_lay_roots(const int32_t* __restrict__ parent, const int64_t* __restrict__ vtx_ptr, int32_t G,
@@ -173,10 +194,23 @@ int build_tree_layout(Handle& h) {
       (st = device_alloc(h, (void**)&h.vtx_of_pre, sizeof(int32_t) * (size_t)n)) ||
       (st = device_alloc(h, (void**)&h.P, sizeof(u128) * (size_t)n)))
     return st;
-  // range-minimum levels: level j + 1 holds the minima of the 32-entry groups of level j, up to one group
+  // range-minimum levels: level j + 1 holds the minima of the 32-entry groups of level j, up to one group;
+  // when level 2 is small enough, it and everything above it is one sparse table instead
   h.rmq_levels = 0;
+  h.rmq_st = nullptr;
+  h.rmq_st_rows = 0;
   for (int64_t sz = n;; sz = (sz + 31) / 32) {
     if (h.rmq_levels >= kRmqMaxLevels) return PDG_E_INVALID_ARG;
+    if (h.rmq_levels == 2 && sz <= kRmqStMax) {
+      int rows = 1;
+      while ((1ll << rows) <= sz) rows++;  // rows t = 0 .. floor(log2 sz)
+      if ((st = device_alloc(h, (void**)&h.rmq_st, sizeof(uint64_t) * (size_t)sz * rows))) return st;
+      h.rmq_st_rows = rows;
+      h.rmq_size[2] = sz;
+      h.rmq_val[2] = h.rmq_st;  // row 0: the level-2 entries themselves
+      h.rmq_levels = 3;
+      break;
+    }
     h.rmq_size[h.rmq_levels] = sz;
     if ((st = device_alloc(h, (void**)&h.rmq_val[h.rmq_levels], sizeof(uint64_t) * (size_t)sz)) ||
         (st = device_alloc(h, (void**)&h.rmq_mask[h.rmq_levels], sizeof(uint32_t) * (size_t)sz)))
@@ -225,18 +259,27 @@ int build_tree_layout(Handle& h) {
       k_st_rank<<<ga, kBlock, 0, s>>>(succ[c], rd[c], succ[c ^ 1], rd[c ^ 1], tptr, n);
       c ^= 1;
     }
-    k_lay_arcs<<<gn, kBlock, 0, s>>>(tadj, tptr, h.parent, rd[c], h.d_vtx_ptr, G, n, h.tour, dflag);
+    k_lay_arcs<<<gn, kBlock, 0, s>>>(tadj, tptr, h.parent, rd[c], succ[c], h.d_vtx_ptr, G, n, h.tour, dflag, bad);
     if ((st = ensure_scan_status(h, A)) || (st = scan_excl_i32(h, dflag, dpre, A, nullptr, A))) return fail(st);
     k_lay_pre<<<ga, kBlock, 0, s>>>(h.tour, dpre, A, h.d_vtx_ptr, G, pre_of);
+    LAY_CK(cudaMemsetAsync(&h.dsc->max_depth, 0, sizeof(int64_t), s));
+    k_lay_depth<<<ga, kBlock, 0, s>>>(h.tour, dpre, A, h.dsc);
   }
   k_lay_roots<<<gn, kBlock, 0, s>>>(h.parent, h.d_vtx_ptr, G, n, pre_of);
   k_lay_vertices<<<gn, kBlock, 0, s>>>(pre_of, h.parent, n, h.vtx_of_pre, parent_pre, h.P, h.rmq_val[0], bad);
   if (A > 0) k_lay_tour<<<ga, kBlock, 0, s>>>(h.tour, pre_of, A, n, bad);
   {
     int32_t hbad = 0;
+    if (A == 0) LAY_CK(cudaMemsetAsync(&h.dsc->max_depth, 0, sizeof(int64_t), s));
     LAY_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LAY_CK(cudaMemcpyAsync(h.hsc, h.dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     LAY_CK(cudaStreamSynchronize(s));
-    if (hbad) return fail(PDG_E_NOT_A_TREE);  // validation admitted a tree the tour does not cover
+    if (hbad) return fail(PDG_E_NOT_A_TREE);  // the parent links are not a tree the tour covers (a cycle)
+    // the fixed-point range of the exact root distances: 2^(e_max - e_min + 53) per edge, max_depth edges
+    h.max_depth = h.hsc->max_depth;
+    int dep_bits = 0;
+    while ((1ll << dep_bits) <= h.max_depth) dep_bits++;
+    if (h.hsc->e_max != INT_MIN && h.hsc->e_max - h.hsc->e_min + 53 + dep_bits > 96) return fail(PDG_E_RANGE);
   }
   if (m > 0) k_lay_edges<<<gm, kBlock, 0, s>>>(h.el_u, h.el_v, pre_of, m);
   LAY_CK(cudaMemcpyAsync(h.parent, parent_pre, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));

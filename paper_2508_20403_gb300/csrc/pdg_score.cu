@@ -37,6 +37,8 @@ struct ScoreArgs {
   const uint32_t* mask[kRmqMaxLevels];
   const uint64_t* pmin[kRmqMaxLevels];
   const uint64_t* smin[kRmqMaxLevels];
+  const uint64_t* st;  // level 2 and up as a sparse table (null: as levels)
+  int64_t st_n;        // its row length (the level-2 entries)
   int S;
   int score_mode;
   uint32_t n;
@@ -50,8 +52,10 @@ struct ScoreArgs {
 // holds the query range [a_j, b_j].  If both ends share a group the range is
 // answered there by its mask and one key; otherwise the tail of a_j's group
 // (smin) and the head of b_j's group (pmin) are single loads, and the groups
-// strictly between become the range of level j + 1.  Every address depends
-// only on (lo, hi), so all loads but the last key are issued together.
+// strictly between become the range of level j + 1.  When level 2 and up are
+// one sparse table, a range that reaches level 2 is answered there by two
+// loads.  Every address depends only on (lo, hi), so all loads but the last
+// key are issued together.
 __device__ __forceinline__ uint64_t range_min(const ScoreArgs& A, uint32_t lo, uint32_t hi) {
   uint64_t best = ~0ull;
   bool done = false;
@@ -59,6 +63,12 @@ __device__ __forceinline__ uint64_t range_min(const ScoreArgs& A, uint32_t lo, u
   int fj = -1;
 #pragma unroll
   for (int j = 0; j < kRmqMaxLevels; j++) {
+    if (!done && j == 2 && A.st) {  // the rest of the range, on level 2, from two entries of the sparse table
+      const int t = 31 - __clz(hi - lo + 1);
+      const uint64_t* row = A.st + (int64_t)t * A.st_n;
+      best = min(best, min(__ldg(row + lo), __ldg(row + hi + 1 - (1u << t))));
+      done = true;
+    }
     if (!done) {
       if ((lo >> 5) == (hi >> 5)) {
         fa = lo;
@@ -162,6 +172,8 @@ int step_score(Handle& h, int score_mode) {
     A.pmin[j] = h.rmq_pmin[jj];
     A.smin[j] = h.rmq_smin[jj];
   }
+  A.st = h.rmq_st;
+  A.st_n = h.rmq_st ? h.rmq_size[2] : 0;
   A.score_mode = score_mode;
   A.n = (uint32_t)h.n;
   A.err = &h.dsc->err;

@@ -207,6 +207,8 @@ struct RmqArgs {
   int64_t size[kRmqMaxLevels];
   int levels;
   uint32_t* done;  // blocks finished (the last one resets it)
+  uint64_t* st;    // level 2 and up as one sparse table (null: as levels)
+  int st_rows;
 };
 
 // entries [base, base + len) of one level (len <= kRmqChunk, base a multiple
@@ -305,6 +307,31 @@ __device__ void rmq_chunk(const uint64_t* __restrict__ val, int64_t size, int64_
   __syncthreads();
 }
 
+// Level 2 and up as a sparse table: row t holds the minimum of the 2^t entries from each position, so any range
+// [lo, hi] of level 2 is the smaller of two entries of row floor(log2(hi - lo + 1)).  Row 0 is level 2 itself
+// (written by the blocks as their level-1 group minima); each further row comes from the one before, kept in
+// shared memory (two rows of at most kRmqStMax entries), and is stored as it is made.
+__device__ void rmq_sparse_table(const RmqArgs& a, uint64_t* buf) {
+  const int64_t n2 = a.size[2];
+  uint64_t* cur = buf;
+  uint64_t* nxt = buf + kRmqStMax;
+  for (int64_t i = threadIdx.x; i < n2; i += kRmqThreads) cur[i] = __ldcg(a.st + i);
+  __syncthreads();
+  for (int r = 1; r < a.st_rows; r++) {
+    const int64_t h = 1ll << (r - 1);
+    uint64_t* row = a.st + (int64_t)r * n2;
+    for (int64_t i = threadIdx.x; i + 2 * h <= n2; i += kRmqThreads) {
+      const uint64_t x = min(cur[i], cur[i + h]);
+      nxt[i] = x;
+      row[i] = x;
+    }
+    __syncthreads();
+    uint64_t* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+}
+
 __global__ void __launch_bounds__(kRmqThreads, 2) k_rmq_build(RmqArgs a) {
   extern __shared__ __align__(16) unsigned char rmq_smem[];
   RmqSmem& sm = *reinterpret_cast<RmqSmem*>(rmq_smem);
@@ -334,6 +361,10 @@ __global__ void __launch_bounds__(kRmqThreads, 2) k_rmq_build(RmqArgs a) {
       __syncthreads();
       if (!s_last) return;
       __threadfence();
+      if (a.st) {  // uniform: the sparse table over level 2, two rows at a time in shared memory
+        rmq_sparse_table(a, reinterpret_cast<uint64_t*>(&sm));
+        break;
+      }
       tail = true;
       j = 2;
       base = 0;
@@ -381,6 +412,8 @@ int step_tree(Handle& h) {
     r.size[j] = h.rmq_size[j];
   }
   r.levels = h.rmq_levels;
+  r.st = h.rmq_st;
+  r.st_rows = h.rmq_st_rows;
   r.done = h.ts_done;
   PDG_CUDA(rmq_smem_attr());
   ++h.launches;

@@ -5,10 +5,10 @@
 // Checks: CSR shape (monotone row_ptr, columns in range, no self loops,
 // strictly increasing neighbours), symmetric weights (bitwise), weights in
 // [2^-900, 2^900], no edge between two graphs of a batch, parent[] with one
-// root per graph whose links are edges of G and acyclic (pointer jumping must
-// terminate within bit_length(n) + 1 rounds), and the fixed-point range of
-// the exact root distances.  The maximum hop depth found here sets the number
-// of pointer-jumping rounds of the tree step.
+// root per graph whose links are edges of G and acyclic, and the fixed-point
+// range of the exact root distances.  Acyclicity and the maximum hop depth
+// (which sets that range) come from pointer jumping here for the callers that
+// build no tree layout; sparsify_init takes both from the layout's Euler tour.
 #include <climits>
 #include <cmath>
 
@@ -27,6 +27,10 @@ __global__ void k_val_rowptr(const int64_t* __restrict__ row_ptr, int64_t n, Dev
     if (row_ptr[u] > row_ptr[u + 1]) atomicOr(&dsc->err, ERR_NOT_CSR);
 }
 
+// Every thread takes kValRun consecutive entries: one search for the row of the
+// first, then the row advances with the entries.
+constexpr int kValRun = 8;
+
 __global__ void __launch_bounds__(kBlock) k_val_entries(const int64_t* __restrict__ row_ptr,
                                                         const int32_t* __restrict__ col,
                                                         const double* __restrict__ w, int64_t n, int64_t nnz,
@@ -34,8 +38,11 @@ __global__ void __launch_bounds__(kBlock) k_val_entries(const int64_t* __restric
                                                         DevScalars* dsc) {
   const double lo = ldexp(1.0, -900), hi = ldexp(1.0, 900);
   int err = 0;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t u = row_of(row_ptr, n, p);
+  for (int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kValRun; p0 < nnz;
+       p0 += (int64_t)gridDim.x * blockDim.x * kValRun) {
+    int64_t u = row_of(row_ptr, n, p0);
+    for (int64_t p = p0; p < p0 + kValRun && p < nnz; p++) {
+    while (row_ptr[u + 1] <= p) u++;  // empty rows are passed over (row_ptr is monotone: checked before)
     const int32_t v = col[p];
     const double x = w[p];
     if (!(x >= lo && x <= hi)) err |= ERR_BAD_WEIGHT;
@@ -49,6 +56,7 @@ __global__ void __launch_bounds__(kBlock) k_val_entries(const int64_t* __restric
     const int64_t q = lower_bound_i32(col, b, e, (int32_t)u);
     if (q >= e || col[q] != (int32_t)u || __double_as_longlong(w[q]) != __double_as_longlong(x))
       err |= ERR_NOT_SYMMETRIC;
+    }
   }
   if (err) atomicOr(&dsc->err, err);
 }
@@ -151,7 +159,7 @@ int validate_csr(Handle& h) {
   return PDG_OK;
 }
 
-int validate_graph(Handle& h) {
+int validate_graph(Handle& h, bool acyclic) {
   const int64_t n = h.n;
   const int grid = grid_for(h, std::max<int64_t>(n, h.nnz));
   // read the device scalars back on the handle's stream (no legacy-stream sync)
@@ -195,8 +203,9 @@ int validate_graph(Handle& h) {
   int err = h.hsc->err;
   for (int64_t r : roots_h)
     if (r != 1) err |= ERR_NOT_A_TREE;
-  if (!(err & (ERR_NOT_CSR | ERR_BAD_WEIGHT | ERR_NOT_A_TREE | ERR_CROSS_GRAPH))) {
-    // acyclicity and depth by pointer jumping
+  if (acyclic && !(err & (ERR_NOT_CSR | ERR_BAD_WEIGHT | ERR_NOT_A_TREE | ERR_CROSS_GRAPH))) {
+    // acyclicity and depth by pointer jumping (sparsify_init leaves both to the tree layout, whose Euler tour
+    // reaches every vertex only if the parent links are acyclic, and checks the fixed-point range there)
     int bits = 0;
     while ((1ll << bits) <= n) bits++;
     int cur = 0;

@@ -250,6 +250,34 @@ def test_init_rejects_bad_inputs(B):
     assert _init_status(B, g.n, rp, bc, w, par) == B.PDG_E_NOT_CSR
 
 
+def test_init_rejects_parent_cycles(B):
+    """Parent links that are edges of G but close a cycle away from the root (one root, every link an edge): no
+    root cuts the Euler tour of the cycle's component, so the layout's list ranking leaves it unterminated and
+    sparsify_init reports the parents as not a tree -- for a 2-cycle, a 4-cycle, and a batch member."""
+    g = W.grid_graph(8)
+    par = g.parent.copy()
+    x = next(v for v in range(g.n) if par[v] >= 0 and par[par[v]] >= 0)
+    bad = par.copy()
+    bad[par[x]] = x  # x and its parent point at each other
+    assert _init_status(B, g.n, g.row_ptr, g.col, g.w, bad) == B.PDG_E_NOT_A_TREE
+    root = int(np.flatnonzero(par < 0)[0])
+    a = next(v for v in range(g.n - 9) if v % 8 < 7 and root not in (v, v + 1, v + 9, v + 8))
+    bad = par.copy()
+    for u, v in ((a, a + 1), (a + 1, a + 9), (a + 9, a + 8), (a + 8, a)):  # a grid square
+        bad[u] = v
+    assert _init_status(B, g.n, g.row_ptr, g.col, g.w, bad) == B.PDG_E_NOT_A_TREE
+    graphs = [W.grid_graph(6), W.grid_graph(5), W.grid_graph(7)]
+    h = graphs[1]
+    y = next(v for v in range(h.n) if h.parent[v] >= 0 and h.parent[h.parent[v]] >= 0)
+    hp = h.parent.copy()
+    hp[h.parent[y]] = y
+    graphs[1] = W.Graph(n=h.n, row_ptr=h.row_ptr, col=h.col, w=h.w, parent=hp, name="cycle")
+    pk = W.pack_graphs(graphs)
+    with pytest.raises(B.PdgError) as e:
+        B.BatchSparsifier.from_packed(pk)
+    assert e.value.status == B.PDG_E_NOT_A_TREE
+
+
 def test_range_error(B):
     # a path 0-1-2 with resistances 2^900 and 2^-900 cannot share one 96-bit fixed point
     from tests.helpers import graph_from_edges
