@@ -20,7 +20,8 @@
 //
 // Construction: tree adjacency with reverse arcs, rows sorted (so the tour is
 // deterministic), the tour successor (after x->y the arc following y->x in
-// y's row), cut at each root, list ranking by pointer jumping, the preorder
+// y's row), cut at each root, list ranking by pointer jumping (one packed
+// word per arc), the preorder
 // rank of every down arc from a prefix count over the tour.
 #include <algorithm>
 #include <climits>
@@ -56,14 +57,34 @@ __global__ void k_lay_cut(const int32_t* __restrict__ parent, const int64_t* __r
 // Position of every arc in the concatenated tour (graph g's tour starts at
 // 2 (vtx_ptr[g] - g)), in original labels: y for x->y when x is y's parent
 // (down), ~x otherwise (up, leaving x); dflag marks the down arcs.
+// List ranking by pointer jumping on one packed word per arc, (successor << 32) | arcs to the end: one
+// gather per arc and round instead of two.
+__global__ void k_lay_pack(const int32_t* __restrict__ succ, const int32_t* __restrict__ rd, int64_t A,
+                           uint64_t* __restrict__ out) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (int64_t)gridDim.x * blockDim.x)
+    out[a] = ((uint64_t)(uint32_t)succ[a] << 32) | (uint32_t)rd[a];
+}
+
+__global__ void k_lay_rank(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t A) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = in[a];
+    const int32_t s = (int32_t)(w >> 32);
+    if (s < 0) {
+      out[a] = w;
+    } else {
+      const uint64_t x = in[s];
+      out[a] = (x & 0xffffffff00000000ull) | (uint32_t)((uint32_t)w + (uint32_t)x);
+    }
+  }
+}
+
 // An arc whose list did not end after the ranking rounds lies on a tour that
 // no root cut: a cycle of parent links away from the root.  Such an arc, or a
 // position outside its graph's tour, marks the tree bad and is not written.
 __global__ void k_lay_arcs(const int32_t* __restrict__ tadj, const int64_t* __restrict__ tptr,
-                           const int32_t* __restrict__ parent, const int32_t* __restrict__ rd,
-                           const int32_t* __restrict__ succ, const int64_t* __restrict__ vtx_ptr, int32_t G,
-                           int64_t n, int32_t* __restrict__ tour, int32_t* __restrict__ dflag,
-                           int32_t* __restrict__ bad) {
+                           const int32_t* __restrict__ parent, const uint64_t* __restrict__ ranked,
+                           const int64_t* __restrict__ vtx_ptr, int32_t G, int64_t n, int32_t* __restrict__ tour,
+                           int32_t* __restrict__ dflag, int32_t* __restrict__ bad) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = tptr[x], e = tptr[x + 1];
     if (b == e) continue;
@@ -72,11 +93,12 @@ __global__ void k_lay_arcs(const int32_t* __restrict__ tadj, const int64_t* __re
     const int64_t base = 2 * (vtx_ptr[g] - g);
     for (int64_t a = b; a < e; a++) {
       const int32_t y = tadj[a];
-      if (succ[a] != -1 || rd[a] < 0 || rd[a] >= len) {
+      const int32_t succ = (int32_t)(ranked[a] >> 32), rd = (int32_t)(uint32_t)ranked[a];
+      if (succ != -1 || rd < 0 || rd >= len) {
         *bad = 1;
         continue;
       }
-      const int64_t pos = base + len - 1 - rd[a];
+      const int64_t pos = base + len - 1 - rd;
       const bool down = parent[y] == (int32_t)x;
       tour[pos] = down ? y : ~(int32_t)x;
       dflag[pos] = down ? 1 : 0;
@@ -224,12 +246,13 @@ int build_tree_layout(Handle& h) {
   }
   uint8_t* tflag = nullptr;
   int32_t *tdeg = nullptr, *cur = nullptr, *tadj = nullptr, *rev = nullptr, *arc_uv = nullptr, *dflag = nullptr;
-  int32_t *succ[2] = {nullptr, nullptr}, *rd[2] = {nullptr, nullptr}, *pre_of = nullptr, *parent_pre = nullptr;
+  int32_t *succ = nullptr, *rd = nullptr, *pre_of = nullptr, *parent_pre = nullptr;
+  uint64_t* ranked[2] = {nullptr, nullptr};
   int64_t *tptr = nullptr, *dpre = nullptr;
   int32_t* bad = nullptr;
   if (!talloc(&tflag, m) || !talloc(&tdeg, n) || !talloc(&cur, n) || !talloc(&tptr, n + 1) || !talloc(&tadj, A) ||
-      !talloc(&rev, A) || !talloc(&arc_uv, m) || !talloc(&succ[0], A) || !talloc(&succ[1], A) || !talloc(&rd[0], A) ||
-      !talloc(&rd[1], A) || !talloc(&dflag, A) || !talloc(&dpre, A + 1) || !talloc(&pre_of, n) ||
+      !talloc(&rev, A) || !talloc(&arc_uv, m) || !talloc(&succ, A) || !talloc(&rd, A) || !talloc(&ranked[0], A) ||
+      !talloc(&ranked[1], A) || !talloc(&dflag, A) || !talloc(&dpre, A + 1) || !talloc(&pre_of, n) ||
       !talloc(&parent_pre, n) || !talloc(&bad, 1))
     return fail(PDG_E_OOM);
 #define LAY_CK(x)                                    \
@@ -250,16 +273,17 @@ int build_tree_layout(Handle& h) {
     k_st_fill<<<gm, kBlock, 0, s>>>(h.el_u, h.el_v, tflag, m, tptr, cur, tadj, rev, arc_uv);
     k_tour_sort_rows<<<gn, kBlock, 0, s>>>(tptr, n, tadj);
     k_tour_fix_rev<<<gn, kBlock, 0, s>>>(tptr, tadj, n, rev);
-    k_st_succ<<<ga, kBlock, 0, s>>>(tadj, rev, tptr, tdeg, n, succ[0], rd[0]);
-    k_lay_cut<<<gn, kBlock, 0, s>>>(h.parent, tptr, tdeg, rev, n, succ[0], rd[0]);
+    k_st_succ<<<ga, kBlock, 0, s>>>(tadj, rev, tptr, tdeg, n, succ, rd);
+    k_lay_cut<<<gn, kBlock, 0, s>>>(h.parent, tptr, tdeg, rev, n, succ, rd);
+    k_lay_pack<<<ga, kBlock, 0, s>>>(succ, rd, A, ranked[0]);
     int bits = 1;
     while ((1ll << bits) <= A) bits++;
     int c = 0;
     for (int it = 0; it < bits; it++) {
-      k_st_rank<<<ga, kBlock, 0, s>>>(succ[c], rd[c], succ[c ^ 1], rd[c ^ 1], tptr, n);
+      k_lay_rank<<<ga, kBlock, 0, s>>>(ranked[c], ranked[c ^ 1], A);
       c ^= 1;
     }
-    k_lay_arcs<<<gn, kBlock, 0, s>>>(tadj, tptr, h.parent, rd[c], succ[c], h.d_vtx_ptr, G, n, h.tour, dflag, bad);
+    k_lay_arcs<<<gn, kBlock, 0, s>>>(tadj, tptr, h.parent, ranked[c], h.d_vtx_ptr, G, n, h.tour, dflag, bad);
     if ((st = ensure_scan_status(h, A)) || (st = scan_excl_i32(h, dflag, dpre, A, nullptr, A))) return fail(st);
     k_lay_pre<<<ga, kBlock, 0, s>>>(h.tour, dpre, A, h.d_vtx_ptr, G, pre_of);
     LAY_CK(cudaMemsetAsync(&h.dsc->max_depth, 0, sizeof(int64_t), s));

@@ -84,7 +84,7 @@ static_assert(kPickPer == 16, "pick layout");
 
 __global__ void __launch_bounds__(kBlock) k_sel_pick(uint32_t* __restrict__ hist, GraphSel* __restrict__ sel,
                                                      const int64_t* __restrict__ off_ptr, int32_t G, int lvl,
-                                                     int64_t* __restrict__ count_out) {
+                                                     int64_t* __restrict__ count_out, int64_t* __restrict__ cand_ptr) {
   __shared__ int64_t sm[kBlock / 32 + 1];
   __shared__ int s_owner;
   const int32_t g = blockIdx.x;
@@ -96,6 +96,10 @@ __global__ void __launch_bounds__(kBlock) k_sel_pick(uint32_t* __restrict__ hist
       s.thresh = 0;
       sel[g] = s;
       count_out[g] = s.count;
+      if (G == 1) {  // a single graph's candidate offsets need no scan
+        cand_ptr[0] = 0;
+        cand_ptr[1] = s.count;
+      }
     }
     return;
   }
@@ -147,6 +151,10 @@ __global__ void __launch_bounds__(kBlock) k_sel_pick(uint32_t* __restrict__ hist
       s.count = s.above1 + run + bin_count;
       s.thresh = ((uint64_t)s.b1 << 52) | ((uint64_t)bin << 40);
       count_out[g] = s.count;
+      if (G == 1) {
+        cand_ptr[0] = 0;
+        cand_ptr[1] = s.count;
+      }
     }
     sel[g] = s;
   }
@@ -156,21 +164,27 @@ __global__ void __launch_bounds__(kBlock) k_sel_pick(uint32_t* __restrict__ hist
 }
 
 // Ordered compaction of the selected edges (key >= the graph's threshold), in
-// canonical id order: a count pass per block chunk, a scan of the block
-// counts, and a write pass that places each tile's selected edges by a block
-// scan.  Both passes stream the keys with vector loads.
+// canonical id order: a count pass per block chunk, then a write pass whose
+// blocks add up the counts of the blocks before them and place each tile's
+// selected edges by a block scan.  Both passes stream the keys with vector
+// loads.
 template <bool WRITE>
 __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restrict__ key, int64_t E,
                                                         const int64_t* __restrict__ off_ptr, int32_t G,
                                                         const GraphSel* __restrict__ sel,
-                                                        int64_t* __restrict__ bcount, const int64_t* __restrict__ boff,
-                                                        int64_t cap, int32_t* __restrict__ cand_idx,
+                                                        int64_t* __restrict__ bcount, int64_t cap,
+                                                        int32_t* __restrict__ cand_idx,
                                                         uint64_t* __restrict__ rkey, int32_t* __restrict__ rval) {
   __shared__ int64_t sm[kBlock / 32 + 1];
   const int64_t chunk = sel_chunk(E, gridDim.x);
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(E, b0 + chunk);
-  int64_t run = WRITE ? boff[blockIdx.x] : 0;
+  int64_t run = 0;
+  if (WRITE) {  // this block's offset: the counts of the blocks before it, added up here (no separate scan)
+    int64_t c = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += kBlock) c += bcount[i];
+    run = block_sum(c, sm);
+  }
   int64_t tot = 0;
   for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
     const int64_t base = t0 + (int64_t)threadIdx.x * kItems;
@@ -232,9 +246,14 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
   }
 }
 
-__global__ void k_sel_total(const int64_t* __restrict__ total_p, const int64_t* __restrict__ cand_ptr, int32_t G,
-                            int64_t cap, DevScalars* dsc) {
-  const int64_t total = *total_p;
+__global__ void __launch_bounds__(kBlock) k_sel_total(const int64_t* __restrict__ bcount, int nb,
+                                                      const int64_t* __restrict__ cand_ptr, int32_t G, int64_t cap,
+                                                      DevScalars* dsc) {
+  __shared__ int64_t sm[kBlock / 32 + 1];
+  int64_t c = 0;
+  for (int i = threadIdx.x; i < nb; i += kBlock) c += bcount[i];
+  const int64_t total = block_sum(c, sm);
+  if (threadIdx.x != 0) return;
   dsc->n_cand_wanted = total;
   if (total > cap || total != cand_ptr[G]) {
     // nothing downstream may touch more than `cap` candidates: run it empty
@@ -259,23 +278,20 @@ int step_select(Handle& h) {
       k_sel_hist<<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, lvl, h.hist);
     }
     ++h.launches;
-    k_sel_pick<<<h.G, kBlock, 0, h.stream>>>(h.hist, h.sel, h.d_off_ptr, h.G, lvl, h.d_graph_tmp);
+    k_sel_pick<<<h.G, kBlock, 0, h.stream>>>(h.hist, h.sel, h.d_off_ptr, h.G, lvl, h.d_graph_tmp, h.d_cand_ptr);
   }
   PDG_CUDA(cudaGetLastError());
-  int st = scan_excl_i64(h, h.d_graph_tmp, h.d_cand_ptr, h.G, nullptr, h.G);
-  if (st) return st;
+  int st;
+  if (h.G > 1 && (st = scan_excl_i64(h, h.d_graph_tmp, h.d_cand_ptr, h.G, nullptr, h.G))) return st;
   int64_t* bcount = h.blk_a;
-  int64_t* boff = h.blk_a + 2560;  // [0, nb]: block offsets, boff[nb] = total
   ++h.launches;
-  k_sel_compact<false><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, nullptr, 0, nullptr,
-                                                    nullptr, nullptr);
-  if ((st = scan_excl_i64(h, bcount, boff, nb, nullptr, nb))) return st;
+  k_sel_compact<false><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, 0, nullptr, nullptr,
+                                                    nullptr);
   ++h.launches;
-  k_sel_compact<true><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, nullptr, boff, h.Rcap,
-                                                   h.cand_idx, h.rk[0], h.rv[0]);
-  int64_t* total = boff + nb;
+  k_sel_compact<true><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, h.Rcap, h.cand_idx,
+                                                   h.rk[0], h.rv[0]);
   ++h.launches;
-  k_sel_total<<<1, 1, 0, h.stream>>>(total, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
+  k_sel_total<<<1, kBlock, 0, h.stream>>>(bcount, nb, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
