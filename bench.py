@@ -866,8 +866,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-pool", type=int, default=128)
-    ap.add_argument("--serve-high-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-high-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-high-rate", type=float, default=1500.0)
+    ap.add_argument("--serve-high-seconds", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-mem-gb", type=int, default=32)
     args = ap.parse_args()
