@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(kBlock) k_build_records(
     int c, const DevScalars* __restrict__ dsc, int64_t cap, int32_t* __restrict__ rec_u, int32_t* __restrict__ rec_v,
     int32_t* __restrict__ rec_anc, int32_t* __restrict__ rec_du, int32_t* __restrict__ rec_dv,
     uint8_t* __restrict__ rec_b, int32_t* __restrict__ rec_rank, int32_t* __restrict__ rec_lca) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_build_records(
 __global__ void __launch_bounds__(kLbThreads) k_seg_starts(const int32_t* __restrict__ rec_lca, DevScalars* dsc,
                                                           int32_t* __restrict__ seg_begin, uint64_t* status,
                                                           uint32_t* ctr, int64_t spin_limit) {
+  dep_sync();
   __shared__ int64_t sm[kLbThreads / 32 + 1];
   __shared__ int64_t s_tile, s_excl;
   __shared__ int s_last;
@@ -236,6 +238,7 @@ __global__ void k_seg_tier(const int32_t* __restrict__ seg_begin, DevScalars* ds
                            int32_t* __restrict__ warp_seg, int32_t* __restrict__ block_seg,
                            int32_t* __restrict__ big_seg, int64_t* __restrict__ big_chunk,
                            int64_t* __restrict__ seg_regs) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t S = dsc->n_seg;
   const int lane = threadIdx.x & 31;
@@ -292,6 +295,7 @@ __global__ void k_big_positions(const int64_t* __restrict__ big_chunk, const int
                                 const uint8_t* __restrict__ rec_b, int32_t* __restrict__ big_pos,
                                 uint8_t* __restrict__ state, int32_t* __restrict__ pos_x,
                                 int64_t* __restrict__ seg_regs) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t nch = dsc->n_big_chunk;
   const int lane = threadIdx.x & 31;
@@ -328,6 +332,7 @@ __global__ void __launch_bounds__(kBlock) k_accept_warp(const int32_t* __restric
                                                         const DevScalars* __restrict__ dsc,
                                                         const int32_t* __restrict__ seg_begin, int c, RecArrays ra,
                                                         uint8_t* __restrict__ acc_flag) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t nw = dsc->n_warp_seg;
   const int lane = threadIdx.x & 31;
@@ -412,6 +417,7 @@ template <int C>
 __global__ void __launch_bounds__(32) k_accept_block(const int32_t* __restrict__ block_seg, DevScalars* dsc,
                                                      const int32_t* __restrict__ seg_begin, RecArrays ra,
                                                      int slots_log2, uint8_t* __restrict__ acc_flag) {
+  dep_sync();
   extern __shared__ __align__(16) unsigned char bt_smem[];
   uint64_t* keys = reinterpret_cast<uint64_t*>(bt_smem);
   uint32_t* slack = reinterpret_cast<uint32_t*>(keys + (1 << slots_log2));
@@ -591,6 +597,7 @@ __device__ __forceinline__ bool slot_flagged(const uint32_t* __restrict__ bits, 
 __global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ flagbits, DevScalars* dsc,
                              int64_t table_cap, uint64_t* __restrict__ cap_out, int64_t* __restrict__ n_flag,
                              int64_t* __restrict__ n_und, const int64_t* __restrict__ seg_pref) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   // slots of all subtask regions: twice the registrations (load <= 0.5) + 16 each
   const int64_t nbs = dsc->n_big_seg;
@@ -621,6 +628,7 @@ __global__ void k_coop_clear(PairSlot* __restrict__ tab, uint32_t* __restrict__ 
 // as many rounds as its longest chain, not for the sum of its chains.
 template <int C>
 __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScalars* dsc) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // e.g. the regions do not fit: the host retries with a larger table
   const int64_t nb = dsc->n_big, nbs = dsc->n_big_seg;
   bool bad = false;
@@ -677,6 +685,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_pair_register(CoopArgs a, DevScal
 // together, one slot per round, like the inserts of phase A1.
 template <int C>
 __global__ void __launch_bounds__(kBlock, 4) k_pair_probe(CoopArgs a, DevScalars* dsc) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // e.g. the regions do not fit: the host retries with a larger table
   const int64_t nb = dsc->n_big, nbs = dsc->n_big_seg;
   bool bad = false;
@@ -921,6 +930,7 @@ __device__ __forceinline__ int exact_probe(const CoopArgs& a, int32_t s, const R
 // indices.
 template <int C>
 __global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalars* dsc) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0) return;
   const int64_t nb = dsc->n_big;
@@ -949,6 +959,7 @@ __global__ void __launch_bounds__(kBlock) k_exact_register(CoopArgs a, DevScalar
 // only settles the prober earlier.
 template <int C>
 __global__ void __launch_bounds__(kBlock) k_exact_round(CoopArgs a, DevScalars* dsc, int round) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0) return;
   if (round > 1 && a.und_count[round - 1] == 0) return;
@@ -982,6 +993,7 @@ __global__ void __launch_bounds__(kBlock) k_exact_round(CoopArgs a, DevScalars* 
 template <int C>
 __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __restrict__ big_seg,
                                const int32_t* __restrict__ seg_begin, int last_round) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_constrained == 0 || a.und_count[last_round] == 0) return;
   const int64_t ns = dsc->n_big_seg;
@@ -1006,6 +1018,7 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
 __global__ void k_big_flags(const int32_t* __restrict__ big_pos, const uint8_t* __restrict__ state,
                             const int32_t* __restrict__ rec_rank, const DevScalars* __restrict__ dsc,
                             uint8_t* __restrict__ acc_flag) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t nb = dsc->n_big;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
@@ -1018,20 +1031,20 @@ __global__ void k_big_flags(const int32_t* __restrict__ big_pos, const uint8_t* 
 template <int C>
 int run_coop(Handle& h, const CoopArgs& a, int grid, int rounds) {
   ++h.launches;
-  k_pair_register<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
+  launch_k(h, k_pair_register<C>, grid, kBlock, 0, a, h.dsc);
   ++h.launches;
-  k_pair_probe<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
+  launch_k(h, k_pair_probe<C>, grid, kBlock, 0, a, h.dsc);
   // round 1 registers every cooperative candidate; the rest of the rounds only
   // walk the (shorter) list of candidates phase A left undecided
   const int grid_und = std::max(1, h.num_sms * 2);
   ++h.launches;
-  k_exact_register<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc);
+  launch_k(h, k_exact_register<C>, grid, kBlock, 0, a, h.dsc);
   for (int r = 1; r <= rounds; r++) {
     ++h.launches;
-    k_exact_round<C><<<grid_und, kBlock, 0, h.stream>>>(a, h.dsc, r);
+    launch_k(h, k_exact_round<C>, grid_und, kBlock, 0, a, h.dsc, r);
   }
   ++h.launches;
-  k_exact_finish<C><<<grid, kBlock, 0, h.stream>>>(a, h.dsc, h.big_seg, h.seg_begin, rounds);
+  launch_k(h, k_exact_finish<C>, grid, kBlock, 0, a, h.dsc, h.big_seg, h.seg_begin, rounds);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
@@ -1067,23 +1080,23 @@ int step_accept(Handle& h, int c) {
   const int64_t cap = h.Rcap;
   int st;
   ++h.launches;
-  k_build_records<<<grid, kBlock, 0, h.stream>>>(h.lsort_rank, h.rank_cand, h.cand_idx, h.off_u, h.off_v, h.lca,
-                                                  h.P, h.parent, c, h.dsc, cap, h.rec_u, h.rec_v, h.rec_anc,
-                                                  h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.rec_lca);
+  launch_k(h, k_build_records, grid, kBlock, 0, h.lsort_rank, h.rank_cand, h.cand_idx, h.off_u, h.off_v, h.lca,
+           h.P, h.parent, c, h.dsc, cap, h.rec_u, h.rec_v, h.rec_anc,
+           h.rec_du, h.rec_dv, h.rec_b, h.rec_rank, h.rec_lca);
   // subtask boundaries, tier lists, per-position tiers
   const int64_t lb_tiles = (cap + kLbTile - 1) / kLbTile;
   if (lb_tiles > h.scan_tiles_cap || lb_tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized with the buffers
   ++h.launches;
-  k_seg_starts<<<(int)std::max<int64_t>(lb_tiles, 1), kLbThreads, 0, h.stream>>>(
-      h.rec_lca, h.dsc, h.seg_begin, h.scan_status, h.scan_ctr, h.opt.spin_limit);
+  launch_k(h, k_seg_starts, (int)std::max<int64_t>(lb_tiles, 1), kLbThreads, 0,
+           h.rec_lca, h.dsc, h.seg_begin, h.scan_status, h.scan_ctr, h.opt.spin_limit);
   ++h.launches;
   const int block_max = block_tier_max(h, c);
-  k_seg_tier<<<grid, kBlock, 0, h.stream>>>(h.seg_begin, h.dsc, h.opt.warp_tier_max, block_max, h.rec_rank,
-                                            h.acc_flag, h.warp_seg, h.block_seg, h.big_seg, h.big_chunk,
-                                            h.seg_regs);
+  launch_k(h, k_seg_tier, grid, kBlock, 0, h.seg_begin, h.dsc, h.opt.warp_tier_max, block_max, h.rec_rank,
+           h.acc_flag, h.warp_seg, h.block_seg, h.big_seg, h.big_chunk,
+           h.seg_regs);
   ++h.launches;
-  k_big_positions<<<grid, kBlock, 0, h.stream>>>(h.big_chunk, h.big_seg, h.seg_begin, h.dsc, h.rec_b, h.big_pos,
-                                                 h.state, h.pos_x, h.seg_regs);
+  launch_k(h, k_big_positions, grid, kBlock, 0, h.big_chunk, h.big_seg, h.seg_begin, h.dsc, h.rec_b, h.big_pos,
+           h.state, h.pos_x, h.seg_regs);
   PDG_CUDA(cudaGetLastError());
   // table regions of the cooperative subtasks
   if ((st = scan_excl_i64(h, h.seg_regs, h.seg_pref, 0, &h.dsc->n_big_seg, cap))) return st;
@@ -1096,6 +1109,7 @@ int step_accept(Handle& h, int c) {
   if (fork) {
     PDG_CUDA(cudaEventRecord(h.ev_fork, h.stream));
     PDG_CUDA(cudaStreamWaitEvent(h.sstream, h.ev_fork, 0));
+    stream_op(h);
   }
   // warp tier
   ++h.launches;
@@ -1121,6 +1135,7 @@ int step_accept(Handle& h, int c) {
   if (fork) PDG_CUDA(cudaEventRecord(h.ev_join, h.sstream));
   st = accept_coop(h, c, grid, ra);
   if (fork && cudaStreamWaitEvent(h.stream, h.ev_join, 0) != cudaSuccess && st == PDG_OK) st = PDG_E_CUDA;
+  stream_op(h);  // the next kernel waits for the side stream's tiers in full
   return st;
 }
 
@@ -1134,9 +1149,10 @@ static int accept_coop(Handle& h, int c, int grid, const RecArrays& ra) {
   int64_t* n_und = h.blk_a + 9802;
   const int R = coop_rounds(h, c);
   PDG_CUDA(cudaMemsetAsync(und_count, 0, sizeof(int64_t) * (R + 1), h.stream));
+  stream_op(h);
   ++h.launches;
-  k_coop_clear<<<grid, kBlock, 0, h.stream>>>(h.ptab, h.flagbits, h.dsc, h.table_cap, d_cap, n_flag, n_und,
-                                              h.seg_pref);
+  launch_k(h, k_coop_clear, grid, kBlock, 0, h.ptab, h.flagbits, h.dsc, h.table_cap, d_cap, n_flag, n_und,
+           h.seg_pref);
   const CoopArgs a{ra,        h.big_pos, h.state,   h.pmask,    h.reg_slot, h.pslot, h.ptab, h.xtab, h.xund1,
                    d_cap,     n_flag,    h.xcap,    und_count,  h.flagbits, h.und_list, n_und, h.pos_x,
                    h.seg_pref, h.dsc};
@@ -1148,7 +1164,7 @@ static int accept_coop(Handle& h, int c, int grid, const RecArrays& ra) {
   }
   if (st) return st;
   ++h.launches;
-  k_big_flags<<<grid, kBlock, 0, h.stream>>>(h.big_pos, h.state, h.rec_rank, h.dsc, h.acc_flag);
+  launch_k(h, k_big_flags, grid, kBlock, 0, h.big_pos, h.state, h.rec_rank, h.dsc, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

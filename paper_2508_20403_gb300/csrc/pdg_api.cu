@@ -116,6 +116,7 @@ __global__ void k_gather_rowptr(const int64_t* __restrict__ row_ptr, const int64
 }
 
 __global__ void k_reset_recover(DevScalars* dsc) {
+  dep_sync();
   dsc->err = 0;
   dsc->e_min = INT_MAX;
   dsc->e_max = INT_MIN;
@@ -123,6 +124,7 @@ __global__ void k_reset_recover(DevScalars* dsc) {
 }
 
 __global__ void k_reset_attempt(DevScalars* dsc) {
+  dep_sync();
   dsc->err &= ERR_RANGE | ERR_TIMEOUT | ERR_BOUNDS;  // errors of steps A1-A3 end the recovery
   dsc->epoch++;
   dsc->bounds_site = 0;
@@ -756,12 +758,16 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
     dev_scores = out_scores ? h.out_scores : nullptr;
   }
   h.launches = 0;
+  DepScope dep_scope(h);  // kernels of the recovery may launch as programmatic dependents
   const bool prof = h.opt.profile != 0;
   if (prof && !h.ev[0])
     for (cudaEvent_t& e : h.ev) PDG_CUDA(cudaEventCreate(&e));
   bool capturing = false;
   auto mark = [&](int i) {
-    if (prof && !capturing) cudaEventRecord(h.ev[i], h.stream);
+    if (prof && !capturing) {
+      cudaEventRecord(h.ev[i], h.stream);
+      stream_op(h);  // the steps timed apart do not overlap
+    }
   };
   float acc_ms[8] = {0};
   // Enqueue one attempt on h.stream: steps A1-A3 (first attempt only; they
@@ -769,6 +775,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
   bool any_select_cur = false;
   auto enqueue = [&](bool first) -> int {
     int e;
+    stream_op(h);  // the previous attempt ended with copies
     // a single graph's first selection histogram is taken by the scoring kernel itself
     h.fuse_hist = first && G == 1 && any_select_cur;
     if (first) {
@@ -776,7 +783,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
       PDG_CUDA(cudaMemcpyAsync(h.d_out_ptr, s.out_ptr, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, h.stream));
       mark(0);
       ++h.launches;
-      k_reset_recover<<<1, 1, 0, h.stream>>>(h.dsc);
+      launch_k(h, k_reset_recover, 1, 1, 0, h.dsc);
       if ((e = step_classify(h))) return e;
       mark(1);
       if ((e = step_tree(h))) return e;
@@ -785,8 +792,9 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
       mark(3);
     }
     ++h.launches;
-    k_reset_attempt<<<1, 1, 0, h.stream>>>(h.dsc);
+    launch_k(h, k_reset_attempt, 1, 1, 0, h.dsc);
     PDG_CUDA(cudaMemcpyAsync(h.sel, s.sel, sizeof(GraphSel) * G, cudaMemcpyHostToDevice, h.stream));
+    stream_op(h);
     mark(4);
     if ((e = step_select(h))) return e;
     mark(5);

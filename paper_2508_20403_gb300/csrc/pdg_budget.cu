@@ -16,6 +16,7 @@ __global__ void k_budget_graph(const int64_t* __restrict__ scan, const int64_t* 
                                const int64_t* __restrict__ kk, const GraphSel* __restrict__ sel, int32_t G,
                                int32_t* __restrict__ gstat, int64_t* __restrict__ gcount,
                                const DevScalars* __restrict__ dsc) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   if (dsc->n_cand != cand_ptr[G]) return;  // selection overflowed: the host grows and repeats
   for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(kBlock) k_budget_write(
     const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ rank_cand, const int32_t* __restrict__ cand_idx,
     const int32_t* __restrict__ off_id, const uint64_t* __restrict__ key, const int64_t* __restrict__ edge_ptr,
     const DevScalars* __restrict__ dsc, int32_t* __restrict__ out_ids, double* __restrict__ out_scores) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   if (N != cand_ptr[G]) return;
@@ -58,12 +60,12 @@ int step_budget(Handle& h, int32_t* out_ids, double* out_scores) {
   int st = scan_excl_u8(h, h.acc_flag, h.scan_tmp, &h.dsc->n_cand, h.Rcap);
   if (st) return st;
   ++h.launches;
-  k_budget_graph<<<(h.G + 255) / 256, 256, 0, h.stream>>>(h.scan_tmp, h.d_cand_ptr, h.d_k, h.sel, h.G, h.gstat,
-                                                          h.gcount, h.dsc);
+  launch_k(h, k_budget_graph, (h.G + 255) / 256, 256, 0, h.scan_tmp, h.d_cand_ptr, h.d_k, h.sel, h.G, h.gstat,
+           h.gcount, h.dsc);
   ++h.launches;
-  k_budget_write<<<grid, kBlock, 0, h.stream>>>(h.acc_flag, h.scan_tmp, h.d_cand_ptr, h.G, h.gstat, h.gcount,
-                                                h.d_out_ptr, h.rank_cand, h.cand_idx, h.off_id, h.key, h.d_edge_ptr,
-                                                h.dsc, out_ids, out_scores);
+  launch_k(h, k_budget_write, grid, kBlock, 0, h.acc_flag, h.scan_tmp, h.d_cand_ptr, h.G, h.gstat, h.gcount,
+           h.d_out_ptr, h.rank_cand, h.cand_idx, h.off_id, h.key, h.d_edge_ptr,
+           h.dsc, out_ids, out_scores);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

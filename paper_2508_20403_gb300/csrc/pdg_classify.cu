@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_list(const int64_t* __restrict_
                                                       const int64_t* __restrict__ off_up,
                                                       int32_t* __restrict__ eu, int32_t* __restrict__ ev,
                                                       double* __restrict__ ew) {
+  dep_sync();
   __shared__ int64_t sm[kBlock / 32 + 1];
   // row starts of the tile, relative to its first entry and clipped to
   // [-1, kTile + 1]: s_rp[j] = row_ptr[r0 + j] - t0
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const int32_t* __restrict__
                                                      double* __restrict__ rtree, int32_t* __restrict__ ou,
                                                      int32_t* __restrict__ ov, int32_t* __restrict__ oid,
                                                      double* __restrict__ ow, DevScalars* __restrict__ dsc) {
+  dep_sync();
   __shared__ int64_t sm[kBlock / 32 + 1];
   // write pass: per-warp queue of (child, weight) for the reciprocals, then
   // the tile's off-tree records (a tile holds at most kTile entries of each)
@@ -321,13 +323,13 @@ int build_edge_list(Handle& h) {
   int64_t* cnt = h.blk_a;
   int64_t* off = h.blk_a + 2560;
   ++h.launches;
-  k_edge_list<false><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.n, h.nnz, cnt, nullptr, nullptr, nullptr,
-                                                  nullptr);
+  launch_k(h, k_edge_list<false>, nb, kBlock, 0, h.row_ptr, h.col, h.w, h.n, h.nnz, cnt, nullptr, nullptr, nullptr,
+           nullptr);
   PDG_CUDA(cudaGetLastError());
   int st = scan_excl_i64(h, cnt, off, nb, nullptr, nb);
   if (st) return st;
   ++h.launches;
-  k_edge_list<true><<<nb, kBlock, 0, h.stream>>>(h.row_ptr, h.col, h.w, h.n, h.nnz, nullptr, off, h.el_u, h.el_v, h.el_w);
+  launch_k(h, k_edge_list<true>, nb, kBlock, 0, h.row_ptr, h.col, h.w, h.n, h.nnz, nullptr, off, h.el_u, h.el_v, h.el_w);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
@@ -342,8 +344,8 @@ int classify_layout(Handle& h) {
   if ((st = device_alloc(h, (void**)&h.cls_off, sizeof(int64_t) * (size_t)(nb + 1)))) return st;
   int64_t* cnt_off = h.blk_a;
   ++h.launches;
-  k_classify<false><<<nb, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, cnt_off, nullptr, nullptr,
-                                                 nullptr, nullptr, nullptr, nullptr, h.dsc);
+  launch_k(h, k_classify<false>, nb, kBlock, 0, h.el_u, h.el_v, h.el_w, h.parent, h.m, cnt_off, nullptr, nullptr,
+           nullptr, nullptr, nullptr, nullptr, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return scan_excl_i64(h, cnt_off, h.cls_off, nb, nullptr, nb);
 }
@@ -353,8 +355,8 @@ int classify_layout(Handle& h) {
 int step_classify(Handle& h) {
   if (h.m == 0) return PDG_OK;
   ++h.launches;
-  k_classify<true><<<h.nblk, kBlock, 0, h.stream>>>(h.el_u, h.el_v, h.el_w, h.parent, h.m, nullptr, h.cls_off,
-                                                    h.rtree, h.off_u, h.off_v, h.off_id, h.off_w, h.dsc);
+  launch_k(h, k_classify<true>, h.nblk, kBlock, 0, h.el_u, h.el_v, h.el_w, h.parent, h.m, nullptr, h.cls_off,
+           h.rtree, h.off_u, h.off_v, h.off_id, h.off_w, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

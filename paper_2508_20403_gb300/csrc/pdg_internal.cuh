@@ -90,6 +90,16 @@ struct DevScalars {
   int64_t bounds_pos, bounds_val;  // its position and offending value
 };
 
+// Programmatic dependent launch.  A kernel started by launch_k may be put on
+// the SMs as the kernel before it on the stream drains (its blocks exiting),
+// before that grid's completion has been signalled; every kernel of the
+// recovery calls dep_sync() first, before it touches device memory:
+// griddepcontrol.wait returns once the previous kernel has completed and its
+// writes are visible (at once when the launch was an ordinary one).  No kernel
+// releases its successor earlier than its own exit (launch_dependents): blocks
+// placed early, while the previous grid still ran, made recoveries slower.
+__device__ __forceinline__ void dep_sync() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // (set by earlier kernels of the stream, so a plain load sees it)
 __device__ __forceinline__ bool attempt_aborted(const DevScalars* d) { return (d->err & kAbortErr) != 0; }
 
@@ -275,6 +285,10 @@ struct Handle {
   cudaStream_t gstream = nullptr;  // private stream: capture and replay
   cudaEvent_t ev_order = nullptr;  // orders gstream after the caller's stream
   cudaStream_t sstream = nullptr;  // side stream: the warp/block tiers beside the cooperative tier
+  // launch_k launches programmatic dependents only inside a recovery (dep_armed)
+  // and only after a kernel it launched itself (dep_ok; cleared by stream_op)
+  bool dep_armed = false;
+  bool dep_ok = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   GraphKey gkey;
@@ -444,6 +458,43 @@ int check_cuda(cudaError_t e);
   } while (0)
 
 int grid_for(const Handle& h, int64_t work, int per_block = kBlock);
+
+// Launches kernel k (which begins with dep_sync()) on the handle's stream:
+// inside a recovery as a programmatic dependent of the kernel before it when
+// that one was launched by launch_k as well, else as an ordinary launch.
+// Errors as for <<<>>>: the launch status is also left for cudaGetLastError.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(Handle& h, void (*k)(P...), dim3 grid, dim3 block, size_t smem, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = (h.dep_armed && h.dep_ok) ? 1 : 0;
+  h.dep_ok = true;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
+}
+
+// After a copy, a fill, an event record or an event wait on the handle's
+// stream: the next kernel waits for it in full.
+inline void stream_op(Handle& h) { h.dep_ok = false; }
+
+// Arms launch_k for the duration of one recovery.
+struct DepScope {
+  Handle& h;
+  explicit DepScope(Handle& hh) : h(hh) {
+    h.dep_armed = true;
+    h.dep_ok = false;
+  }
+  ~DepScope() {
+    h.dep_armed = false;
+    h.dep_ok = false;
+  }
+};
 
 // device-wide exclusive scan: out[i] = sum in[0..i), out[N] = total.
 // N may live on the device (n_dev != nullptr) or be given on the host.

@@ -48,6 +48,7 @@ __device__ __forceinline__ void store_items(int64_t* __restrict__ out, int64_t b
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_scan_small(const T* __restrict__ in, int64_t* __restrict__ out,
                                                        int64_t n_host, const int64_t* n_dev) {
+  dep_sync();
   __shared__ int64_t sm[kBlock / 32 + 1];
   const int64_t N = load_n(n_host, n_dev);
   int64_t run = 0;
@@ -67,6 +68,7 @@ template <typename T>
 __global__ void __launch_bounds__(kLbThreads) k_scan_onepass(const T* __restrict__ in, int64_t* __restrict__ out,
                                                              int64_t n_host, const int64_t* n_dev, uint64_t* status,
                                                              uint32_t* ctr, int64_t spin_limit, DevScalars* dsc) {
+  dep_sync();
   __shared__ int64_t sm[kLbThreads / 32 + 1];
   __shared__ int64_t s_tile, s_excl;
   __shared__ int s_last;
@@ -116,12 +118,12 @@ int scan_impl(Handle& h, const T* in, int64_t* out, int64_t n_host, const int64_
   if (n_max <= 0) n_max = 1;
   ++h.launches;
   if (n_max <= kScanSmall) {
-    k_scan_small<T><<<1, kBlock, 0, h.stream>>>(in, out, n_host, n_dev);
+    launch_k(h, k_scan_small<T>, 1, kBlock, 0, in, out, n_host, n_dev);
   } else {
     const int64_t tiles = (n_max + kLbTile - 1) / kLbTile;
     if (tiles > h.scan_tiles_cap || tiles > 0x7fffffff) return PDG_E_INVALID_ARG;  // sized at init / growth
-    k_scan_onepass<T><<<(int)tiles, kLbThreads, 0, h.stream>>>(in, out, n_host, n_dev, h.scan_status, h.scan_ctr,
-                                                               h.opt.spin_limit, h.dsc);
+    launch_k(h, k_scan_onepass<T>, (int)tiles, kLbThreads, 0, in, out, n_host, n_dev, h.scan_status, h.scan_ctr,
+             h.opt.spin_limit, h.dsc);
   }
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;

@@ -126,6 +126,7 @@ __device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i, uint32
 constexpr int64_t kTicketMinEdges = 1ll << 24;
 
 __global__ void __launch_bounds__(kBlock) k_score(ScoreArgs A, int64_t E, DevScalars* __restrict__ dsc) {
+  dep_sync();
   __shared__ uint32_t s_hist[kSelBins];
   uint32_t* sh = A.hist ? s_hist : nullptr;  // uniform over the grid
   if (sh) {
@@ -180,7 +181,7 @@ int step_score(Handle& h, int score_mode) {
   A.key = h.key;
   A.lca = h.lca;
   A.hist = h.fuse_hist ? h.hist : nullptr;
-  k_score<<<grid_for(h, h.E_off), kBlock, 0, h.stream>>>(A, h.E_off, h.dsc);
+  launch_k(h, k_score, grid_for(h, h.E_off), kBlock, 0, A, h.E_off, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

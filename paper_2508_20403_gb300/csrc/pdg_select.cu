@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kBlock) k_sel_hist(const uint64_t* __restrict_
                                                      const int64_t* __restrict__ off_ptr, int32_t G,
                                                      const GraphSel* __restrict__ sel, int lvl,
                                                      uint32_t* __restrict__ hist) {
+  dep_sync();
   __shared__ uint32_t sh[kSelBins];
   const int64_t chunk = sel_chunk(E, gridDim.x);
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
@@ -85,6 +86,7 @@ static_assert(kPickPer == 16, "pick layout");
 __global__ void __launch_bounds__(kBlock) k_sel_pick(uint32_t* __restrict__ hist, GraphSel* __restrict__ sel,
                                                      const int64_t* __restrict__ off_ptr, int32_t G, int lvl,
                                                      int64_t* __restrict__ count_out, int64_t* __restrict__ cand_ptr) {
+  dep_sync();
   __shared__ int64_t sm[kBlock / 32 + 1];
   __shared__ int s_owner;
   const int32_t g = blockIdx.x;
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
                                                         int64_t* __restrict__ bcount, int64_t cap,
                                                         int32_t* __restrict__ cand_idx,
                                                         uint64_t* __restrict__ rkey, int32_t* __restrict__ rval) {
+  dep_sync();
   __shared__ int64_t sm[kBlock / 32 + 1];
   const int64_t chunk = sel_chunk(E, gridDim.x);
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
@@ -249,6 +252,7 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
 __global__ void __launch_bounds__(kBlock) k_sel_total(const int64_t* __restrict__ bcount, int nb,
                                                       const int64_t* __restrict__ cand_ptr, int32_t G, int64_t cap,
                                                       DevScalars* dsc) {
+  dep_sync();
   __shared__ int64_t sm[kBlock / 32 + 1];
   int64_t c = 0;
   for (int i = threadIdx.x; i < nb; i += kBlock) c += bcount[i];
@@ -275,23 +279,23 @@ int step_select(Handle& h) {
   for (int lvl = 0; lvl < 2; lvl++) {
     if (any_select && !(lvl == 0 && h.fuse_hist)) {
       ++h.launches;
-      k_sel_hist<<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, lvl, h.hist);
+      launch_k(h, k_sel_hist, nb, kBlock, 0, h.key, E, h.d_off_ptr, h.G, h.sel, lvl, h.hist);
     }
     ++h.launches;
-    k_sel_pick<<<h.G, kBlock, 0, h.stream>>>(h.hist, h.sel, h.d_off_ptr, h.G, lvl, h.d_graph_tmp, h.d_cand_ptr);
+    launch_k(h, k_sel_pick, h.G, kBlock, 0, h.hist, h.sel, h.d_off_ptr, h.G, lvl, h.d_graph_tmp, h.d_cand_ptr);
   }
   PDG_CUDA(cudaGetLastError());
   int st;
   if (h.G > 1 && (st = scan_excl_i64(h, h.d_graph_tmp, h.d_cand_ptr, h.G, nullptr, h.G))) return st;
   int64_t* bcount = h.blk_a;
   ++h.launches;
-  k_sel_compact<false><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, 0, nullptr, nullptr,
-                                                    nullptr);
+  launch_k(h, k_sel_compact<false>, nb, kBlock, 0, h.key, E, h.d_off_ptr, h.G, h.sel, bcount, 0, nullptr, nullptr,
+           nullptr);
   ++h.launches;
-  k_sel_compact<true><<<nb, kBlock, 0, h.stream>>>(h.key, E, h.d_off_ptr, h.G, h.sel, bcount, h.Rcap, h.cand_idx,
-                                                   h.rk[0], h.rv[0]);
+  launch_k(h, k_sel_compact<true>, nb, kBlock, 0, h.key, E, h.d_off_ptr, h.G, h.sel, bcount, h.Rcap, h.cand_idx,
+           h.rk[0], h.rv[0]);
   ++h.launches;
-  k_sel_total<<<1, kBlock, 0, h.stream>>>(bcount, nb, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
+  launch_k(h, k_sel_total, 1, kBlock, 0, bcount, nb, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

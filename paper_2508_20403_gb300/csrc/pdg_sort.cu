@@ -53,6 +53,7 @@ constexpr uint32_t kCountMask = (1u << 30) - 1;
 // in the current buffer: ghist[d][bin].
 __global__ void __launch_bounds__(kBlock) k_os_hist(const uint64_t* k0, const uint64_t* k1, const DevScalars* dsc,
                                                     int shift0, int ndig, uint32_t* __restrict__ ghist) {
+  dep_sync();
   __shared__ uint32_t sh[kMaxDigits][kRdxBins];
   const int64_t N = dsc->n_cand;
   const uint64_t* keys = dsc->radix_sel ? k1 : k0;
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(kBlock) k_os_hist(const uint64_t* k0, const ui
 // here (sel[d]: the buffer pass d reads) together with the final choice.
 __global__ void k_os_scan(uint32_t* __restrict__ ghist, int ndig, DevScalars* dsc, uint32_t* __restrict__ goff,
                           int32_t* __restrict__ skip, int32_t* __restrict__ sel) {
+  dep_sync();
   __shared__ int32_t s_skip[kMaxDigits];
   const int lane = threadIdx.x & 31, d = threadIdx.x >> 5;  // launched with 32 * ndig threads
   const uint32_t N = (uint32_t)dsc->n_cand;
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_os_scatter(const uint64_t* k0
                                                        const uint32_t* __restrict__ goff, const int32_t* skip,
                                                        const int32_t* selp, uint32_t* status, uint32_t* counters,
                                                        int64_t spin_limit) {
+  dep_sync();
   constexpr int kOsTile = kOsThreads * kOsItems;
   constexpr int kRdxPerWarp = kOsTile / kRdxWarps;  // kOsItems rounds of 32
   extern __shared__ __align__(16) unsigned char os_smem[];
@@ -275,6 +278,7 @@ namespace {
 __global__ void k_key_graph(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1, const int32_t* __restrict__ v0,
                             const int32_t* __restrict__ v1, const int64_t* __restrict__ cand_ptr, int32_t G,
                             DevScalars* dsc) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   uint64_t* k = dsc->radix_sel ? k1 : k0;
@@ -287,6 +291,7 @@ __global__ void k_key_graph(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1
 __global__ void k_key_lca(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1, int32_t* __restrict__ v0,
                           int32_t* __restrict__ v1, const int32_t* __restrict__ cand_idx,
                           const int32_t* __restrict__ lca, int32_t* __restrict__ rank_cand, DevScalars* dsc) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   uint64_t* k = dsc->radix_sel ? k1 : k0;
@@ -301,6 +306,7 @@ __global__ void k_key_lca(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1, 
 
 __global__ void k_copy_vals(const int32_t* __restrict__ v0, const int32_t* __restrict__ v1, int32_t* __restrict__ out,
                             DevScalars* dsc) {
+  dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t N = dsc->n_cand;
   const int32_t* v = dsc->radix_sel ? v1 : v0;
@@ -336,9 +342,9 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
   int32_t* skip = reinterpret_cast<int32_t*>(h.radix_hist + 16 * kRdxBins) + pass0;
   int32_t* sel = reinterpret_cast<int32_t*>(h.radix_hist + 16 * kRdxBins) + kRadixPassesMax + pass0;
   ++h.launches;
-  k_os_hist<<<grid_hist, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.dsc, shift0, ndig, ghist);
+  launch_k(h, k_os_hist, grid_hist, kBlock, 0, h.rk[0], h.rk[1], h.dsc, shift0, ndig, ghist);
   ++h.launches;
-  k_os_scan<<<1, 32 * ndig, 0, h.stream>>>(ghist, ndig, h.dsc, goff, skip, sel);
+  launch_k(h, k_os_scan, 1, 32 * ndig, 0, ghist, ndig, h.dsc, goff, skip, sel);
   for (int d = 0; d < ndig; d++) {
     const int p = pass0 + d;
     uint32_t* status = h.radix_status + (int64_t)p * tiles_max * kRdxBins;
@@ -346,9 +352,9 @@ static int onesweep(Handle& h, int shift0, int ndig, int pass0) {
     ++h.launches;
     const int grid = (int)std::max<int64_t>(tiles_max, 1);
 #define PDG_OS_SCATTER(I)                                                                                    \
-  k_os_scatter<I><<<grid, kOsThreads, os_smem_bytes(I), h.stream>>>(                                         \
-      h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.dsc, shift0 + 8 * d,         \
-      goff + d * kRdxBins, skip + d, sel + d, status, counters, h.opt.spin_limit)
+  launch_k(h, k_os_scatter<I>, grid, kOsThreads, os_smem_bytes(I), h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.rk[0], \
+           h.rk[1], h.rv[0], h.rv[1], h.dsc, shift0 + 8 * d, goff + d * kRdxBins, skip + d, sel + d, status,   \
+           counters, h.opt.spin_limit)
     if (items == 4) PDG_OS_SCATTER(4);
     else if (items == 8) PDG_OS_SCATTER(8);
     else PDG_OS_SCATTER(6);
@@ -410,17 +416,21 @@ struct CoopSmem {
   int32_t uniform[kMaxDigits];
 };
 
+// Thread 0 of each block announces the block's arrival with a release
+// reduction (the block's writes, ordered before it by __syncthreads, become
+// visible with it) and polls the count with acquire loads: no full fence and
+// no returned atomic on the path.  The wait is bounded (spin_limit).
 __device__ __forceinline__ void coop_barrier(const CoopSortArgs& a, uint32_t& target) {
   __syncthreads();
   target += gridDim.x;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(a.bar, 1u);
-    volatile uint32_t* b = a.bar;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar) : "memory");
+    uint32_t v;
     int64_t spins = 0;
-    while (*b < target && spins < a.spin_limit) spins++;
-    if (*b < target) atomicOr(&a.dsc->err, ERR_TIMEOUT);
-    __threadfence();
+    do {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a.bar) : "memory");
+    } while (v < target && ++spins < a.spin_limit);
+    if (v < target) atomicOr(&a.dsc->err, ERR_TIMEOUT);
   }
   __syncthreads();
 }
@@ -593,6 +603,7 @@ __device__ __forceinline__ void coop_keyset(const CoopSortArgs& a, CoopSmem& sm,
 }
 
 __global__ void __launch_bounds__(kCoThreads) k_sort_coop(CoopSortArgs a) {
+  dep_sync();
   extern __shared__ __align__(16) unsigned char co_smem[];
   CoopSmem& sm = *reinterpret_cast<CoopSmem*>(co_smem);
   if (attempt_aborted(a.dsc)) return;  // the attempt is void (uniform over the grid: set before the launch)
@@ -664,6 +675,7 @@ static int step_sort_coop(Handle& h, int grid_max) {
   PDG_CUDA(cudaMemsetAsync(h.radix_counters, 0, sizeof(uint32_t) * 2 * kRadixPassesMax, h.stream));
   uint32_t* totals = h.radix_hist + kRadixHistOnesweep;  // beside the words the per-pass path keeps zero
   PDG_CUDA(cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kCoKeySets * kMaxDigits * kRdxBins, h.stream));
+  stream_op(h);
   CoopSortArgs a{};
   a.k[0] = h.rk[0];
   a.k[1] = h.rk[1];
@@ -695,7 +707,8 @@ static int step_sort_coop(Handle& h, int grid_max) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ++h.launches;
-  PDG_CUDA(cudaLaunchKernelEx(&cfg, k_sort_coop, a));
+  PDG_CUDA(cudaLaunchKernelEx(&cfg, k_sort_coop, a));  // an ordinary (cooperative) launch
+  h.dep_ok = true;  // it begins with dep_sync(): the next kernel may depend on it programmatically
   return PDG_OK;
 }
 
@@ -712,6 +725,7 @@ int step_sort(Handle& h) {
   PDG_CUDA(cudaMemsetAsync(h.radix_status, 0, sizeof(uint32_t) * (size_t)kRadixPassesMax * tiles_max * kRdxBins,
                            h.stream));
   PDG_CUDA(cudaMemsetAsync(h.radix_counters, 0, sizeof(uint32_t) * 2 * kRadixPassesMax, h.stream));
+  stream_op(h);
   int st;
   int pass = 0;
   // 1. score descending (ties keep ascending id order)
@@ -719,7 +733,7 @@ int step_sort(Handle& h) {
   pass += 8;
   if (h.G > 1) {
     ++h.launches;
-    k_key_graph<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.d_cand_ptr, h.G, h.dsc);
+    launch_k(h, k_key_graph, grid, kBlock, 0, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.d_cand_ptr, h.G, h.dsc);
     int nd = 0;
     while ((1ll << (8 * nd)) < h.G) nd++;
     if ((st = onesweep(h, 0, nd, pass))) return st;
@@ -727,12 +741,12 @@ int step_sort(Handle& h) {
   }
   // 2. group ranks by LCA
   ++h.launches;
-  k_key_lca<<<grid, kBlock, 0, h.stream>>>(h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.cand_idx, h.lca, h.rank_cand, h.dsc);
+  launch_k(h, k_key_lca, grid, kBlock, 0, h.rk[0], h.rk[1], h.rv[0], h.rv[1], h.cand_idx, h.lca, h.rank_cand, h.dsc);
   int nd = 0;
   while ((1ll << (8 * nd)) < h.n) nd++;
   if ((st = onesweep(h, 0, nd, pass))) return st;
   ++h.launches;
-  k_copy_vals<<<grid, kBlock, 0, h.stream>>>(h.rv[0], h.rv[1], h.lsort_rank, h.dsc);
+  launch_k(h, k_copy_vals, grid, kBlock, 0, h.rv[0], h.rv[1], h.lsort_rank, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

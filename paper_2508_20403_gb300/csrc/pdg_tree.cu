@@ -132,6 +132,7 @@ __device__ __forceinline__ u128 block_sum_u128(u128 x, u128* s_warp) {
 }
 
 __global__ void __launch_bounds__(kTsThreads) k_tree_sum(TreeScanArgs a) {
+  dep_sync();
   __shared__ u128 s_warp[kTsThreads / 32];
   const bool range_ok = range_fits(a.dsc, a.dep_bits);
   const int e_min = a.dsc->e_min;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kTsThreads) k_tree_sum(TreeScanArgs a) {
 }
 
 __global__ void __launch_bounds__(kTsThreads, 4) k_tree_scan(TreeScanArgs a) {
+  dep_sync();
   __shared__ u128 s_warp[kTsThreads / 32];
   __shared__ u128 s_pre[kTsThreads / 32];
   const bool range_ok = range_fits(a.dsc, a.dep_bits);
@@ -333,6 +335,7 @@ __device__ void rmq_sparse_table(const RmqArgs& a, uint64_t* buf) {
 }
 
 __global__ void __launch_bounds__(kRmqThreads, 2) k_rmq_build(RmqArgs a) {
+  dep_sync();
   extern __shared__ __align__(16) unsigned char rmq_smem[];
   RmqSmem& sm = *reinterpret_cast<RmqSmem*>(rmq_smem);
   __shared__ int s_last;
@@ -397,9 +400,9 @@ int step_tree(Handle& h) {
     const int64_t tiles = (h.A + kTsTile - 1) / kTsTile;
     TreeScanArgs a{h.tour, h.A, h.rtree, h.parent, dep_bits, h.dsc, h.P, h.rmq_val[0], h.ts_sum};
     ++h.launches;
-    k_tree_sum<<<(int)tiles, kTsThreads, 0, h.stream>>>(a);
+    launch_k(h, k_tree_sum, (int)tiles, kTsThreads, 0, a);
     ++h.launches;
-    k_tree_scan<<<(int)tiles, kTsThreads, 0, h.stream>>>(a);
+    launch_k(h, k_tree_scan, (int)tiles, kTsThreads, 0, a);
     PDG_CUDA(cudaGetLastError());
   }
   // the range-minimum structure over val0
@@ -417,7 +420,7 @@ int step_tree(Handle& h) {
   r.done = h.ts_done;
   PDG_CUDA(rmq_smem_attr());
   ++h.launches;
-  k_rmq_build<<<(int)((h.rmq_size[0] + kRmqChunk - 1) / kRmqChunk), kRmqThreads, sizeof(RmqSmem), h.stream>>>(r);
+  launch_k(h, k_rmq_build, (int)((h.rmq_size[0] + kRmqChunk - 1) / kRmqChunk), kRmqThreads, sizeof(RmqSmem), r);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
