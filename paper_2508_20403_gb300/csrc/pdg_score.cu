@@ -125,7 +125,9 @@ __device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i, uint32
 // Shorter lists use a plain grid-stride loop, whose window is narrower still.
 constexpr int64_t kTicketMinEdges = 1ll << 24;
 
-__global__ void __launch_bounds__(kBlock) k_score(ScoreArgs A, int64_t E, DevScalars* __restrict__ dsc) {
+// Eight blocks per SM (32 registers, a few bytes spilled): the gathers of a
+// full SM's warps in flight hide more of their latency than the registers saved.
+__global__ void __launch_bounds__(kBlock, 8) k_score(ScoreArgs A, int64_t E, DevScalars* __restrict__ dsc) {
   dep_sync();
   __shared__ uint32_t s_hist[kSelBins];
   uint32_t* sh = A.hist ? s_hist : nullptr;  // uniform over the grid
