@@ -4,12 +4,14 @@
 // rounded once to nearest-even as IEEE 754 defines them:
 //   r = fl(1/w)            step A1, the resistive weight of a tree edge (Eq. RT)
 //   R = fl(D * 2^-S)       step A3, the exact fixed-point path sum to FP64
-//   s = fl(w * R)          step A3, the stretch score
+//   s = fl(w * R)          step A3, the stretch score (one hardware multiply)
 // On this GPU the double-precision pipe is a small fraction of the integer and
-// single-precision pipes, so these are computed from the bit patterns with
-// integer arithmetic (the results are bit-identical to the IEEE operations;
-// the test-suite compares them with the oracle's C doubles).  Inputs outside
-// the normal range of the fast paths fall back to the hardware operation.
+// single-precision pipes; the reciprocal (a multi-step sequence on that pipe)
+// and the conversion (which has no single hardware instruction) are computed
+// from the bit patterns with integer arithmetic.  The results are bit-identical
+// to the IEEE operations (the test-suite compares them with the oracle's C
+// doubles); inputs outside the normal range of the fast path fall back to the
+// hardware operation.
 //
 //   reciprocal: Newton's iteration x <- x + x (1 - m x) for 1/m on the 53-bit
 //     significand m, started from the single-precision reciprocal of its top
@@ -18,10 +20,8 @@
 //     quotient floor(2^105 / m) by comparing products, and the rounding bit
 //     from the remainder (no ties: 2^106 / m is never an odd integer for a
 //     significand that is not a power of two).
-//   product: the 106-bit product of the significands, normalised and rounded
-//     to 53 bits by its remainder (ties to even).
-//   fixed point to FP64: the leading bit of the 128-bit integer fixes the
-//     exponent; the 53 bits below it, rounded by the remainder, the significand.
+//   fixed point to FP64: the leading bit of the integer fixes the exponent;
+//     the 53 bits below it, rounded by the remainder, the significand.
 #pragma once
 
 #include <stdint.h>
@@ -101,41 +101,18 @@ PDG_HD uint64_t rcp_rn_bits(uint64_t wb, bool* ok) {
   return ((2045 - e) << 52) | (q & kMant);  // q in (2^52, 2^53): 1/w = q 2^(1022 - (e-1023) - 52 - 52)
 }
 
-// IEEE bits of fl(a * b) for positive normal a, b; *ok is false when the
-// result leaves the normal range (the caller then multiplies in hardware)
-PDG_HD uint64_t mul_rn_bits(uint64_t a, uint64_t b, bool* ok) {
-  const int64_t ea = (int64_t)(a >> 52), eb = (int64_t)(b >> 52);
-  const u128 p = (u128)((a & kMant) | (1ull << 52)) * ((b & kMant) | (1ull << 52));  // [2^104, 2^106)
-  const int top = (p >> 105) ? 1 : 0;
-  const int sh = 52 + top;
-  int64_t e = ea + eb - 1023 + top;
-  uint64_t q = (uint64_t)(p >> sh);
-  const uint64_t rem = (uint64_t)p & ((1ull << sh) - 1);
-  const uint64_t half = 1ull << (sh - 1);
-  if (rem > half || (rem == half && (q & 1))) {
-    q++;
-    if (q >> 53) {
-      q >>= 1;
-      e++;
-    }
-  }
-  *ok = (e >= 1 && e <= 2046);
-  return ((uint64_t)e << 52) | (q & kMant);
-}
-
-// IEEE bits of fl(x * 2^-S) for an integer 0 < x < 2^128 whose value is a
-// normal double
-PDG_HD uint64_t fixed_to_bits(u128 x, int S) {
-  const uint64_t hi = (uint64_t)(x >> 64), lo = (uint64_t)x;
+// IEEE bits of fl(x * 2^-S) for an integer 0 < x = hi 2^64 + lo < 2^115 (the
+// exact path sums stay below 2^97) whose value is a normal double: every shift
+// and mask stays within 64 bits.
+PDG_HD uint64_t fixed_hl_to_bits(uint64_t hi, uint64_t lo, int S) {
   int p = hi ? 127 - clz64(hi) : 63 - clz64(lo);  // leading bit
+  const int sh = p - 52;                          // at most 62
   uint64_t q;
-  if (p <= 52) {
-    q = lo << (52 - p);
+  if (sh <= 0) {
+    q = lo << (-sh);  // exact (hi is zero here)
   } else {
-    const int sh = p - 52;
-    q = (uint64_t)(x >> sh);
-    const u128 rem = x & ((((u128)1) << sh) - 1);
-    const u128 half = ((u128)1) << (sh - 1);
+    q = (hi << (64 - sh)) | (lo >> sh);  // below 2^53: hi < 2^(p - 63)
+    const uint64_t rem = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
     if (rem > half || (rem == half && (q & 1))) {
       q++;
       if (q >> 53) {

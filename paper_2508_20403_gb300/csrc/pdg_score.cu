@@ -13,8 +13,9 @@
 // The query reads at most two partial groups per level of the range-minimum
 // structure; the addresses depend only on (u, v), so all mask loads are
 // issued together, then all key loads: three dependent rounds of gathers per
-// edge (P(u), P(v) with the masks; the keys; P(l)).  The conversion and the
-// product run on the integer pipes (pdg_fp.cuh).
+// edge (P(u), P(v) with the masks; the keys; P(l)).  The conversion runs on
+// the integer pipes (pdg_fp.cuh); the product is one FP64 multiply, which the
+// FP64 pipe takes in fewer issue slots than an integer version of it.
 //
 // The score is positive, so its IEEE bit pattern read as an unsigned integer
 // orders like the score itself; key[i] stores those bits for the selection
@@ -105,14 +106,10 @@ __device__ __forceinline__ void score_edge(const ScoreArgs& A, int64_t i, uint32
   }
   const u128 Pl = A.P[l];
   const u128 r_fixed = (Pu >> 32) + (Pv >> 32) - ((Pl >> 32) << 1);
-  const uint64_t rb = fixed_to_bits(r_fixed, A.S);
+  const uint64_t rb = fixed_hl_to_bits((uint64_t)(r_fixed >> 64), (uint64_t)r_fixed, A.S);  // below 2^97
   uint64_t sb = rb;
-  if (A.score_mode != PDG_SCORE_RESISTANCE) {
-    const double w = A.ow[i];
-    bool ok;
-    sb = mul_rn_bits((uint64_t)__double_as_longlong(w), rb, &ok);
-    if (!ok) sb = (uint64_t)__double_as_longlong(__dmul_rn(w, __longlong_as_double((long long)rb)));
-  }
+  if (A.score_mode != PDG_SCORE_RESISTANCE)  // one IEEE multiply, rounded to nearest-even
+    sb = (uint64_t)__double_as_longlong(__dmul_rn(A.ow[i], __longlong_as_double((long long)rb)));
   A.key[i] = sb;
   A.lca[i] = l;
   if (s_hist) atomicAdd(&s_hist[sb >> 52], 1u);
