@@ -554,19 +554,22 @@ __device__ __forceinline__ void coop_keyset(const CoopSortArgs& a, CoopSmem& sm,
     coop_barrier(a, target);
     // the tile's prefix per digit: counts of the earlier tiles, summed by every block for itself.  The
     // 256 counts of a tile are one 1 KB row: 64 threads read a row (16 bytes each), the eight row
-    // groups take every eighth earlier tile, four rows in flight per thread, then add up in shared memory.
+    // groups take every eighth earlier tile, then add up in shared memory.
     if (t < tiles) {
       const int q = threadIdx.x & 63, rg = threadIdx.x >> 6;
+      // sixteen rows in flight per thread: the rows of up to 128 earlier tiles in one round of loads
+      // (the block is alone on its SM, so the registers are there)
+      constexpr int kRows = 16;
       uint4 acc = make_uint4(0, 0, 0, 0);
-      for (int64_t r0 = rg; r0 < t; r0 += 32) {
-        uint4 x[4];
+      for (int64_t r0 = rg; r0 < t; r0 += 8 * kRows) {
+        uint4 x[kRows];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < kRows; u++) {
           const int64_t r = r0 + 8 * u;
           x[u] = r < t ? __ldcg(reinterpret_cast<const uint4*>(a.counts + r * kRdxBins) + q) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < kRows; u++) {
           acc.x += x[u].x;
           acc.y += x[u].y;
           acc.z += x[u].z;
