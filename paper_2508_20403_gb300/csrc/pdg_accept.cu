@@ -995,7 +995,9 @@ __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __res
                                const int32_t* __restrict__ seg_begin, int last_round) {
   dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
-  if (dsc->n_constrained == 0 || a.und_count[last_round] == 0) return;
+  const int64_t left = dsc->n_constrained == 0 ? 0 : a.und_count[last_round];
+  if (blockIdx.x == 0 && threadIdx.x == 0) dsc->finish_left = left;  // sizes the next recovery's rounds
+  if (left == 0) return;
   const int64_t ns = dsc->n_big_seg;
   const uint64_t cap = *a.cap;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ns; x += (int64_t)gridDim.x * blockDim.x) {
@@ -1060,7 +1062,7 @@ static int block_tier_max(const Handle& h, int c) {
 
 int coop_rounds(const Handle& h, int c) {
   int R = std::max(1, std::min(h.opt.max_rounds, 64));
-  if (h.rounds_mem > 0 && h.c_mem == c && h.mode_mem == h.opt.score_mode) R = std::min(R, h.rounds_mem + 1);
+  if (h.rounds_mem >= 0 && h.c_mem == c && h.mode_mem == h.opt.score_mode) R = std::min(R, std::max(1, h.rounds_mem));
   return R;
 }
 

@@ -146,6 +146,7 @@ __global__ void k_reset_attempt(DevScalars* dsc) {
   dsc->n_warp_cand = 0;
   dsc->n_constrained = 0;
   dsc->n_big_chunk = 0;
+  dsc->finish_left = 0;
 }
 
 // endpoints of canonical ids in the caller's vertex ids (u < v): the edge
@@ -904,7 +905,7 @@ static int run_recovery(pdg_sparsifier* hp, const double* alpha, int32_t c, cons
       }
       h.c_mem = c;
       h.mode_mem = h.opt.score_mode;
-      h.rounds_mem = h.hsc->rounds_used;
+      h.rounds_mem = h.hsc->rounds_used + (h.hsc->finish_left > 0 ? 1 : 0);
       if (first && !replayed && h.opt.use_graph && attempts == 1) {
         // this call needed one attempt: capture it for replay by later calls
         const cudaStream_t user = h.stream;

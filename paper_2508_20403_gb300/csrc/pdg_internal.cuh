@@ -88,6 +88,7 @@ struct DevScalars {
   int32_t bounds_site;  // first failed bounds check (see ERR_BOUNDS)
   int32_t bounds_where;  // its round (99: serial finisher)
   int64_t bounds_pos, bounds_val;  // its position and offending value
+  int64_t finish_left;  // cooperative tier: candidates the rounds left to the serial finisher
 };
 
 // Programmatic dependent launch.  A kernel started by launch_k may be put on
@@ -213,10 +214,11 @@ struct Handle {
   // there (any prefix holding the first k recovered edges gives the same set)
   std::vector<int64_t> want_mem, k_mem;
   int c_mem = -1, mode_mem = -1;
-  // cooperative-tier rounds the last recovery with (c_mem, mode_mem) ran; a
-  // later one launches one round more than that (the serial finisher
-  // completes whatever a short round count leaves, so any count is exact)
-  int rounds_mem = 0;
+  // cooperative-tier rounds a later recovery with (c_mem, mode_mem) launches:
+  // the rounds the last one ran, one more if it left candidates to the serial
+  // finisher (which completes whatever a short round count leaves, so any
+  // count is exact; -1: no recovery yet)
+  int rounds_mem = -1;
   int64_t* d_cand_ptr = nullptr;  // G+1
   int64_t* d_graph_tmp = nullptr;  // G+1 scratch
 

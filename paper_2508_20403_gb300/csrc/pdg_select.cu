@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
                                                         const GraphSel* __restrict__ sel,
                                                         int64_t* __restrict__ bcount, int64_t cap,
                                                         int32_t* __restrict__ cand_idx,
-                                                        uint64_t* __restrict__ rkey, int32_t* __restrict__ rval) {
+                                                        uint64_t* __restrict__ rkey, int32_t* __restrict__ rval,
+                                                        const int64_t* __restrict__ cand_ptr, DevScalars* dsc) {
   dep_sync();
   __shared__ int64_t sm[kBlock / 32 + 1];
   const int64_t chunk = sel_chunk(E, gridDim.x);
@@ -187,6 +188,17 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
     int64_t c = 0;
     for (int i = threadIdx.x; i < (int)blockIdx.x; i += kBlock) c += bcount[i];
     run = block_sum(c, sm);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {  // the last block's end is the total
+      const int64_t total = run + bcount[blockIdx.x];
+      dsc->n_cand_wanted = total;
+      if (total > cap || total != cand_ptr[G]) {
+        // nothing downstream may touch more than `cap` candidates: run it empty
+        dsc->n_cand = 0;
+        atomicOr(&dsc->err, ERR_CAPACITY);
+      } else {
+        dsc->n_cand = total;
+      }
+    }
   }
   int64_t tot = 0;
   for (int64_t t0 = b0; t0 < b1; t0 += kTile) {
@@ -249,25 +261,6 @@ __global__ void __launch_bounds__(kBlock) k_sel_compact(const uint64_t* __restri
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_sel_total(const int64_t* __restrict__ bcount, int nb,
-                                                      const int64_t* __restrict__ cand_ptr, int32_t G, int64_t cap,
-                                                      DevScalars* dsc) {
-  dep_sync();
-  __shared__ int64_t sm[kBlock / 32 + 1];
-  int64_t c = 0;
-  for (int i = threadIdx.x; i < nb; i += kBlock) c += bcount[i];
-  const int64_t total = block_sum(c, sm);
-  if (threadIdx.x != 0) return;
-  dsc->n_cand_wanted = total;
-  if (total > cap || total != cand_ptr[G]) {
-    // nothing downstream may touch more than `cap` candidates: run it empty
-    dsc->n_cand = 0;
-    atomicOr(&dsc->err, ERR_CAPACITY);
-  } else {
-    dsc->n_cand = total;
-  }
-}
-
 }  // namespace
 
 int step_select(Handle& h) {
@@ -290,12 +283,10 @@ int step_select(Handle& h) {
   int64_t* bcount = h.blk_a;
   ++h.launches;
   launch_k(h, k_sel_compact<false>, nb, kBlock, 0, h.key, E, h.d_off_ptr, h.G, h.sel, bcount, 0, nullptr, nullptr,
-           nullptr);
+           nullptr, h.d_cand_ptr, h.dsc);
   ++h.launches;
   launch_k(h, k_sel_compact<true>, nb, kBlock, 0, h.key, E, h.d_off_ptr, h.G, h.sel, bcount, h.Rcap, h.cand_idx,
-           h.rk[0], h.rv[0]);
-  ++h.launches;
-  launch_k(h, k_sel_total, 1, kBlock, 0, bcount, nb, h.d_cand_ptr, h.G, h.Rcap, h.dsc);
+           h.rk[0], h.rv[0], h.d_cand_ptr, h.dsc);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }

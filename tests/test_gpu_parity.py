@@ -135,8 +135,9 @@ def test_prefix_memory_across_calls(B):
 
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_round_memory_across_budgets(B, use_graph):
-    """A handle launches one cooperative round more than its last recovery needed; a later budget that needs
-    more rounds leaves the rest to the serial finisher and must still match the oracle, replayed or not."""
+    """A handle launches the cooperative rounds its last recovery needed (one more when that one left work to the
+    serial finisher); a later budget that needs more rounds leaves the rest to the serial finisher and must still
+    match the oracle, replayed or not."""
     g = W.rmat_graph(13, seed=77)
     o = B.default_options(use_graph=use_graph)
     with B.Sparsifier.from_graph(g, options=o) as sp:
