@@ -989,44 +989,47 @@ __global__ void __launch_bounds__(kBlock) k_exact_round(CoopArgs a, DevScalars* 
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&dsc->rounds_used, round);
 }
 
-// serial completion in rank order, one thread per cooperative subtask
+// The cooperative tier's end: every candidate's recovered flag (by rank).  In
+// the common case the rounds decided every candidate, and the threads write
+// the flags of all positions; otherwise one thread per cooperative subtask
+// completes it serially in rank order and writes its flags as it goes.
 template <int C>
 __global__ void k_exact_finish(CoopArgs a, DevScalars* dsc, const int32_t* __restrict__ big_seg,
-                               const int32_t* __restrict__ seg_begin, int last_round) {
+                               const int32_t* __restrict__ seg_begin, int last_round, uint8_t* __restrict__ acc_flag) {
   dep_sync();
   if (attempt_aborted(dsc)) return;  // the attempt is void
   const int64_t left = dsc->n_constrained == 0 ? 0 : a.und_count[last_round];
   if (blockIdx.x == 0 && threadIdx.x == 0) dsc->finish_left = left;  // sizes the next recovery's rounds
-  if (left == 0) return;
+  if (left == 0) {
+    const int64_t nb = dsc->n_big;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t s = a.big_pos[q];
+      const uint8_t st = a.state[s];
+      acc_flag[a.ra.rank[s]] = (st == ST_ACCEPTED || st == ST_ACCEPTED_NEW) ? 1 : 0;
+    }
+    return;
+  }
   const int64_t ns = dsc->n_big_seg;
   const uint64_t cap = *a.cap;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ns; x += (int64_t)gridDim.x * blockDim.x) {
     const int32_t q = big_seg[x];
     for (int32_t s = seg_begin[q]; s < seg_begin[q + 1]; s++) {
       const uint8_t st = a.state[s];
-      if (st == ST_ACCEPTED || st == ST_REJECTED) continue;
+      if (st == ST_ACCEPTED || st == ST_REJECTED) {
+        acc_flag[a.ra.rank[s]] = st == ST_REJECTED ? 0 : 1;
+        continue;
+      }
       Rec r;
       load_rec(a.ra, s, C, r);
       if (st == ST_UNDECIDED && exact_probe<C, false, false>(a, s, r, a.pmask[s], 0, 99, cap, 0) == 2) {
         a.state[s] = ST_REJECTED;
+        acc_flag[r.rank] = 0;
         continue;
       }
       exact_register<C, false>(a, s, r.b, r.rank, true, 0, cap, 0);
       a.state[s] = ST_ACCEPTED;
+      acc_flag[r.rank] = 1;
     }
-  }
-}
-
-__global__ void k_big_flags(const int32_t* __restrict__ big_pos, const uint8_t* __restrict__ state,
-                            const int32_t* __restrict__ rec_rank, const DevScalars* __restrict__ dsc,
-                            uint8_t* __restrict__ acc_flag) {
-  dep_sync();
-  if (attempt_aborted(dsc)) return;  // the attempt is void
-  const int64_t nb = dsc->n_big;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t s = big_pos[q];
-    const uint8_t st = state[s];
-    acc_flag[rec_rank[s]] = (st == ST_ACCEPTED || st == ST_ACCEPTED_NEW) ? 1 : 0;
   }
 }
 
@@ -1046,7 +1049,7 @@ int run_coop(Handle& h, const CoopArgs& a, int grid, int rounds) {
     launch_k(h, k_exact_round<C>, grid_und, kBlock, 0, a, h.dsc, r);
   }
   ++h.launches;
-  launch_k(h, k_exact_finish<C>, grid, kBlock, 0, a, h.dsc, h.big_seg, h.seg_begin, rounds);
+  launch_k(h, k_exact_finish<C>, grid, kBlock, 0, a, h.dsc, h.big_seg, h.seg_begin, rounds, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
@@ -1165,8 +1168,6 @@ static int accept_coop(Handle& h, int c, int grid, const RecArrays& ra) {
     default: st = run_coop<3>(h, a, grid, R); break;
   }
   if (st) return st;
-  ++h.launches;
-  launch_k(h, k_big_flags, grid, kBlock, 0, h.big_pos, h.state, h.rec_rank, h.dsc, h.acc_flag);
   PDG_CUDA(cudaGetLastError());
   return PDG_OK;
 }
