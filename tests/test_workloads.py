@@ -46,3 +46,25 @@ def test_generated_graphs_are_valid():
 def test_seeds_reproduce():
     assert _same(W.grid_graph(20), W.grid_graph(20))
     assert not np.array_equal(W.grid_graph(20, seed=1).w, W.grid_graph(20, seed=2).w)
+
+
+def test_pack_into_preallocated_buffers():
+    """The serving workers pack each batch straight into larger pinned staging arrays: the first N+1 / nnz / N
+    entries must equal a fresh pack, and the disjoint union must keep every graph's CSR, weights and tree."""
+    graphs = [W.grid_graph(7), W.rmat_graph(8, seed=3), W.grid_graph(4)]
+    N, nnz = W.packed_sizes(graphs)
+    ref = W.pack_graphs(graphs)
+    assert (N, nnz) == (ref.row_ptr.size - 1, ref.col.size)
+    bufs = (np.full(N + 17, -7, dtype=np.int64), np.full(nnz + 5, -7, dtype=np.int32),
+            np.full(nnz + 5, np.nan), np.full(N + 3, -7, dtype=np.int32))
+    pk = W.pack_graphs(graphs, out=bufs)
+    for a, b in ((pk.row_ptr, ref.row_ptr), (pk.col, ref.col), (pk.w, ref.w), (pk.parent, ref.parent)):
+        assert np.array_equal(a, b)
+    assert np.shares_memory(pk.col, bufs[1]) and bufs[1][nnz] == -7  # written in place, nothing past the end
+    for i, g in enumerate(graphs):
+        v0, v1 = int(pk.vtx_ptr[i]), int(pk.vtx_ptr[i + 1])
+        e0 = int(pk.row_ptr[v0])
+        assert np.array_equal(pk.row_ptr[v0:v1 + 1] - e0, g.row_ptr)
+        assert np.array_equal(pk.col[e0:e0 + 2 * g.m] - v0, g.col)
+        par = pk.parent[v0:v1]
+        assert np.array_equal(np.where(par < 0, -1, par - v0), g.parent)
