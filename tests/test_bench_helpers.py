@@ -69,3 +69,35 @@ def test_kernel_traffic_only_for_unchanged_kernel(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k_score", "w") == 1215.0
     (d / "pdg_score.cu").write_bytes(src + b"// edited\n")
     assert bench.ncu_traffic("k_score", "w") is None
+
+
+class _FakeNvml:
+    max_mhz = 2070.0
+
+    def __init__(self, samples):
+        self.samples = samples
+
+
+def test_clock_record_from_nvml_samples():
+    cs = bench.ClockSampler(0)
+    bits = bench._NvmlSampler.BITS
+    cs.nvml = _FakeNvml([(2070.0, 0), (2070.0, bits["sw_power_cap"]), (1965.0, bits["hw_slowdown"]), (2070.0, 0)])
+    rec = cs.summary()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 4
+    assert rec["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    cs.nvml = _FakeNvml([])
+    assert cs.summary()["reasons"] == ["no samples"]
+
+
+def test_clock_record_from_nvidia_smi_csv(tmp_path):
+    cs = bench.ClockSampler(0)
+    cs.path = str(tmp_path / "clocks.csv")
+    cs.proc = object()  # the sampler ran
+    rows = ["0, 2070, 2070, 905.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1380.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # unreadable sample
+            "0, 2070, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active"]
+    (tmp_path / "clocks.csv").write_text("\n".join(rows) + "\n")
+    rec = cs.summary()
+    assert rec["samples"] == 3 and rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"] and rec["source"] == "nvidia-smi"
